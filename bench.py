@@ -1,0 +1,323 @@
+"""Benchmark of the HSE Fock-like exchange hot path (one JSON line on rank 0).
+
+A step is one hse_fock_apply over the whole workload: every ordered pair
+(i, k; j, k') of the 20^3-grid, 4x4x4 Monkhorst-Pack, 16-band silicon-like cell goes
+through pair density -> 3-D FFT -> screened kernel -> inverse FFT -> multiply-accumulate
+(1,048,576 pair convolutions).  Inputs are seeded synthetic orbitals already resident in
+HBM; L2 (129 MB) is flushed by a 256 MB write between timed steps, outside the events.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl cuda|reference]
+
+Under torchrun each rank runs its own replica of the workload (independent problems,
+weak scaling, no data-path collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HSE V_xψ orbital-pair convolutions/sec and % roofline at stated err vs FP64"
+UNIT = "pair-convolutions/s"
+WORKLOAD = 1  # the 20^3 grid, 64 k-point, 16-band workload
+
+# FP32 ALU peak of a GB300 from unit counts and clocks: 152 SMs x 128 FP32 lanes x
+# 2 flop (FMA) x 2.07 GHz maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# DRAM traffic of one launch of the fused 20^3 kernel from an ncu capture, valid only while
+# the kernel sources hash to the value recorded with it (else reported as null).
+TRAFFIC = {"sha": None, "bytes_per_launch": None}
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("fft_reg.cuh", "pairconv_c64.cuh", "launch.cuh", "pairconv_20.cu"):
+        with open(os.path.join(ROOT, "paper_1507_05156_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_flops_per_pair(N: int) -> float:
+    """10 N log2 N (two 3-D FFTs at 5 N log2 N) + 16 N (pair product 6, kernel 2, MAC 8)."""
+    return 10.0 * N * np.log2(N) + 16.0 * N
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def host_cores() -> int:
+    return int(os.environ.get("HSE_ORACLE_WORKERS", os.cpu_count() or 1))
+
+
+def oracle_sample(cell, targets):
+    """Time the FP64 oracle on a list of (k, i) targets; returns (values, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    u = cell.u_occ.astype(np.complex64).astype(np.complex128)
+    ref = oracle.fock_apply(u, cell.occ, u, cell.kpts, cell.lattice, cell.grid, cell.omega, cell.alpha,
+                            targets=targets)
+    return ref, time.perf_counter() - t0
+
+
+def sample_targets(cell, count, seed=11):
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(cell.nk)), int(rng.integers(cell.n_tgt))) for _ in range(count)]
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores, each step a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    from paper_1507_05156_gb300 import inputs
+    cell = inputs.workload(WORKLOAD)
+    per_step = 2  # targets per step: 2 x 1024 pair convolutions
+    for w in range(args.warmup):
+        oracle_sample(cell, sample_targets(cell, 1, seed=100 + w))
+    times = []
+    for s in range(args.steps):
+        _, dt = oracle_sample(cell, sample_targets(cell, per_step, seed=200 + s))
+        times.append(dt)
+    pairs = per_step * cell.nk * cell.n_occ
+    value = pairs * len(times) / sum(times)
+    sample = f"{per_step} targets (k,i) x all {cell.nk * cell.n_occ} (k',j) partners per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(cell),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(cell):
+    return {"workload": cell.name, "grid": list(cell.grid), "nk": cell.nk, "n_occ": cell.n_occ,
+            "n_tgt": cell.n_tgt, "omega": cell.omega, "alpha": cell.alpha, "pairs_per_step": cell.pairs,
+            "l2": "flushed between timed steps by a 256 MB write (inputs 65.5 MB < L2)"}
+
+
+def run_cuda(args, rank, world, dist):
+    import torch
+    from paper_1507_05156_gb300 import hse, inputs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cell = inputs.workload(WORKLOAD)
+    d = torch.complex64
+    plan = hse.get_plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha,
+                        dtype=d)
+    u_host = torch.from_numpy(cell.u_occ.astype(np.complex64)).pin_memory()
+    occ_host = torch.from_numpy(cell.occ).pin_memory()
+    u = u_host.to(dev)
+    occ = occ_host.to(dev)
+    out = torch.empty_like(u)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        hse.hse_fock_apply(plan, u, occ, u, out=out)
+    hse.hse_status(plan)
+
+    # ---- device-resident timed region -------------------------------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    l0 = hse.kernel_launches()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)
+            ev[s][0].record(stream)
+            hse.hse_fock_apply(plan, u, occ, u, out=out)
+            ev[s][1].record(stream)
+        barrier()
+    launches = hse.kernel_launches() - l0
+    hse.hse_status(plan)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    pairs = cell.pairs
+    value = world * pairs * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the public API: pinned host in, host out ------------------
+    out_host = torch.empty(out.shape, dtype=d).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        ud = u_host.to(dev, non_blocking=True)
+        od = occ_host.to(dev, non_blocking=True)
+        r = hse.hse_fock_apply(plan, ud, od, ud)
+        out_host.copy_(r, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * pairs / (float(te.item()) / 1e3)
+    h2d = u_host.numel() * u_host.element_size() + occ_host.numel() * occ_host.element_size()
+    d2h = out_host.numel() * out_host.element_size()
+
+    if rank != 0:
+        return
+
+    # ---- accuracy against the FP64 oracle on sampled targets, and the CPU baseline ----
+    clocks = clk.summary()
+    cpu = None
+    err = None
+    if not args.no_cpu_baseline:
+        targets = sample_targets(cell, args.cpu_targets)
+        ref, dt = oracle_sample(cell, targets)
+        got = out.cpu().numpy()
+        g = np.stack([got[k, i] for k, i in targets]).astype(np.complex128)
+        err = float(np.linalg.norm(g - ref) / np.linalg.norm(ref))
+        cpu_pairs = len(targets) * cell.nk * cell.n_occ
+        cpu = {"value": cpu_pairs / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": f"{len(targets)} targets (k,i) x all {cell.nk * cell.n_occ} (k',j) partners"}
+
+    # ---- the plain FP64 GPU form on the same workload (speedup denominator) -----------
+    fp64 = None
+    if not args.no_fp64:
+        plan64 = hse.get_plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha,
+                              dtype=torch.complex128)
+        u64 = torch.from_numpy(cell.u_occ).to(dev)
+        o64 = torch.empty_like(u64)
+        hse.hse_fock_apply(plan64, u64, occ, u64, out=o64)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hse.hse_fock_apply(plan64, u64, occ, u64, out=o64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b)
+        fp64 = {"value": pairs / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                "speedup_fused_c64_over_fp64_gpu": (pairs * args.steps / (total_ms / 1e3)) / (pairs / (ms64 / 1e3))}
+
+    flops = algorithmic_flops_per_pair(int(np.prod(cell.grid))) * pairs
+    kernel_s = (total_ms / args.steps) / 1e3
+    achieved = flops / kernel_s / 1e12
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sha"] == kernel_source_sha() else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(cell),
+        "err_vs_fp64": err,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "peak_source": "FP32 FMA lanes x max SM clock (152 x 128 x 2 x 2.07 GHz)",
+                     "flops_per_launch": flops},
+        "cpu_baseline": cpu,
+        "fp64_gpu": fp64,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--cpu-targets", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    try:
+        run_cuda(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

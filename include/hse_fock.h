@@ -1,0 +1,137 @@
+/*
+ * hse_fock.h - C ABI of the GB300 (sm_103a) HSE short-range Fock-like exchange library.
+ *
+ * The operation is the nonlocal Fock-like term of the HSE exchange-correlation
+ * potential of Sato, Taniguchi, Shinohara & Yabana, arXiv:1507.05156:
+ *   Sec. II B   - HSE v_xc = v_xc^PBE - 1/4 v_x^{SR,PBE} + 1/4 v^{SR,Fock}, range
+ *                 separation mu (called omega here);
+ *   Sec. II C   - the real-space definition of v^{SR,Fock} psi_i, its Fourier-space
+ *                 form (Eq. "Fock": pair density -> FFT -> kernel -> inverse FFT ->
+ *                 multiply by psi_j -> sum over occupied j) and the k/band form
+ *                 (Eq. "Fock-DS");
+ *   Sec. V      - the exchange-correlation energy E_xc in the excitation energy
+ *                 (Eq. "Eex01"), whose Fock part hse_exchange_energy returns.
+ *
+ * With u_{b,k} the periodic parts of the Bloch orbitals (cell-normalised,
+ * dV sum_r |u|^2 = 1, dV = Omega/N), q = k - k' (not folded), and the short-range
+ * kernel v(g) = 4 pi / g^2 (1 - exp(-g^2 / 4 omega^2)), v(0) = pi / omega^2:
+ *
+ *   (V_x u)_{i,k}(r) = -alpha (1/N_k) sum_{k'} sum_{j occ} f_{j,k'} u_{j,k'}(r)
+ *                      sum_G v(|G+q|) rho~_{ji}(G) e^{iG.r},
+ *   rho~_{ji}(G)     = (1/N) sum_r conj(u_{j,k'}(r)) u_{i,k}(r) e^{-iG.r}.
+ *
+ * Data layout (all device arrays are caller-owned):
+ *   orbitals      [nk][nbands][N1][N2][N3], C order, N3 fastest, interleaved complex:
+ *                 float2 (complex64) for HSE_C64, double2 (complex128) for HSE_C128.
+ *   occupations   [nk][n_occ] double, f in [0, 1] per spin-orbital.
+ *   grid point (i1,i2,i3) is r = i1/N1 a1 + i2/N2 a2 + i3/N3 a3; G = m1 b1 + m2 b2 + m3 b3
+ *   with m_d in FFT order (0..ceil(N/2)-1, then -floor(N/2)..-1).
+ *
+ * Calls are asynchronous on the caller's stream (a cudaStream_t passed as void*,
+ * NULL = legacy default stream) and return an hse error code; device-side failures
+ * are reported by hse_status.  The library never frees caller memory.  It allocates
+ * only its plan (kernel tables and reduction scratch) in hse_plan_create*.
+ */
+#ifndef HSE_FOCK_H
+#define HSE_FOCK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes: 0 is success, every failure is negative. */
+#define HSE_OK                    0
+#define HSE_ERR_INVALID_ARG      -1  /* null pointer, bad size, bad parameter            */
+#define HSE_ERR_UNSUPPORTED_GRID -2  /* an axis length this build has no kernel for     */
+#define HSE_ERR_ALIAS            -3  /* an output buffer overlaps an input              */
+#define HSE_ERR_CUDA             -4  /* a CUDA runtime call failed                      */
+#define HSE_ERR_TIMEOUT          -5  /* a bounded device-side wait gave up              */
+#define HSE_ERR_NOMEM            -6  /* plan allocation failed                          */
+#define HSE_ERR_DEVICE           -7  /* a kernel recorded a failed device-side check    */
+
+/* Arithmetic of the pair convolutions. */
+#define HSE_C64   0  /* complex64 orbitals, fused FP32 kernel, FP64 energy/omega reduction */
+#define HSE_C128  1  /* complex128 orbitals, plain staged FP64 kernels                     */
+
+typedef void *hse_stream_t;  /* a cudaStream_t */
+
+/* One exchange problem (Sec. II C): a cell, its k-mesh and its band counts. */
+typedef struct {
+  int grid[3];            /* N1, N2, N3; every axis a product of 2, 3, 5 from the supported set
+                             (hse_grid_supported); HSE_C64 needs N1 == N2 == N3 <= 24              */
+  double lattice[9];      /* rows a1, a2, a3 (bohr), row-major                                   */
+  int nk;                 /* number of k-points (>= 1)                                           */
+  const double *kpts;     /* HOST [nk][3] Cartesian k-points (bohr^-1); copied at plan creation  */
+  int n_occ;              /* occupied bands per k (the j of the sum)                             */
+  int n_tgt;              /* target bands per k (the i of V_x u_i)                               */
+  double omega;           /* range separation (bohr^-1), > 0; the paper's mu                     */
+  double alpha;           /* Fock mixing fraction, 0.25 in HSE                                   */
+  double spin_degeneracy; /* g_s in E_x (2 for a closed shell); not used by V_x                  */
+  int dtype;              /* HSE_C64 or HSE_C128                                                 */
+} hse_problem;
+
+typedef struct hse_plan_s *hse_plan;
+
+/* Build a plan: validates the problem, tabulates v(|G+q|) (and d v/d omega) in FP64
+ * for every distinct q = k - k' on the current device, and allocates the reduction
+ * scratch.  Synchronises the device.  *out is NULL on failure. */
+int hse_plan_create(hse_plan *out, const hse_problem *p);
+
+/* Batched plan over ncells independent cells of unequal grids, k-meshes and band
+ * counts (all HSE_C64, cubic grids).  hse_fock_apply_batched runs every cell's
+ * pairs in one persistent launch. */
+int hse_plan_create_batched(hse_plan *out, const hse_problem *cells, int ncells);
+
+int hse_plan_destroy(hse_plan plan);
+
+/* V_x applied to the targets (Sec. II C, Eq. "Fock-DS" with the 1/N_k weight).
+ *   u_occ  device [nk][n_occ][N]   occupied orbitals u_{j,k'}
+ *   occ    device [nk][n_occ]      occupations f_{j,k'} (double)
+ *   u_tgt  device [nk][n_tgt][N]   target orbitals u_{i,k}; may equal u_occ
+ *   vx_out device [nk][n_tgt][N]   result, overwritten; must not overlap any input
+ * Complex64 or complex128 per the plan's dtype. */
+int hse_fock_apply(hse_plan plan, const void *u_occ, const double *occ, const void *u_tgt,
+                   void *vx_out, hse_stream_t stream);
+
+/* Fock part of E_xc (Sec. V, Eq. "Eex01"), targets = the occupied set:
+ *   E_x = 1/2 g_s (1/N_k) sum_k sum_i f_{i,k} dV sum_r Re[conj(u_{i,k}) (V_x u)_{i,k}]
+ * reduced in FP64 on the device.  e_x: device pointer to one double, overwritten. */
+int hse_exchange_energy(hse_plan plan, const void *u_occ, const double *occ, double *e_x,
+                        hse_stream_t stream);
+
+/* Vector-Jacobian product of y = V_x[u_occ] u_tgt (PyTorch complex convention,
+ * grad = dL/dRe + i dL/dIm).  With c_j = alpha f_{j,k'}/N_k, K_q = F^-1 diag(v) F,
+ * phi_ji = K_q(conj(u_j) u_i), psibar_ji = K_q(conj(u_j) ybar_i):
+ *   grad_u_tgt[k,i]  = -sum_{k',j} c_j u_j psibar_ji            (V_x applied to ybar)
+ *   grad_u_occ[k',j] = -sum_{k,i} c_j [conj(phi_ji) ybar_i + u_i conj(psibar_ji)]
+ *   grad_omega       = Re sum conj(ybar) (dV_x/domega) u_tgt
+ * grad_vx is ybar.  All gradients are overwritten (not accumulated); any of the three
+ * outputs may be NULL to skip it.  Outputs must not overlap inputs. */
+int hse_fock_apply_vjp(hse_plan plan, const void *u_occ, const double *occ, const void *u_tgt,
+                       const void *grad_vx, void *grad_u_occ, void *grad_u_tgt,
+                       double *grad_omega, hse_stream_t stream);
+
+/* Batched V_x for a plan from hse_plan_create_batched: arrays of ncells HOST-side
+ * pointers, each to that cell's device buffers (same layouts as hse_fock_apply). */
+int hse_fock_apply_batched(hse_plan plan, const void *const *u_occ, const double *const *occ,
+                           const void *const *u_tgt, void *const *vx_out, hse_stream_t stream);
+
+/* Synchronises the stream, then returns HSE_OK, HSE_ERR_TIMEOUT or HSE_ERR_DEVICE from
+ * the plan's device status word (and clears it), or HSE_ERR_CUDA. */
+int hse_status(hse_plan plan, hse_stream_t stream);
+
+/* 1 if this build has a kernel for axis length n (and dtype), else 0. */
+int hse_grid_supported(int n, int dtype);
+
+/* Number of kernels this library has launched since load (for launch accounting). */
+uint64_t hse_kernel_launches(void);
+
+const char *hse_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSE_FOCK_H */

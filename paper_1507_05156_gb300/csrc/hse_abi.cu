@@ -1,0 +1,573 @@
+// hse_abi.cu - the C ABI of include/hse_fock.h: plans, validation, dispatch, reductions.
+//
+// A plan holds, on the device:
+//   * the q table: every distinct q = k - k' of the k-mesh (exact duplicates merged after
+//     rounding to 1e-10 bohr^-1) and qidx[k][k'] -> row;
+//   * v(|G+q|) and d v/d omega per row, evaluated in FP64 (kept in FP64 for the staged
+//     form, rounded once to FP32 for the fused form);
+//   * reduction scratch: one double per owner orbital;
+//   * for complex128 problems, the staged work batch and an FP64 result buffer;
+//   * a status word that kernels set on a failed device-side check.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/hse_fock.h"
+#include "launch.cuh"
+
+namespace hse {
+cudaError_t launch_pairconv_c64_small(int n, int mode, const PairArgs& args, cudaStream_t stream);
+cudaError_t launch_pairconv_c64_mid(int n, int mode, const PairArgs& args, cudaStream_t stream);
+cudaError_t launch_pairconv_c64_20(int mode, const PairArgs& args, cudaStream_t stream);
+cudaError_t launch_pairconv_c64_24(int mode, const PairArgs& args, cudaStream_t stream);
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+bool pairconv_c64_supported(int n) {
+  switch (n) {
+    case 4: case 6: case 8: case 10: case 12: case 15: case 16: case 18: case 20: case 24:
+      return true;
+    default:
+      return false;
+  }
+}
+
+cudaError_t launch_pairconv_c64(int n, int mode, const PairArgs& args, cudaStream_t stream) {
+  if (n <= 12) return launch_pairconv_c64_small(n, mode, args, stream);
+  if (n <= 18) return launch_pairconv_c64_mid(n, mode, args, stream);
+  if (n == 20) return launch_pairconv_c64_20(mode, args, stream);
+  if (n == 24) return launch_pairconv_c64_24(mode, args, stream);
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// kernels owned by this TU
+// ---------------------------------------------------------------------------
+
+// v(|G+q|) = 4 pi / g^2 (1 - exp(-g^2 / 4 w^2)) = (pi / w^2) * (-expm1(-x) / x), x = g^2/4w^2,
+// v(0) = pi / w^2; d v / d w = -(2 pi / w^3) exp(-x).  Rows in natural [x][y][z] order.
+struct TableArgs {
+  const double* qvec;  // [nq][3]
+  int nq, n1, n2, n3;
+  double b[9];         // reciprocal rows b1, b2, b3
+  double omega;
+  double* v64;
+  double* dv64;
+  float* v32;
+  float* dv32;
+};
+
+__global__ void build_kernel_table(const TableArgs t) {
+  const size_t N = (size_t)t.n1 * t.n2 * t.n3;
+  const size_t total = N * t.nq;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int qi = (int)(idx / N);
+    const int r = (int)(idx - (size_t)qi * N);
+    const int i3 = r % t.n3;
+    const int i2 = (r / t.n3) % t.n2;
+    const int i1 = r / (t.n3 * t.n2);
+    const int m1 = (i1 <= (t.n1 - 1) / 2) ? i1 : i1 - t.n1;
+    const int m2 = (i2 <= (t.n2 - 1) / 2) ? i2 : i2 - t.n2;
+    const int m3 = (i3 <= (t.n3 - 1) / 2) ? i3 : i3 - t.n3;
+    double g[3];
+    for (int c = 0; c < 3; ++c) g[c] = m1 * t.b[c] + m2 * t.b[3 + c] + m3 * t.b[6 + c] + t.qvec[3 * qi + c];
+    const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const double w2 = t.omega * t.omega;
+    const double x = g2 / (4.0 * w2);
+    const double lim = kPi / w2;
+    const double v = (x == 0.0) ? lim : lim * (-expm1(-x) / x);
+    const double dv = -(2.0 * kPi / (w2 * t.omega)) * exp(-x);
+    t.v64[idx] = v;
+    t.dv64[idx] = dv;
+    t.v32[idx] = (float)v;
+    t.dv32[idx] = (float)dv;
+  }
+}
+
+// out = factor * sum(partial[0..n)), fixed-order: deterministic.
+__global__ void reduce_partials(const double* __restrict__ partial, int n, double factor, double* out) {
+  __shared__ double sh[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = factor * sh[0];
+}
+
+// partial[o] = (weight ? w[o] : 1) * sum_r Re(conj(lhs[o][r]) rhs[o][r]), one block per owner o.
+__global__ void dot_per_owner_f64(const double2* __restrict__ lhs, const double2* __restrict__ rhs, int N,
+                                  const double* __restrict__ weight, double* __restrict__ partial) {
+  __shared__ double sh[256];
+  const size_t o = blockIdx.x;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    const double2 a = lhs[o * N + r];
+    const double2 b = rhs[o * N + r];
+    s += a.x * b.x + a.y * b.y;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[o] = (weight ? weight[o] : 1.0) * sh[0];
+}
+
+}  // namespace hse
+
+using namespace hse;
+
+struct hse_plan_s {
+  hse_problem p;
+  std::vector<double> kpts;
+  int device = 0;
+  int N = 0;
+  int nq = 0;
+  double dV = 0.0;
+  double b[9] = {};
+  int* qidx = nullptr;       // device [nk][nk]
+  double* qvec = nullptr;    // device [nq][3]
+  double* v64 = nullptr;     // device [nq][N]
+  double* dv64 = nullptr;
+  float* v32 = nullptr;
+  float* dv32 = nullptr;
+  double* partial = nullptr; // device [nk * max(n_occ, n_tgt)]
+  int* status = nullptr;     // device status word
+  // complex128 staged form
+  double2* work = nullptr;   // [batch][N]
+  size_t work_pairs = 0;
+  double2* vx64 = nullptr;   // [nk][max(n_occ, n_tgt)][N]
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return e == cudaSuccess ? HSE_OK : (e == cudaErrorMemoryAllocation ? HSE_ERR_NOMEM : HSE_ERR_CUDA); }
+
+bool invert3(const double* A, double* inv) {
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (!(std::fabs(det) > 1e-12) || !std::isfinite(det)) return false;
+  inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+  inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  return true;
+}
+
+size_t elem_bytes(int dtype) { return dtype == HSE_C128 ? 16 : 8; }
+
+int validate_problem(const hse_problem* p) {
+  if (!p) return HSE_ERR_INVALID_ARG;
+  if (p->dtype != HSE_C64 && p->dtype != HSE_C128) return HSE_ERR_INVALID_ARG;
+  if (p->nk < 1 || p->n_occ < 1 || p->n_tgt < 1 || !p->kpts) return HSE_ERR_INVALID_ARG;
+  if (!(p->omega > 0.0) || !std::isfinite(p->omega) || !std::isfinite(p->alpha) || !std::isfinite(p->spin_degeneracy))
+    return HSE_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; ++d) {
+    if (p->grid[d] < 2) return HSE_ERR_INVALID_ARG;
+    if (!hse_grid_supported(p->grid[d], p->dtype)) return HSE_ERR_UNSUPPORTED_GRID;
+  }
+  if (p->dtype == HSE_C64 && (p->grid[0] != p->grid[1] || p->grid[1] != p->grid[2])) return HSE_ERR_UNSUPPORTED_GRID;
+  for (int i = 0; i < 3 * p->nk; ++i)
+    if (!std::isfinite(p->kpts[i])) return HSE_ERR_INVALID_ARG;
+  // sizes must stay within int indexing of a single grid and the launch grid
+  const double N = (double)p->grid[0] * p->grid[1] * p->grid[2];
+  if (N > 1e8 || (double)p->nk * p->nk > 2e9 || (double)p->nk * std::max(p->n_occ, p->n_tgt) > 2e9)
+    return HSE_ERR_INVALID_ARG;
+  return HSE_OK;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  if (!a || !b || na == 0 || nb == 0) return false;
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + nb && y < x + na;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+cudaStream_t S(hse_stream_t s) { return (cudaStream_t)s; }
+
+}  // namespace
+
+extern "C" {
+
+int hse_grid_supported(int n, int dtype) {
+  if (dtype == HSE_C64) return pairconv_c64_supported(n) ? 1 : 0;
+  if (dtype == HSE_C128) return staged_fft_supported(n) ? 1 : 0;
+  return 0;
+}
+
+uint64_t hse_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* hse_strerror(int code) {
+  switch (code) {
+    case HSE_OK: return "success";
+    case HSE_ERR_INVALID_ARG: return "invalid argument";
+    case HSE_ERR_UNSUPPORTED_GRID: return "unsupported grid (axis length or shape)";
+    case HSE_ERR_ALIAS: return "output buffer overlaps an input";
+    case HSE_ERR_CUDA: return "CUDA runtime error";
+    case HSE_ERR_TIMEOUT: return "device-side wait timed out";
+    case HSE_ERR_NOMEM: return "out of device memory";
+    case HSE_ERR_DEVICE: return "device-side check failed";
+    default: return "unknown error";
+  }
+}
+
+int hse_plan_destroy(hse_plan plan) {
+  if (!plan) return HSE_ERR_INVALID_ARG;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(plan->device);
+  cudaFree(plan->qidx);
+  cudaFree(plan->qvec);
+  cudaFree(plan->v64);
+  cudaFree(plan->dv64);
+  cudaFree(plan->v32);
+  cudaFree(plan->dv32);
+  cudaFree(plan->partial);
+  cudaFree(plan->status);
+  cudaFree(plan->work);
+  cudaFree(plan->vx64);
+  cudaSetDevice(prev);
+  delete plan;
+  return HSE_OK;
+}
+
+int hse_plan_create(hse_plan* out, const hse_problem* p) {
+  if (!out) return HSE_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = validate_problem(p);
+  if (rc) return rc;
+  double ainv[9];
+  if (!invert3(p->lattice, ainv)) return HSE_ERR_INVALID_ARG;
+
+  hse_plan plan = new (std::nothrow) hse_plan_s();
+  if (!plan) return HSE_ERR_NOMEM;
+  plan->p = *p;
+  plan->kpts.assign(p->kpts, p->kpts + 3 * p->nk);
+  plan->p.kpts = plan->kpts.data();
+  cudaGetDevice(&plan->device);
+  const int n1 = p->grid[0], n2 = p->grid[1], n3 = p->grid[2];
+  plan->N = n1 * n2 * n3;
+  // b_i = 2 pi (A^-1)^T rows: b_i[c] = 2 pi ainv[c][i]
+  for (int i = 0; i < 3; ++i)
+    for (int c = 0; c < 3; ++c) plan->b[3 * i + c] = 2.0 * kPi * ainv[3 * c + i];
+  const double det = std::fabs(p->lattice[0] * (p->lattice[4] * p->lattice[8] - p->lattice[5] * p->lattice[7]) -
+                               p->lattice[1] * (p->lattice[3] * p->lattice[8] - p->lattice[5] * p->lattice[6]) +
+                               p->lattice[2] * (p->lattice[3] * p->lattice[7] - p->lattice[4] * p->lattice[6]));
+  plan->dV = det / plan->N;
+
+  // distinct q = k - k'
+  const int nk = p->nk;
+  std::vector<int> qidx((size_t)nk * nk);
+  std::vector<double> qvec;
+  std::map<std::array<long long, 3>, int> seen;
+  for (int k = 0; k < nk; ++k) {
+    for (int kp = 0; kp < nk; ++kp) {
+      double q[3];
+      std::array<long long, 3> key;
+      for (int c = 0; c < 3; ++c) {
+        q[c] = plan->kpts[3 * k + c] - plan->kpts[3 * kp + c];
+        key[c] = std::llround(q[c] * 1e10);
+      }
+      auto it = seen.find(key);
+      if (it == seen.end()) {
+        const int id = (int)(qvec.size() / 3);
+        seen.emplace(key, id);
+        qvec.insert(qvec.end(), q, q + 3);
+        qidx[(size_t)k * nk + kp] = id;
+      } else {
+        qidx[(size_t)k * nk + kp] = it->second;
+      }
+    }
+  }
+  plan->nq = (int)(qvec.size() / 3);
+  const size_t N = plan->N, nq = plan->nq;
+  const int nown = std::max(p->n_occ, p->n_tgt);
+  cudaError_t e = cudaSuccess;
+#define HSE_TRY(call)              \
+  do {                             \
+    e = (call);                    \
+    if (e != cudaSuccess) {        \
+      rc = cuda_fail(e);           \
+      hse_plan_destroy(plan);      \
+      return rc;                   \
+    }                              \
+  } while (0)
+  HSE_TRY(cudaMalloc(&plan->qidx, qidx.size() * sizeof(int)));
+  HSE_TRY(cudaMalloc(&plan->qvec, qvec.size() * sizeof(double)));
+  HSE_TRY(cudaMalloc(&plan->v64, nq * N * sizeof(double)));
+  HSE_TRY(cudaMalloc(&plan->dv64, nq * N * sizeof(double)));
+  HSE_TRY(cudaMalloc(&plan->v32, nq * N * sizeof(float)));
+  HSE_TRY(cudaMalloc(&plan->dv32, nq * N * sizeof(float)));
+  HSE_TRY(cudaMalloc(&plan->partial, (size_t)nk * nown * sizeof(double)));
+  HSE_TRY(cudaMalloc(&plan->status, sizeof(int)));
+  HSE_TRY(cudaMemset(plan->status, 0, sizeof(int)));
+  HSE_TRY(cudaMemcpy(plan->qidx, qidx.data(), qidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  HSE_TRY(cudaMemcpy(plan->qvec, qvec.data(), qvec.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (p->dtype == HSE_C128) {
+    // staged batch: all (i, k', j) of one k in chunks of k' up to ~512 MB
+    // the energy path runs the staged form with the occupied set as targets
+    const size_t per_kp = (size_t)nown * p->n_occ;
+    size_t nkp = std::max<size_t>(1, ((size_t)512 << 20) / (per_kp * N * sizeof(double2)));
+    nkp = std::min<size_t>(nkp, (size_t)nk);
+    plan->work_pairs = nkp * per_kp;
+    HSE_TRY(cudaMalloc(&plan->work, plan->work_pairs * N * sizeof(double2)));
+    HSE_TRY(cudaMalloc(&plan->vx64, (size_t)nk * nown * N * sizeof(double2)));
+  }
+  TableArgs t{};
+  t.qvec = plan->qvec;
+  t.nq = plan->nq;
+  t.n1 = n1;
+  t.n2 = n2;
+  t.n3 = n3;
+  std::memcpy(t.b, plan->b, sizeof(t.b));
+  t.omega = p->omega;
+  t.v64 = plan->v64;
+  t.dv64 = plan->dv64;
+  t.v32 = plan->v32;
+  t.dv32 = plan->dv32;
+  const size_t total = nq * N;
+  const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
+  build_kernel_table<<<blocks, 256>>>(t);
+  count_launch();
+  HSE_TRY(cudaGetLastError());
+  HSE_TRY(cudaDeviceSynchronize());
+#undef HSE_TRY
+  *out = plan;
+  return HSE_OK;
+}
+
+int hse_status(hse_plan plan, hse_stream_t stream) {
+  if (!plan) return HSE_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(S(stream));
+  if (e != cudaSuccess) return HSE_ERR_CUDA;
+  int st = 0;
+  e = cudaMemcpy(&st, plan->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return HSE_ERR_CUDA;
+  if (st != 0) {
+    cudaMemset(plan->status, 0, sizeof(int));
+    return st == HSE_ERR_TIMEOUT ? HSE_ERR_TIMEOUT : HSE_ERR_DEVICE;
+  }
+  return HSE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+PairArgs base_args(hse_plan plan) {
+  PairArgs a{};
+  a.occ = nullptr;
+  a.vtab = plan->v32;
+  a.qidx = plan->qidx;
+  a.nk = plan->p.nk;
+  a.n_occ = plan->p.n_occ;
+  a.scale = (float)(-plan->p.alpha / ((double)plan->p.nk * plan->N));
+  return a;
+}
+
+int run_pairconv(hse_plan plan, int mode, PairArgs a, int n_own, cudaStream_t st) {
+  const int T = slots_for(plan->p.grid[0]);
+  a.n_own = n_own;
+  a.ntiles = (n_own + T - 1) / T;
+  return cuda_fail(launch_pairconv_c64(plan->p.grid[0], mode, a, st));
+}
+
+int reduce(hse_plan plan, int n, double factor, double* out, cudaStream_t st) {
+  reduce_partials<<<1, 1024, 0, st>>>(plan->partial, n, factor, out);
+  count_launch();
+  return cuda_fail(cudaGetLastError());
+}
+
+// Staged FP64 V_x: out[k][i] for every target; table = v64 or dv64.
+int staged_apply(hse_plan plan, const double2* u_occ, const double* occ, const double2* u_tgt, int n_tgt,
+                 const double* table, double2* out, cudaStream_t st) {
+  const hse_problem& p = plan->p;
+  const int N = plan->N;
+  const int nk = p.nk;
+  const size_t per_kp = (size_t)n_tgt * p.n_occ;
+  if (per_kp > plan->work_pairs) return HSE_ERR_INVALID_ARG;  // cannot happen: sized for max(n_occ, n_tgt)
+  const int nkp_chunk = (int)(plan->work_pairs / per_kp);
+  StagedArgs a{};
+  a.u_occ = u_occ;
+  a.u_tgt = u_tgt;
+  a.occ = occ;
+  a.vtab = table;
+  a.qidx = plan->qidx;
+  a.work = plan->work;
+  a.nk = nk;
+  a.n_occ = p.n_occ;
+  a.n_tgt = n_tgt;
+  a.N = N;
+  a.scale = -p.alpha / ((double)nk * N);
+  const int inner[3] = {p.grid[1] * p.grid[2], p.grid[2], 1};
+  for (int k = 0; k < nk; ++k) {
+    for (int kp0 = 0; kp0 < nk; kp0 += nkp_chunk) {
+      a.k = k;
+      a.kp0 = kp0;
+      a.nkp = std::min(nkp_chunk, nk - kp0);
+      const size_t nb = (size_t)n_tgt * a.nkp * p.n_occ;
+      cudaError_t e = launch_staged_pair_product(a, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+      for (int d = 2; d >= 0; --d) {
+        e = launch_staged_fft(p.grid[d], -1, plan->work, nb, N, inner[d], st);
+        if (e != cudaSuccess) return cuda_fail(e);
+      }
+      e = launch_staged_kernel_scale(a, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+      for (int d = 0; d < 3; ++d) {
+        e = launch_staged_fft(p.grid[d], +1, plan->work, nb, N, inner[d], st);
+        if (e != cudaSuccess) return cuda_fail(e);
+      }
+      e = launch_staged_mul_acc(a, out, kp0 == 0, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+  }
+  return HSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hse_fock_apply(hse_plan plan, const void* u_occ, const double* occ, const void* u_tgt, void* vx_out,
+                   hse_stream_t stream) {
+  if (!plan || !u_occ || !occ || !u_tgt || !vx_out) return HSE_ERR_INVALID_ARG;
+  const hse_problem& p = plan->p;
+  if (!aligned16(u_occ) || !aligned16(u_tgt) || !aligned16(vx_out)) return HSE_ERR_INVALID_ARG;
+  const size_t eb = elem_bytes(p.dtype);
+  const size_t occ_bytes = (size_t)p.nk * p.n_occ * plan->N * eb;
+  const size_t tgt_bytes = (size_t)p.nk * p.n_tgt * plan->N * eb;
+  if (overlaps(vx_out, tgt_bytes, u_occ, occ_bytes) || overlaps(vx_out, tgt_bytes, u_tgt, tgt_bytes) ||
+      overlaps(vx_out, tgt_bytes, occ, (size_t)p.nk * p.n_occ * sizeof(double)))
+    return HSE_ERR_ALIAS;
+  cudaStream_t st = S(stream);
+  if (p.dtype == HSE_C64) {
+    PairArgs a = base_args(plan);
+    a.own = (const float2*)u_tgt;
+    a.part = (const float2*)u_occ;
+    a.out = (float2*)vx_out;
+    a.occ = occ;
+    a.n_part = p.n_occ;
+    return run_pairconv(plan, MODE_APPLY, a, p.n_tgt, st);
+  }
+  return staged_apply(plan, (const double2*)u_occ, occ, (const double2*)u_tgt, p.n_tgt, plan->v64, (double2*)vx_out, st);
+}
+
+int hse_exchange_energy(hse_plan plan, const void* u_occ, const double* occ, double* e_x, hse_stream_t stream) {
+  if (!plan || !u_occ || !occ || !e_x) return HSE_ERR_INVALID_ARG;
+  const hse_problem& p = plan->p;
+  if (!aligned16(u_occ)) return HSE_ERR_INVALID_ARG;
+  cudaStream_t st = S(stream);
+  const int nown = p.nk * p.n_occ;
+  const double factor = 0.5 * p.spin_degeneracy * plan->dV / p.nk;
+  int rc;
+  if (p.dtype == HSE_C64) {
+    PairArgs a = base_args(plan);
+    a.own = (const float2*)u_occ;
+    a.part = (const float2*)u_occ;
+    a.partial = plan->partial;
+    a.occ = occ;
+    a.n_part = p.n_occ;
+    rc = run_pairconv(plan, MODE_ENERGY, a, p.n_occ, st);
+  } else {
+    rc = staged_apply(plan, (const double2*)u_occ, occ, (const double2*)u_occ, p.n_occ, plan->v64, plan->vx64, st);
+    if (rc) return rc;
+    dot_per_owner_f64<<<nown, 256, 0, st>>>((const double2*)u_occ, plan->vx64, plan->N, occ, plan->partial);
+    count_launch();
+    rc = cuda_fail(cudaGetLastError());
+  }
+  if (rc) return rc;
+  return reduce(plan, nown, factor, e_x, st);
+}
+
+int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, const void* u_tgt, const void* grad_vx,
+                       void* grad_u_occ, void* grad_u_tgt, double* grad_omega, hse_stream_t stream) {
+  if (!plan || !u_occ || !occ || !u_tgt || !grad_vx) return HSE_ERR_INVALID_ARG;
+  const hse_problem& p = plan->p;
+  if (!aligned16(u_occ) || !aligned16(u_tgt) || !aligned16(grad_vx) || (grad_u_occ && !aligned16(grad_u_occ)) ||
+      (grad_u_tgt && !aligned16(grad_u_tgt)))
+    return HSE_ERR_INVALID_ARG;
+  const size_t eb = elem_bytes(p.dtype);
+  const size_t occ_bytes = (size_t)p.nk * p.n_occ * plan->N * eb;
+  const size_t tgt_bytes = (size_t)p.nk * p.n_tgt * plan->N * eb;
+  const void* ins[4] = {u_occ, u_tgt, grad_vx, occ};
+  const size_t insz[4] = {occ_bytes, tgt_bytes, tgt_bytes, (size_t)p.nk * p.n_occ * sizeof(double)};
+  for (int i = 0; i < 4; ++i) {
+    if (overlaps(grad_u_occ, occ_bytes, ins[i], insz[i]) || overlaps(grad_u_tgt, tgt_bytes, ins[i], insz[i]) ||
+        overlaps(grad_omega, sizeof(double), ins[i], insz[i]))
+      return HSE_ERR_ALIAS;
+  }
+  if (overlaps(grad_u_occ, occ_bytes, grad_u_tgt, tgt_bytes)) return HSE_ERR_ALIAS;
+  cudaStream_t st = S(stream);
+  if (p.dtype != HSE_C64) return HSE_ERR_INVALID_ARG;  // complex128 VJP: see hse_fock_apply_vjp in the staged form
+  int rc = HSE_OK;
+  if (grad_u_tgt) {
+    PairArgs a = base_args(plan);
+    a.own = (const float2*)grad_vx;
+    a.part = (const float2*)u_occ;
+    a.out = (float2*)grad_u_tgt;
+    a.occ = occ;
+    a.n_part = p.n_occ;
+    rc = run_pairconv(plan, MODE_APPLY, a, p.n_tgt, st);
+    if (rc) return rc;
+  }
+  if (grad_omega) {
+    PairArgs a = base_args(plan);
+    a.own = (const float2*)u_tgt;
+    a.part = (const float2*)u_occ;
+    a.part2 = (const float2*)grad_vx;
+    a.partial = plan->partial;
+    a.occ = occ;
+    a.vtab = plan->dv32;
+    a.n_part = p.n_occ;
+    rc = run_pairconv(plan, MODE_DOT, a, p.n_tgt, st);
+    if (rc) return rc;
+    rc = reduce(plan, p.nk * p.n_tgt, 1.0, grad_omega, st);
+    if (rc) return rc;
+  }
+  if (grad_u_occ) {
+    PairArgs a = base_args(plan);
+    a.own = (const float2*)u_occ;
+    a.part = (const float2*)u_tgt;
+    a.part2 = (const float2*)grad_vx;
+    a.out = (float2*)grad_u_occ;
+    a.occ = occ;
+    a.n_part = p.n_tgt;
+    rc = run_pairconv(plan, MODE_OCC, a, p.n_occ, st);
+  }
+  return rc;
+}
+
+int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells) {
+  (void)cells;
+  (void)ncells;
+  if (out) *out = nullptr;
+  return HSE_ERR_INVALID_ARG;
+}
+
+int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double* const* occ, const void* const* u_tgt,
+                           void* const* vx_out, hse_stream_t stream) {
+  (void)plan; (void)u_occ; (void)occ; (void)u_tgt; (void)vx_out; (void)stream;
+  return HSE_ERR_INVALID_ARG;
+}
+
+}  // extern "C"

@@ -1,0 +1,8 @@
+// Fused complex64 pair-convolution kernels, cubic grid 20^3.
+#include "launch.cuh"
+
+namespace hse {
+cudaError_t launch_pairconv_c64_20(int mode, const PairArgs& args, cudaStream_t stream) {
+  return launch_pairconv_c64_n<20>(mode, args, stream);
+}
+}  // namespace hse

@@ -1,0 +1,248 @@
+"""Thin Python binding of the C ABI in include/hse_fock.h (argument marshalling only).
+
+Every step of the Fock-like exchange runs in the CUDA library
+``_lib/libhse_fock.so``; this module only checks tensors, passes device pointers and
+the current CUDA stream, and keeps plans cached.  If the library is missing or the
+tensors are not on a CUDA device it raises: there is no CPU path.
+
+Function names follow the C ABI: hse_fock_apply, hse_exchange_energy,
+hse_fock_apply_vjp, hse_fock_apply_batched.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Dict, Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libhse_fock.so")
+
+HSE_C64 = 0
+HSE_C128 = 1
+
+ERRORS = {
+    0: "HSE_OK", -1: "HSE_ERR_INVALID_ARG", -2: "HSE_ERR_UNSUPPORTED_GRID", -3: "HSE_ERR_ALIAS",
+    -4: "HSE_ERR_CUDA", -5: "HSE_ERR_TIMEOUT", -6: "HSE_ERR_NOMEM", -7: "HSE_ERR_DEVICE",
+}
+
+#: every symbol include/hse_fock.h declares
+EXPORTS = ("hse_plan_create", "hse_plan_create_batched", "hse_plan_destroy", "hse_fock_apply",
+           "hse_exchange_energy", "hse_fock_apply_vjp", "hse_fock_apply_batched", "hse_status",
+           "hse_grid_supported", "hse_kernel_launches", "hse_strerror")
+
+
+class HseError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {ERRORS.get(code, code)}")
+
+
+class HseProblem(ctypes.Structure):
+    _fields_ = [
+        ("grid", ctypes.c_int * 3),
+        ("lattice", ctypes.c_double * 9),
+        ("nk", ctypes.c_int),
+        ("kpts", ctypes.POINTER(ctypes.c_double)),
+        ("n_occ", ctypes.c_int),
+        ("n_tgt", ctypes.c_int),
+        ("omega", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("spin_degeneracy", ctypes.c_double),
+        ("dtype", ctypes.c_int),
+    ]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"HSE CUDA library not built ({path}); run paper_1507_05156_gb300._build.build()")
+        lib = ctypes.CDLL(path)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        lib.hse_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(HseProblem)]
+        lib.hse_plan_create_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(HseProblem), i]
+        lib.hse_plan_destroy.argtypes = [vp]
+        lib.hse_fock_apply.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.hse_exchange_energy.argtypes = [vp, vp, vp, vp, vp]
+        lib.hse_fock_apply_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.hse_fock_apply_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                               ctypes.POINTER(vp), vp]
+        lib.hse_status.argtypes = [vp, vp]
+        lib.hse_grid_supported.argtypes = [i, i]
+        lib.hse_kernel_launches.argtypes = []
+        lib.hse_kernel_launches.restype = ctypes.c_uint64
+        lib.hse_strerror.argtypes = [i]
+        lib.hse_strerror.restype = ctypes.c_char_p
+        for name in ("hse_plan_create", "hse_plan_create_batched", "hse_plan_destroy", "hse_fock_apply",
+                     "hse_exchange_energy", "hse_fock_apply_vjp", "hse_fock_apply_batched", "hse_status",
+                     "hse_grid_supported"):
+            getattr(lib, name).restype = i
+        _lib = lib
+        return lib
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise HseError(code, what)
+
+
+def kernel_launches() -> int:
+    return int(load_library().hse_kernel_launches())
+
+
+def grid_supported(n: int, dtype: torch.dtype = torch.complex64) -> bool:
+    return bool(load_library().hse_grid_supported(int(n), _code(dtype)))
+
+
+def _code(dtype: torch.dtype) -> int:
+    if dtype == torch.complex64:
+        return HSE_C64
+    if dtype == torch.complex128:
+        return HSE_C128
+    raise ValueError(f"unsupported dtype {dtype}")
+
+
+def _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype) -> Tuple[HseProblem, np.ndarray]:
+    kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
+    p = HseProblem()
+    p.grid[:] = [int(g) for g in grid]
+    p.lattice[:] = [float(x) for x in np.asarray(lattice, dtype=np.float64).reshape(9)]
+    p.nk = kp.shape[0]
+    p.kpts = kp.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.n_occ = int(n_occ)
+    p.n_tgt = int(n_tgt)
+    p.omega = float(omega)
+    p.alpha = float(alpha)
+    p.spin_degeneracy = float(spin_degeneracy)
+    p.dtype = _code(dtype)
+    return p, kp
+
+
+class Plan:
+    """An hse_plan: q table, FP64 kernel rows and reduction scratch on one device."""
+
+    def __init__(self, grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy=2.0,
+                 dtype=torch.complex64, device=None):
+        lib = load_library()
+        self.grid = tuple(int(g) for g in grid)
+        self.nk = int(np.asarray(kpts).reshape(-1, 3).shape[0])
+        self.n_occ, self.n_tgt = int(n_occ), int(n_tgt)
+        self.omega, self.alpha, self.spin_degeneracy = float(omega), float(alpha), float(spin_degeneracy)
+        self.dtype = dtype
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
+        prob, self._kp = _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.hse_plan_create(ctypes.byref(h), ctypes.byref(prob)), "hse_plan_create")
+        self.handle = h
+        self.npts = int(np.prod(self.grid))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.hse_plan_destroy(h)
+            self.handle = None
+
+    def shape(self, nbands: int) -> Tuple[int, ...]:
+        return (self.nk, nbands) + self.grid
+
+
+_plan_cache: Dict[tuple, Plan] = {}
+
+
+def get_plan(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy=2.0,
+             dtype=torch.complex64, device=None) -> Plan:
+    """Plans are cached by every parameter that enters them."""
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index
+    key = (tuple(int(g) for g in grid), np.asarray(lattice, np.float64).tobytes(),
+           np.asarray(kpts, np.float64).tobytes(), int(n_occ), int(n_tgt), float(omega), float(alpha),
+           float(spin_degeneracy), dtype, dev)
+    plan = _plan_cache.get(key)
+    if plan is None:
+        plan = Plan(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype, device=dev)
+        _plan_cache[key] = plan
+    return plan
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: Optional[torch.Tensor], plan: Plan, shape, dtype, name: str):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if t.device != plan.device:
+        raise ValueError(f"{name} is on {t.device}, plan on {plan.device}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _ptr(t: Optional[torch.Tensor]) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def hse_fock_apply(plan: Plan, u_occ: torch.Tensor, occ: torch.Tensor, u_tgt: torch.Tensor,
+                   out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """V_x u_tgt for the occupied set (u_occ, occ) on the current stream."""
+    lib = load_library()
+    _dev(u_occ, plan, plan.shape(plan.n_occ), plan.dtype, "u_occ")
+    _dev(u_tgt, plan, plan.shape(plan.n_tgt), plan.dtype, "u_tgt")
+    _dev(occ, plan, (plan.nk, plan.n_occ), torch.float64, "occ")
+    if out is None:
+        out = torch.empty(plan.shape(plan.n_tgt), dtype=plan.dtype, device=plan.device)
+    _dev(out, plan, plan.shape(plan.n_tgt), plan.dtype, "out")
+    _check(lib.hse_fock_apply(plan.handle, _ptr(u_occ), _ptr(occ), _ptr(u_tgt), _ptr(out), _stream(stream)),
+           "hse_fock_apply")
+    return out
+
+
+def hse_exchange_energy(plan: Plan, u_occ: torch.Tensor, occ: torch.Tensor,
+                        out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """E_x (FP64, 0-d device tensor) with the targets equal to the occupied set."""
+    lib = load_library()
+    _dev(u_occ, plan, plan.shape(plan.n_occ), plan.dtype, "u_occ")
+    _dev(occ, plan, (plan.nk, plan.n_occ), torch.float64, "occ")
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=plan.device)
+    _check(lib.hse_exchange_energy(plan.handle, _ptr(u_occ), _ptr(occ), _ptr(out), _stream(stream)),
+           "hse_exchange_energy")
+    return out
+
+
+def hse_fock_apply_vjp(plan: Plan, u_occ, occ, u_tgt, grad_vx, need_occ=True, need_tgt=True, need_omega=True,
+                       stream=None):
+    """(grad_u_occ, grad_u_tgt, grad_omega); entries not requested are None."""
+    lib = load_library()
+    _dev(u_occ, plan, plan.shape(plan.n_occ), plan.dtype, "u_occ")
+    _dev(u_tgt, plan, plan.shape(plan.n_tgt), plan.dtype, "u_tgt")
+    _dev(grad_vx, plan, plan.shape(plan.n_tgt), plan.dtype, "grad_vx")
+    _dev(occ, plan, (plan.nk, plan.n_occ), torch.float64, "occ")
+    g_occ = torch.empty(plan.shape(plan.n_occ), dtype=plan.dtype, device=plan.device) if need_occ else None
+    g_tgt = torch.empty(plan.shape(plan.n_tgt), dtype=plan.dtype, device=plan.device) if need_tgt else None
+    g_om = torch.empty((), dtype=torch.float64, device=plan.device) if need_omega else None
+    _check(lib.hse_fock_apply_vjp(plan.handle, _ptr(u_occ), _ptr(occ), _ptr(u_tgt), _ptr(grad_vx), _ptr(g_occ),
+                                  _ptr(g_tgt), _ptr(g_om), _stream(stream)), "hse_fock_apply_vjp")
+    return g_occ, g_tgt, g_om
+
+
+def hse_status(plan: Plan, stream=None) -> None:
+    _check(load_library().hse_status(plan.handle, _stream(stream)), "hse_status")
