@@ -130,6 +130,30 @@ uint64_t hse_kernel_launches(void);
 
 const char *hse_strerror(int code);
 
+/* Exchange energy for callers that cannot allocate device memory: no counterpart in the
+ * paper; it computes the same E_x as hse_exchange_energy (HSE_C64, cubic grids) without a
+ * plan and without any allocation.
+ *
+ * Who needs it: an application whose device memory belongs to another allocator (a
+ * framework's memory pool, a fixed per-process budget) that it may not grow, or a
+ * latency-critical loop where cudaMalloc/cudaFree would synchronise the device.  Plans
+ * allocate, so those callers cannot use hse_plan_create.
+ *
+ * Scratch: one static __device__ array of HSE_NOALLOC_SCRATCH_BYTES (4 MiB) that every GPU
+ * loading this library holds until the process exits.  It must hold
+ *   align256(24 nk) + align256(4 nk^2) + align256(4 nk^2 N) + align256(8 nk n_occ) bytes
+ * (N = grid points, align256 rounds up to 256); larger problems return HSE_ERR_INVALID_ARG
+ * before any device work.  Example: a 12^3 grid with 8 k-points needs about 0.44 MiB.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  All calls
+ * share the one array and each call overwrites all of it that it reads, but calls that
+ * overlap on the GPU (other streams, other host threads) race on it: serialise them.
+ * p->kpts is read on the host (copied with cudaMemcpyAsync on `stream`); u_occ, occ and
+ * e_x are device pointers as for hse_exchange_energy.  Asynchronous on `stream`. */
+#define HSE_NOALLOC_SCRATCH_BYTES (4u << 20)
+int hse_exchange_energy_noalloc(const hse_problem *p, const void *u_occ, const double *occ,
+                                double *e_x, hse_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

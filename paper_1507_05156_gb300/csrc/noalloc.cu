@@ -1,0 +1,171 @@
+// noalloc.cu - hse_exchange_energy_noalloc: the exchange energy without any allocation.
+//
+// Some callers cannot call cudaMalloc: an application whose device memory is owned by
+// another allocator (a framework's memory pool or a fixed per-process budget) that it may
+// not grow, or a latency-critical loop in which cudaMalloc / cudaFree would synchronise the
+// device.  hse_plan_create allocates (kernel tables, reduction scratch), so such callers
+// cannot use the plan-based entry points.  This entry point needs no plan: its scratch is
+// one file-scope __device__ array of fixed size, which every GPU that loads the library
+// holds until the process exits.
+//
+// Scratch layout (bytes from the start of the array, each part 256-byte aligned):
+//   kpts     double [nk][3]         the caller's k-points, copied in
+//   qidx     int    [nk * nk]       row of (k, k'): k * nk + k'
+//   vtab     float  [nk * nk][N]    v(|G + k - k'|) per ordered k-point pair
+//   partial  double [nk * n_occ]    f_i Re<u_i, V_x u_i> per occupied orbital
+// Every part is fully overwritten by each call before it is read, so nothing from a
+// previous call leaks into the result.  Calls that overlap on the GPU (on different
+// streams, or from different host threads) share this one array and race: serialise them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/hse_fock.h"
+#include "launch.cuh"
+
+// The scratch array.  In host code this name is only a host-side stand-in; the device
+// address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HSE_NOALLOC_SCRATCH_BYTES];
+
+namespace hse {
+
+__global__ void reduce_partials(const double* __restrict__ partial, int n, double factor, double* out);
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_ptr[kMaxDevices] = {};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Recip {
+  double b[9];  // rows b1, b2, b3 (bohr^-1)
+};
+
+// Rows of v(|G+q|) for q = kpts[k] - kpts[k'], row k * nk + k', natural [x][y][z] order.
+__global__ void noalloc_kernel_rows(const double* __restrict__ kpts, int nk, int n, const Recip rb, double omega,
+                                    int* __restrict__ qidx, float* __restrict__ vtab) {
+  const size_t N = (size_t)n * n * n;
+  const size_t rows = (size_t)nk * nk;
+  const size_t total = rows * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = idx / N;
+    const int r = (int)(idx - row * N);
+    const int k = (int)(row / nk);
+    const int kp = (int)(row - (size_t)k * nk);
+    if (r == 0) qidx[row] = (int)row;
+    const int i3 = r % n, i2 = (r / n) % n, i1 = r / (n * n);
+    const int m1 = (i1 <= (n - 1) / 2) ? i1 : i1 - n;
+    const int m2 = (i2 <= (n - 1) / 2) ? i2 : i2 - n;
+    const int m3 = (i3 <= (n - 1) / 2) ? i3 : i3 - n;
+    double g2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double g = m1 * rb.b[c] + m2 * rb.b[3 + c] + m3 * rb.b[6 + c] + kpts[3 * k + c] - kpts[3 * kp + c];
+      g2 += g * g;
+    }
+    const double w2 = omega * omega;
+    const double x = g2 / (4.0 * w2);
+    const double lim = kPi / w2;
+    vtab[idx] = (float)((x == 0.0) ? lim : lim * (-expm1(-x) / x));
+  }
+}
+
+}  // namespace
+}  // namespace hse
+
+using namespace hse;
+
+extern "C" int hse_exchange_energy_noalloc(const hse_problem* p, const void* u_occ, const double* occ, double* e_x,
+                                           hse_stream_t stream) {
+  if (!p || !u_occ || !occ || !e_x || !p->kpts) return HSE_ERR_INVALID_ARG;
+  if (p->dtype != HSE_C64) return HSE_ERR_INVALID_ARG;
+  const int n = p->grid[0];
+  if (p->grid[1] != n || p->grid[2] != n || !pairconv_c64_supported(n)) return HSE_ERR_UNSUPPORTED_GRID;
+  if (p->nk < 1 || p->n_occ < 1 || !(p->omega > 0.0) || !std::isfinite(p->omega) || !std::isfinite(p->alpha) ||
+      !std::isfinite(p->spin_degeneracy))
+    return HSE_ERR_INVALID_ARG;
+  if ((((uintptr_t)u_occ) & 15u) != 0) return HSE_ERR_INVALID_ARG;
+  for (int i = 0; i < 3 * p->nk; ++i)
+    if (!std::isfinite(p->kpts[i])) return HSE_ERR_INVALID_ARG;
+  const double* A = p->lattice;
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (!(std::fabs(det) > 1e-12) || !std::isfinite(det)) return HSE_ERR_INVALID_ARG;
+
+  // the problem must fit the fixed scratch array
+  const size_t nk = (size_t)p->nk, N = (size_t)n * n * n;
+  const size_t off_q = align256(nk * 3 * sizeof(double));
+  const size_t off_v = off_q + align256(nk * nk * sizeof(int));
+  const size_t off_p = off_v + align256(nk * nk * N * sizeof(float));
+  const size_t need = off_p + align256(nk * (size_t)p->n_occ * sizeof(double));
+  if (need > (size_t)HSE_NOALLOC_SCRATCH_BYTES || nk * nk > (size_t)1 << 30) return HSE_ERR_INVALID_ARG;
+
+  // device address of the scratch array: looked up once per device, with it current
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HSE_ERR_CUDA;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return HSE_ERR_CUDA;
+      g_noalloc_ptr[dev] = (unsigned char*)ptr;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  double* d_kpts = (double*)base;
+  int* d_qidx = (int*)(base + off_q);
+  float* d_vtab = (float*)(base + off_v);
+  double* d_partial = (double*)(base + off_p);
+
+  // reciprocal rows b_i = 2 pi (A^-1)^T, passed to the kernel by value
+  double inv[9];
+  inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+  inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  Recip rb;
+  for (int i = 0; i < 3; ++i)
+    for (int c = 0; c < 3; ++c) rb.b[3 * i + c] = 2.0 * kPi * inv[3 * c + i];
+
+  cudaStream_t st = (cudaStream_t)stream;
+  // the caller's host k-points into the scratch (stream-ordered before the kernels)
+  if (cudaMemcpyAsync(d_kpts, p->kpts, nk * 3 * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return HSE_ERR_CUDA;
+  const size_t total = nk * nk * N;
+  const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
+  noalloc_kernel_rows<<<blocks, 256, 0, st>>>(d_kpts, p->nk, n, rb, p->omega, d_qidx, d_vtab);
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess) return HSE_ERR_CUDA;
+
+  PairArgs a{};
+  a.own = (const float2*)u_occ;
+  a.part = (const float2*)u_occ;
+  a.partial = d_partial;
+  a.occ = occ;
+  a.vtab = d_vtab;
+  a.qidx = d_qidx;
+  a.nk = p->nk;
+  a.n_own = p->n_occ;
+  a.n_part = p->n_occ;
+  a.n_occ = p->n_occ;
+  a.scale = (float)(-p->alpha / ((double)p->nk * N));
+  const int T = slots_for(n);
+  a.ntiles = (p->n_occ + T - 1) / T;
+  if (launch_pairconv_c64(n, MODE_ENERGY, a, st) != cudaSuccess) return HSE_ERR_CUDA;
+
+  const double dV = std::fabs(det) / (double)N;
+  const double factor = 0.5 * p->spin_degeneracy * dV / p->nk;
+  reduce_partials<<<1, 1024, 0, st>>>(d_partial, p->nk * p->n_occ, factor, e_x);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? HSE_OK : HSE_ERR_CUDA;
+}

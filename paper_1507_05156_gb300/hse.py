@@ -32,7 +32,7 @@ ERRORS = {
 #: every symbol include/hse_fock.h declares
 EXPORTS = ("hse_plan_create", "hse_plan_create_batched", "hse_plan_destroy", "hse_fock_apply",
            "hse_exchange_energy", "hse_fock_apply_vjp", "hse_fock_apply_batched", "hse_status",
-           "hse_grid_supported", "hse_kernel_launches", "hse_strerror")
+           "hse_grid_supported", "hse_kernel_launches", "hse_strerror", "hse_exchange_energy_noalloc")
 
 
 class HseError(RuntimeError):
@@ -82,6 +82,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hse_grid_supported.argtypes = [i, i]
         lib.hse_kernel_launches.argtypes = []
         lib.hse_kernel_launches.restype = ctypes.c_uint64
+        lib.hse_exchange_energy_noalloc.argtypes = [ctypes.POINTER(HseProblem), vp, vp, vp, vp]
+        lib.hse_exchange_energy_noalloc.restype = i
         lib.hse_strerror.argtypes = [i]
         lib.hse_strerror.restype = ctypes.c_char_p
         for name in ("hse_plan_create", "hse_plan_create_batched", "hse_plan_destroy", "hse_fock_apply",
