@@ -15,6 +15,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -24,28 +25,55 @@
 #include "launch.cuh"
 
 namespace hse {
-cudaError_t launch_pairconv_c64_small(int n, int mode, const PairArgs& args, cudaStream_t stream);
-cudaError_t launch_pairconv_c64_mid(int n, int mode, const PairArgs& args, cudaStream_t stream);
-cudaError_t launch_pairconv_c64_20(int mode, const PairArgs& args, cudaStream_t stream);
-cudaError_t launch_pairconv_c64_24(int mode, const PairArgs& args, cudaStream_t stream);
+cudaError_t launch_pairconv_c64_small(int n, int mode, const PairArgs& args, int bps, cudaStream_t stream);
+cudaError_t launch_pairconv_c64_mid(int n, int mode, const PairArgs& args, int bps, cudaStream_t stream);
+cudaError_t launch_pairconv_c64_20(int mode, const PairArgs& args, int bps, cudaStream_t stream);
+cudaError_t launch_pairconv_c64_24(int mode, const PairArgs& args, int bps, cudaStream_t stream);
+int occupancy_pairconv_c64_small(int n, int mode, int bps);
+int occupancy_pairconv_c64_mid(int n, int mode, int bps);
+int occupancy_pairconv_c64_20(int mode, int bps);
+int occupancy_pairconv_c64_24(int mode, int bps);
+
+int pairconv_c64_occupancy(int n, int mode, int bps) {
+  if (n <= 12) return occupancy_pairconv_c64_small(n, mode, bps);
+  if (n <= 18) return occupancy_pairconv_c64_mid(n, mode, bps);
+  if (n == 20) return occupancy_pairconv_c64_20(mode, bps);
+  if (n == 24) return occupancy_pairconv_c64_24(mode, bps);
+  return 0;
+}
+
+// out[i] = sum_s buf[s * count + i], splits in ascending order (deterministic)
+__global__ void reduce_splits(float4* __restrict__ out, const float4* __restrict__ buf, int nsplit, size_t count4) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count4; i += (size_t)gridDim.x * blockDim.x) {
+    float4 a = buf[i];
+    for (int sp = 1; sp < nsplit; ++sp) {
+      const float4 b = buf[(size_t)sp * count4 + i];
+      a.x += b.x;
+      a.y += b.y;
+      a.z += b.z;
+      a.w += b.w;
+    }
+    out[i] = a;
+  }
+}
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 bool pairconv_c64_supported(int n) {
   switch (n) {
-    case 4: case 6: case 8: case 10: case 12: case 15: case 16: case 18: case 20: case 24:
+    case 4: case 6: case 8: case 10: case 12: case 16: case 18: case 20: case 24:
       return true;
     default:
       return false;
   }
 }
 
-cudaError_t launch_pairconv_c64(int n, int mode, const PairArgs& args, cudaStream_t stream) {
-  if (n <= 12) return launch_pairconv_c64_small(n, mode, args, stream);
-  if (n <= 18) return launch_pairconv_c64_mid(n, mode, args, stream);
-  if (n == 20) return launch_pairconv_c64_20(mode, args, stream);
-  if (n == 24) return launch_pairconv_c64_24(mode, args, stream);
+cudaError_t launch_pairconv_c64(int n, int mode, const PairArgs& args, int bps, cudaStream_t stream) {
+  if (n <= 12) return launch_pairconv_c64_small(n, mode, args, bps, stream);
+  if (n <= 18) return launch_pairconv_c64_mid(n, mode, args, bps, stream);
+  if (n == 20) return launch_pairconv_c64_20(mode, args, bps, stream);
+  if (n == 24) return launch_pairconv_c64_24(mode, args, bps, stream);
   return cudaErrorInvalidValue;
 }
 
@@ -151,6 +179,10 @@ struct hse_plan_s {
   double2* work = nullptr;   // [batch][N]
   size_t work_pairs = 0;
   double2* vx64 = nullptr;   // [nk][max(n_occ, n_tgt)][N]
+  int blocks_per_sm = 2;     // occupancy variant of the fused kernel
+  int nsplit[2] = {1, 1};    // k'-loop splits of the fused kernel for owners = targets / occupied
+  float2* split_buf = nullptr;  // [nsplit][nk][n_own][N] partial outputs when nsplit > 1
+  size_t split_buf_elems = 0;
 };
 
 namespace {
@@ -245,6 +277,7 @@ int hse_plan_destroy(hse_plan plan) {
   cudaFree(plan->status);
   cudaFree(plan->work);
   cudaFree(plan->vx64);
+  cudaFree(plan->split_buf);
   cudaSetDevice(prev);
   delete plan;
   return HSE_OK;
@@ -264,6 +297,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   plan->kpts.assign(p->kpts, p->kpts + 3 * p->nk);
   plan->p.kpts = plan->kpts.data();
   cudaGetDevice(&plan->device);
+  if (const char* env = std::getenv("HSE_BLOCKS_PER_SM")) plan->blocks_per_sm = std::atoi(env) >= 2 ? 2 : 1;
   const int n1 = p->grid[0], n2 = p->grid[1], n3 = p->grid[2];
   plan->N = n1 * n2 * n3;
   // b_i = 2 pi (A^-1)^T rows: b_i[c] = 2 pi ainv[c][i]
@@ -317,7 +351,43 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   HSE_TRY(cudaMalloc(&plan->dv64, nq * N * sizeof(double)));
   HSE_TRY(cudaMalloc(&plan->v32, nq * N * sizeof(float)));
   HSE_TRY(cudaMalloc(&plan->dv32, nq * N * sizeof(float)));
-  HSE_TRY(cudaMalloc(&plan->partial, (size_t)nk * nown * sizeof(double)));
+  if (p->dtype == HSE_C64) {
+    // Split the k' loop so that the work items fill the resident CTA slots in nearly whole
+    // waves; the partial outputs are summed by reduce_splits.
+    int sms = 0;
+    HSE_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device));
+    const int occ_blocks = std::max(1, pairconv_c64_occupancy(n1, MODE_APPLY, plan->blocks_per_sm));
+    const long long slots = (long long)sms * occ_blocks;
+    const int owners[2] = {p->n_tgt, p->n_occ};
+    size_t buf = 0;
+    for (int o = 0; o < 2; ++o) {
+      const int T = slots_for(n1);
+      const long long items = (long long)nk * ((owners[o] + T - 1) / T);
+      double best_eff = 0.0;
+      int best = 1;
+      for (int ns = 1; ns <= std::min(8, nk); ++ns) {
+        const long long it = items * ns;
+        const long long waves = (it + slots - 1) / slots;
+        const double eff = (double)it / (double)(waves * slots);
+        if (eff > best_eff + 0.02) {
+          best_eff = eff;
+          best = ns;
+        }
+      }
+      const size_t need = best > 1 ? (size_t)best * nk * owners[o] * N : 0;
+      if (need * sizeof(float2) > ((size_t)4 << 30)) best = 1;  // keep split buffers modest
+      plan->nsplit[o] = best;
+      if (best > 1) buf = std::max(buf, need);
+    }
+    if (buf) {
+      HSE_TRY(cudaMalloc(&plan->split_buf, buf * sizeof(float2)));
+      plan->split_buf_elems = buf;
+    }
+  }
+  {
+    const int nsmax = std::max(plan->nsplit[0], plan->nsplit[1]);
+    HSE_TRY(cudaMalloc(&plan->partial, (size_t)nsmax * nk * nown * sizeof(double)));
+  }
   HSE_TRY(cudaMalloc(&plan->status, sizeof(int)));
   HSE_TRY(cudaMemset(plan->status, 0, sizeof(int)));
   HSE_TRY(cudaMemcpy(plan->qidx, qidx.data(), qidx.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -385,10 +455,34 @@ PairArgs base_args(hse_plan plan) {
 }
 
 int run_pairconv(hse_plan plan, int mode, PairArgs a, int n_own, cudaStream_t st) {
-  const int T = slots_for(plan->p.grid[0]);
+  const int n = plan->p.grid[0];
+  const int T = slots_for(n);
   a.n_own = n_own;
   a.ntiles = (n_own + T - 1) / T;
-  return cuda_fail(launch_pairconv_c64(plan->p.grid[0], mode, a, st));
+  a.nsplit = plan->nsplit[n_own == plan->p.n_tgt ? 0 : 1];
+  const size_t count = (size_t)plan->p.nk * n_own * plan->N;
+  float2* final_out = a.out;
+  if (mode == MODE_ENERGY || mode == MODE_DOT) {
+    a.split_stride = (size_t)plan->p.nk * n_own;  // doubles between the splits' partials
+  } else {
+    a.split_stride = count;
+    if (a.nsplit > 1) a.out = plan->split_buf;
+  }
+  cudaError_t e = launch_pairconv_c64(n, mode, a, plan->blocks_per_sm, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if ((mode == MODE_APPLY || mode == MODE_OCC) && a.nsplit > 1) {
+    const size_t count4 = count / 2;  // N is even: whole float4 pairs
+    const unsigned blocks = (unsigned)std::min<size_t>((count4 + 255) / 256, 152 * 16);
+    reduce_splits<<<blocks, 256, 0, st>>>((float4*)final_out, (const float4*)plan->split_buf, a.nsplit, count4);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  return cuda_fail(e);
+}
+
+// number of partial doubles a reduction over owners of this count must sum
+int partial_count(hse_plan plan, int n_own) {
+  return plan->nsplit[n_own == plan->p.n_tgt ? 0 : 1] * plan->p.nk * n_own;
 }
 
 int reduce(hse_plan plan, int n, double factor, double* out, cudaStream_t st) {
@@ -496,7 +590,7 @@ int hse_exchange_energy(hse_plan plan, const void* u_occ, const double* occ, dou
     rc = cuda_fail(cudaGetLastError());
   }
   if (rc) return rc;
-  return reduce(plan, nown, factor, e_x, st);
+  return reduce(plan, p.dtype == HSE_C64 ? partial_count(plan, p.n_occ) : nown, factor, e_x, st);
 }
 
 int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, const void* u_tgt, const void* grad_vx,
@@ -541,7 +635,7 @@ int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, cons
     a.n_part = p.n_occ;
     rc = run_pairconv(plan, MODE_DOT, a, p.n_tgt, st);
     if (rc) return rc;
-    rc = reduce(plan, p.nk * p.n_tgt, 1.0, grad_omega, st);
+    rc = reduce(plan, partial_count(plan, p.n_tgt), 1.0, grad_omega, st);
     if (rc) return rc;
   }
   if (grad_u_occ) {

@@ -12,46 +12,85 @@ void count_launch(int n = 1);
 
 // Fused complex64 pair-convolution launch for a cubic grid of side n (one TU per size
 // group keeps the build parallel).  Returns a cudaError_t.
-cudaError_t launch_pairconv_c64(int n, int mode, const PairArgs& args, cudaStream_t stream);
+cudaError_t launch_pairconv_c64(int n, int mode, const PairArgs& args, int blocks_per_sm, cudaStream_t stream);
 bool pairconv_c64_supported(int n);
+int pairconv_c64_occupancy(int n, int mode, int blocks_per_sm);
 
 // One staged FP64 1-D transform pass along an axis of length L with element stride inner.
 cudaError_t launch_staged_fft(int L, int dir, double2* work, size_t nbatch, int N, int inner, cudaStream_t stream);
 bool staged_fft_supported(int L);
 
-// Template body used by the per-size translation units.
-template <int n>
-cudaError_t launch_pairconv_c64_n(int mode, const PairArgs& args, cudaStream_t stream) {
-  constexpr size_t smem = pairconv_smem_bytes<n>();
-  constexpr int threads = slots_for(n) * n * n;
-  const dim3 grid((unsigned)((size_t)args.nk * args.ntiles));
-  cudaError_t err = cudaSuccess;
-  switch (mode) {
-#define HSE_PC_CASE(M)                                                                                     \
-  case M: {                                                                                               \
-    static bool attr_done[64] = {};                                                                       \
-    int dev = 0;                                                                                          \
-    cudaGetDevice(&dev);                                                                                  \
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;                                              \
-    if (!attr_done[dev]) {                                                                                \
-      err = cudaFuncSetAttribute(pairconv_c64_kernel<n, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)smem);                                                              \
-      if (err != cudaSuccess) return err;                                                                 \
-      attr_done[dev] = true;                                                                              \
-    }                                                                                                     \
-    pairconv_c64_kernel<n, M><<<grid, threads, smem, stream>>>(args);                                     \
-    break;                                                                                                \
+// Template body used by the per-size translation units.  `blocks_per_sm` selects the
+// occupancy variant (1: registers uncapped; 2: two CTAs per SM where they fit).
+template <int n, int MODE, int MINB>
+cudaError_t pairconv_set_attr() {
+  static bool attr_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr_done[dev]) {
+    cudaError_t err = cudaFuncSetAttribute(pairconv_c64_kernel<n, MODE, MINB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)pairconv_smem_bytes<n>());
+    if (err != cudaSuccess) return err;
+    attr_done[dev] = true;
   }
-    HSE_PC_CASE(MODE_APPLY)
-    HSE_PC_CASE(MODE_ENERGY)
-    HSE_PC_CASE(MODE_DOT)
-    HSE_PC_CASE(MODE_OCC)
-#undef HSE_PC_CASE
-    default:
-      return cudaErrorInvalidValue;
-  }
+  return cudaSuccess;
+}
+
+template <int n, int MODE, int MINB>
+cudaError_t launch_pairconv_variant(const PairArgs& args, cudaStream_t stream) {
+  cudaError_t err = pairconv_set_attr<n, MODE, MINB>();
+  if (err != cudaSuccess) return err;
+  const dim3 grid((unsigned)((size_t)args.nsplit * args.nk * args.ntiles));
+  pairconv_c64_kernel<n, MODE, MINB><<<grid, Geo<n>::THREADS, pairconv_smem_bytes<n>(), stream>>>(args);
   count_launch();
   return cudaGetLastError();
+}
+
+// Resident CTAs per SM of a variant (0 on error).
+template <int n, int MODE, int MINB>
+int pairconv_occupancy_variant() {
+  if (pairconv_set_attr<n, MODE, MINB>() != cudaSuccess) return 0;
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pairconv_c64_kernel<n, MODE, MINB>, Geo<n>::THREADS,
+                                                    pairconv_smem_bytes<n>()) != cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+template <int n, int MODE>
+cudaError_t launch_pairconv_mode(const PairArgs& args, int blocks_per_sm, cudaStream_t stream) {
+  if (blocks_per_sm >= 2 && Geo<n>::MAXB >= 2) return launch_pairconv_variant<n, MODE, Geo<n>::MAXB>(args, stream);
+  return launch_pairconv_variant<n, MODE, 1>(args, stream);
+}
+
+template <int n, int MODE>
+int pairconv_occupancy_mode(int blocks_per_sm) {
+  if (blocks_per_sm >= 2 && Geo<n>::MAXB >= 2) return pairconv_occupancy_variant<n, MODE, Geo<n>::MAXB>();
+  return pairconv_occupancy_variant<n, MODE, 1>();
+}
+
+template <int n>
+cudaError_t launch_pairconv_c64_n(int mode, const PairArgs& args, int blocks_per_sm, cudaStream_t stream) {
+  switch (mode) {
+    case MODE_APPLY: return launch_pairconv_mode<n, MODE_APPLY>(args, blocks_per_sm, stream);
+    case MODE_ENERGY: return launch_pairconv_mode<n, MODE_ENERGY>(args, blocks_per_sm, stream);
+    case MODE_DOT: return launch_pairconv_mode<n, MODE_DOT>(args, blocks_per_sm, stream);
+    case MODE_OCC: return launch_pairconv_mode<n, MODE_OCC>(args, blocks_per_sm, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int n>
+int pairconv_occupancy_n(int mode, int blocks_per_sm) {
+  switch (mode) {
+    case MODE_APPLY: return pairconv_occupancy_mode<n, MODE_APPLY>(blocks_per_sm);
+    case MODE_ENERGY: return pairconv_occupancy_mode<n, MODE_ENERGY>(blocks_per_sm);
+    case MODE_DOT: return pairconv_occupancy_mode<n, MODE_DOT>(blocks_per_sm);
+    case MODE_OCC: return pairconv_occupancy_mode<n, MODE_OCC>(blocks_per_sm);
+    default: return 0;
+  }
 }
 
 }  // namespace hse

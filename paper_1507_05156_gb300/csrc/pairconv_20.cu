@@ -2,7 +2,9 @@
 #include "launch.cuh"
 
 namespace hse {
-cudaError_t launch_pairconv_c64_20(int mode, const PairArgs& args, cudaStream_t stream) {
-  return launch_pairconv_c64_n<20>(mode, args, stream);
+cudaError_t launch_pairconv_c64_20(int mode, const PairArgs& args, int bps, cudaStream_t stream) {
+  return launch_pairconv_c64_n<20>(mode, args, bps, stream);
 }
+
+int occupancy_pairconv_c64_20(int mode, int bps) { return pairconv_occupancy_n<20>(mode, bps); }
 }  // namespace hse

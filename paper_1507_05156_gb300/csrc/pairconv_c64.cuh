@@ -10,41 +10,74 @@
 //   Y: inverse FFT along y
 //   Z: inverse FFT along z, multiply by the partner and accumulate (epilogue)
 //
-// so HBM (in practice L2) traffic per pair is one read of each orbital pencil and the
-// kernel row; the owner's accumulator lives in shared memory for the whole loop and is
-// written once.  Thread t of a slot owns pencil (t / n, t % n) of whichever axis the
-// stage transforms.  Shared-memory layout, per slot, structure-of-arrays float:
-//   grid  G[x*Q + y*P + z]  (P odd, Q = n mod 32: bank-conflict-light pencils)
-//   acc   A[(x*n + y)*P + z]
+// Each thread owns two pencils per stage and transforms them one after the other (so only
+// one pencil is live in registers and two CTAs fit per SM at 20^3); in every stage the
+// lanes of a warp take consecutive pencils.  The shared grid is interleaved complex,
+// G[x*Q + y*P + z], with pitches P, Q chosen by an offline search of the bank mapping of
+// all four transposes.  The owner's accumulator lives in Tensor Memory (one TMEM lane per
+// thread, 2 x 2n columns) for the whole partner loop and is written to HBM once.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "fft_reg.cuh"
+#include "tmem.cuh"
+#include "tmem_gen.cuh"
 
 namespace hse {
 
-__host__ __device__ constexpr int pitch_z(int n) { return (n % 2 == 0) ? n + 1 : n; }
-__host__ __device__ constexpr int pitch_x(int n) {
-  return n * pitch_z(n) + (((n - n * pitch_z(n)) % 32) + 32) % 32;
+// Per grid side: pitches (complex units), Z-stage lane order (zfast_y: lanes run along y,
+// else along x), Z-stage access width in complex values (1: 64 bit, 2: 128 bit), owner
+// orbitals per CTA.
+struct KCfg {
+  int P, Q, zfast_y, zvec, slots;
+};
+
+__host__ __device__ constexpr KCfg kcfg(int n) {
+  return n == 4    ? KCfg{4, 22, 1, 2, 32}
+         : n == 6  ? KCfg{6, 38, 1, 2, 16}
+         : n == 8  ? KCfg{9, 72, 1, 1, 8}
+         : n == 10 ? KCfg{10, 106, 1, 2, 4}
+         : n == 12 ? KCfg{12, 156, 1, 2, 4}
+         : n == 16 ? KCfg{16, 257, 0, 1, 2}
+         : n == 18 ? KCfg{18, 338, 1, 2, 1}
+         : n == 20 ? KCfg{21, 420, 1, 1, 1}
+         : n == 24 ? KCfg{25, 600, 1, 1, 1}
+                   : KCfg{0, 0, 0, 0, 0};
+}
+
+__host__ __device__ constexpr int slots_for(int n) { return kcfg(n).slots; }
+
+__host__ __device__ constexpr int pow2_at_least(int x) {
+  int p = 32;
+  while (p < x) p *= 2;
+  return p;
 }
 
 template <int n>
 struct Geo {
-  static constexpr int P = pitch_z(n);
-  static constexpr int Q = pitch_x(n);
+  static constexpr KCfg C = kcfg(n);
+  static_assert(C.P > 0 && n % 2 == 0, "fused form needs an even grid side from the supported set");
+  static constexpr int P = C.P, Q = C.Q, ZFAST_Y = C.zfast_y, ZVEC = C.zvec, T = C.slots;
+  static constexpr int H = n / 2;
   static constexpr int NN = n * n;
   static constexpr int N = n * n * n;
-  static constexpr int G_FLOATS = Q * n;
-  static constexpr int A_FLOATS = NN * P;
-  static constexpr int SLOT_FLOATS = 2 * G_FLOATS + 2 * A_FLOATS;
+  static constexpr int TS = n * H;                                // threads per owner slot (2 pencils each)
+  static constexpr int THREADS = ((T * TS + 31) / 32) * 32;       // whole warps (TMEM ops are warp-wide)
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int GRID_CPX = n * Q;                          // complex slots of one slot's grid
+  static constexpr int ROW = 2 * n;                               // floats of one pencil's accumulator
+  static constexpr int TAB = 2 * ROW;                             // column of the kernel-row cache
+  static constexpr int COLS_PER_WARP = 2 * ROW + 2 * n;           // 2 accumulators + 2 kernel rows
+  static constexpr int TMEM_COLS = pow2_at_least(((WARPS + 3) / 4) * COLS_PER_WARP);
+  static constexpr size_t SMEM_BYTES = (size_t)T * GRID_CPX * sizeof(float2);
+  static_assert(TMEM_COLS <= 512, "accumulator exceeds tensor memory");
+  // two CTAs per SM are possible when tensor memory and shared memory allow it; the
+  // 2-CTA variant caps registers (per-SMSP register file), the 1-CTA variant does not
+  static constexpr int MAXB = (512 / TMEM_COLS >= 2 && 2 * (SMEM_BYTES + 1024) <= 233472) ? 2 : 1;
+  static_assert(ZVEC == 1 || (P % 2 == 0 && Q % 2 == 0), "128-bit Z accesses need even pitches");
 };
-
-// Owner orbitals per CTA (slots), chosen so a CTA has 400-648 threads and fits smem.
-__host__ __device__ constexpr int slots_for(int n) {
-  return n <= 4 ? 32 : n <= 6 ? 16 : n <= 8 ? 8 : n <= 12 ? 4 : n <= 16 ? 2 : 1;
-}
 
 // What a launch computes.
 enum PairMode : int {
@@ -66,205 +99,325 @@ struct PairArgs {
   int nk, n_own, n_part, n_occ;
   int ntiles;           // ceil(n_own / slots)
   float scale;          // -alpha / (N_k * N): per-pair scale is scale * f
+  int nsplit;           // the k' loop is split into nsplit work items per owner tile
+  size_t split_stride;  // elements between the per-split outputs (out: float2, partial: double)
 };
 
 template <int n>
 __device__ __forceinline__ void load_pencil_global(cpx<float> (&v)[n], const float2* __restrict__ p) {
-  if constexpr (n % 2 == 0) {
-    const float4* p4 = reinterpret_cast<const float4*>(p);
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int e = 0; e < n / 2; ++e) {
+    const float4 w = __ldg(p4 + e);
+    v[2 * e] = {w.x, w.y};
+    v[2 * e + 1] = {w.z, w.w};
+  }
+}
+
+// One pencil of the smem grid: n complex values at base + e * stride.  A stride of 1 with
+// VEC = 2 moves two neighbours per 128-bit access.
+template <int n, int VEC>
+__device__ __forceinline__ void load_s(cpx<float> (&v)[n], const float2* g, int base, int stride) {
+  if constexpr (VEC == 2) {
 #pragma unroll
     for (int e = 0; e < n / 2; ++e) {
-      const float4 w = __ldg(p4 + e);
+      const float4 w = *reinterpret_cast<const float4*>(g + base + 2 * e);
       v[2 * e] = {w.x, w.y};
       v[2 * e + 1] = {w.z, w.w};
     }
   } else {
 #pragma unroll
     for (int e = 0; e < n; ++e) {
-      const float2 w = __ldg(p + e);
+      const float2 w = g[base + e * stride];
       v[e] = {w.x, w.y};
     }
   }
 }
 
-template <int n>
-__device__ __forceinline__ void load_s(cpx<float> (&v)[n], const float* re, const float* im, int base, int stride) {
+template <int n, int VEC>
+__device__ __forceinline__ void store_s(const cpx<float> (&v)[n], float2* g, int base, int stride) {
+  if constexpr (VEC == 2) {
 #pragma unroll
-  for (int e = 0; e < n; ++e) v[e] = {re[base + e * stride], im[base + e * stride]};
-}
-
-template <int n>
-__device__ __forceinline__ void store_s(const cpx<float> (&v)[n], float* re, float* im, int base, int stride) {
+    for (int e = 0; e < n / 2; ++e)
+      *reinterpret_cast<float4*>(g + base + 2 * e) = make_float4(v[2 * e].x, v[2 * e].y, v[2 * e + 1].x, v[2 * e + 1].y);
+  } else {
 #pragma unroll
-  for (int e = 0; e < n; ++e) {
-    re[base + e * stride] = v[e].x;
-    im[base + e * stride] = v[e].y;
+    for (int e = 0; e < n; ++e) g[base + e * stride] = make_float2(v[e].x, v[e].y);
   }
 }
 
-// Stages Z(fwd) .. Z(inv) of one pair on the slot's smem grid.  On entry v holds the
-// pair density of this thread's z-pencil; on exit it holds phi = K_q(rho) * s on the
-// same z-pencil.  All threads of the CTA must call it together (it synchronises).
+// Pencil p (0 <= p < n^2) of each stage; lanes of a warp take consecutive p.
 template <int n>
-__device__ __forceinline__ void pair_chain(cpx<float> (&v)[n], float* gre, float* gim, int a, int b,
-                                           const float* __restrict__ vrow, float s) {
+struct Pencil {
   using G = Geo<n>;
-  fft<n, -1, float>(v);
-  store_s<n>(v, gre, gim, a * G::Q + b * G::P, 1);
-  __syncthreads();
-  // Y: thread owns (x = a, z = b)
-  load_s<n>(v, gre, gim, a * G::Q + b, G::P);
-  fft<n, -1, float>(v);
-  store_s<n>(v, gre, gim, a * G::Q + b, G::P);
-  __syncthreads();
-  // X: thread owns (y = a, z = b); kernel row element (x, y, z) at x*n^2 + a*n + b
-  load_s<n>(v, gre, gim, a * G::P + b, G::Q);
-  fft<n, -1, float>(v);
-#pragma unroll
-  for (int e = 0; e < n; ++e) {
-    const float w = __ldg(vrow + e * G::NN + a * n + b) * s;
-    v[e].x *= w;
-    v[e].y *= w;
+  int zs;      // Z stage: smem base of z-pencil (x, y), stride 1
+  int zg;      // Z stage: global offset (x n + y) n of that pencil
+  int ys;      // Y stage: pencil (x = p / n, z = p % n), stride P
+  int xs;      // X stage: pencil (y = p / n, z = p % n), stride Q
+  int vr;      // X stage: kernel row element (x, y, z) at x n^2 + p
+  __device__ __forceinline__ explicit Pencil(int p) {
+    const int hi = p / n, lo = p - hi * n;
+    const int zx = G::ZFAST_Y ? hi : lo;
+    const int zy = G::ZFAST_Y ? lo : hi;
+    zs = zx * G::Q + zy * G::P;
+    zg = (zx * n + zy) * n;
+    ys = hi * G::Q + lo;
+    xs = hi * G::P + lo;
+    vr = p;
   }
-  fft<n, +1, float>(v);
-  store_s<n>(v, gre, gim, a * G::P + b, G::Q);
-  __syncthreads();
-  // Y inverse
-  load_s<n>(v, gre, gim, a * G::Q + b, G::P);
-  fft<n, +1, float>(v);
-  store_s<n>(v, gre, gim, a * G::Q + b, G::P);
-  __syncthreads();
-  // Z inverse
-  load_s<n>(v, gre, gim, a * G::Q + b * G::P, 1);
-  fft<n, +1, float>(v);
+};
+
+// Stage Y (DIR) for both pencils of the thread: load, FFT, store.
+template <int n, int DIR>
+__device__ __forceinline__ void stage_y(float2* g, int t, bool valid) {
+  using G = Geo<n>;
+#pragma unroll 1
+  for (int ps = 0; ps < 2; ++ps) {
+    const Pencil<n> pc(t + ps * G::TS);
+    cpx<float> v[n];
+    load_s<n, 1>(v, g, pc.ys, G::P);
+    fft<n, DIR, float>(v);
+    if (valid) store_s<n, 1>(v, g, pc.ys, G::P);
+  }
 }
 
-template <int n, int MODE>
-__global__ void __launch_bounds__(slots_for(n) * n * n, 1) pairconv_c64_kernel(const PairArgs args) {
+// Stage X: FFT, multiply by the kernel row (cached in TMEM, already times -alpha/(N_k N))
+// times the occupation f, inverse FFT, for both pencils.  Warp-wide (TMEM loads).
+template <int n>
+__device__ __forceinline__ void stage_x(float2* g, int t, bool valid, uint32_t ttab, float f) {
   using G = Geo<n>;
-  constexpr int T = slots_for(n);
-  extern __shared__ float smem[];
-  const int slot = threadIdx.x / G::NN;
-  const int t = threadIdx.x - slot * G::NN;
-  const int a = t / n;
-  const int b = t - a * n;
-  float* gre = smem + slot * G::SLOT_FLOATS;
-  float* gim = gre + G::G_FLOATS;
-  float* are = gim + G::G_FLOATS;
-  float* aim = are + G::A_FLOATS;
+#pragma unroll 1
+  for (int ps = 0; ps < 2; ++ps) {
+    const Pencil<n> pc(t + ps * G::TS);
+    float tv[n];
+    TmemRow<n>::load(ttab + (uint32_t)(ps * n), tv);
+    cpx<float> v[n];
+    load_s<n, 1>(v, g, pc.xs, G::Q);
+    fft<n, -1, float>(v);
+#pragma unroll
+    for (int e = 0; e < n; ++e) {
+      const float w = tv[e] * f;
+      v[e].x *= w;
+      v[e].y *= w;
+    }
+    fft<n, +1, float>(v);
+    if (valid) store_s<n, 1>(v, g, pc.xs, G::Q);
+  }
+}
 
-  const int k = blockIdx.x / args.ntiles;                         // owner k-point
-  const int band = (blockIdx.x - k * args.ntiles) * T + slot;     // owner band
-  const bool active = band < args.n_own;
+// Kernel row v(|G+q|) * scale of this thread's two X-pencils into the TMEM cache.
+template <int n>
+__device__ __forceinline__ void cache_kernel_row(int t, uint32_t ttab, const float* __restrict__ vrow, float scale) {
+  using G = Geo<n>;
+#pragma unroll 1
+  for (int ps = 0; ps < 2; ++ps) {
+    const int p = t + ps * G::TS;
+    float tv[n];
+#pragma unroll
+    for (int e = 0; e < n; ++e) tv[e] = __ldg(vrow + e * G::NN + p) * scale;
+    TmemRow<n>::store(ttab + (uint32_t)(ps * n), tv);
+  }
+}
+
+// Z forward for both pencils: v = conj(a) * b, FFT along z, store.
+template <int n>
+__device__ __forceinline__ void stage_z_forward(float2* g, int t, bool valid, const float2* __restrict__ a,
+                                                const float2* __restrict__ b) {
+  using G = Geo<n>;
+#pragma unroll 1
+  for (int ps = 0; ps < 2; ++ps) {
+    const Pencil<n> pc(t + ps * G::TS);
+    cpx<float> v[n], w[n];
+    load_pencil_global<n>(w, a + pc.zg);
+    load_pencil_global<n>(v, b + pc.zg);
+#pragma unroll
+    for (int e = 0; e < n; ++e) v[e] = {w[e].x * v[e].x + w[e].y * v[e].y, w[e].x * v[e].y - w[e].y * v[e].x};
+    fft<n, -1, float>(v);
+    if (valid) store_s<n, G::ZVEC>(v, g, pc.zs, 1);
+  }
+}
+
+enum Epi : int {
+  EPI_MUL = 0,      // acc += w * phi
+  EPI_CONJPHI = 1,  // acc += conj(phi) * w
+  EPI_WCONJ = 2,    // acc += w * conj(phi)
+};
+
+// Z inverse for both pencils, then the epilogue into each pencil's TMEM row.  Executed by
+// every thread of the warp (TMEM accesses are warp-wide).
+template <int n, int EPI>
+__device__ __forceinline__ void stage_z_inverse(const float2* g, int t, const float2* __restrict__ wbase,
+                                                uint32_t trow0) {
+  using G = Geo<n>;
+#pragma unroll 1
+  for (int ps = 0; ps < 2; ++ps) {
+    const Pencil<n> pc(t + ps * G::TS);
+    cpx<float> v[n];
+    load_s<n, G::ZVEC>(v, g, pc.zs, 1);
+    fft<n, +1, float>(v);
+    float acc[G::ROW];
+    const uint32_t trow = trow0 + (uint32_t)(ps * G::ROW);
+    TmemRow<G::ROW>::load(trow, acc);
+    cpx<float> w[n];
+    load_pencil_global<n>(w, wbase + pc.zg);
+#pragma unroll
+    for (int e = 0; e < n; ++e) {
+      float& ar = acc[2 * e];
+      float& ai = acc[2 * e + 1];
+      if constexpr (EPI == EPI_MUL) {  // acc += w phi
+        ar = fmaf(w[e].x, v[e].x, fmaf(-w[e].y, v[e].y, ar));
+        ai = fmaf(w[e].x, v[e].y, fmaf(w[e].y, v[e].x, ai));
+      } else if constexpr (EPI == EPI_CONJPHI) {  // acc += conj(phi) w
+        ar = fmaf(v[e].x, w[e].x, fmaf(v[e].y, w[e].y, ar));
+        ai = fmaf(v[e].x, w[e].y, fmaf(-v[e].y, w[e].x, ai));
+      } else {  // acc += w conj(phi)
+        ar = fmaf(w[e].x, v[e].x, fmaf(w[e].y, v[e].y, ar));
+        ai = fmaf(w[e].y, v[e].x, fmaf(-w[e].x, v[e].y, ai));
+      }
+    }
+    TmemRow<G::ROW>::store(trow, acc);
+  }
+}
+
+// One pair chain between the Z stages; all threads of the CTA call it together.
+template <int n>
+__device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32_t ttab, float f) {
+  __syncthreads();
+  stage_y<n, -1>(g, t, valid);
+  __syncthreads();
+  stage_x<n>(g, t, valid, ttab, f);
+  __syncthreads();
+  stage_y<n, +1>(g, t, valid);
+  __syncthreads();
+}
+
+template <int n, int MODE, int MINB>
+__global__ void __launch_bounds__(Geo<n>::THREADS, MINB) pairconv_c64_kernel(const PairArgs args) {
+  using G = Geo<n>;
+  extern __shared__ __align__(16) float4 smem4[];
+  __shared__ uint32_t tmem_base_sh;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const bool valid = tid < G::T * G::TS;
+  const int slot = valid ? tid / G::TS : 0;
+  const int t = valid ? tid - slot * G::TS : 0;
+  float2* g = reinterpret_cast<float2*>(smem4) + slot * G::GRID_CPX;
+
+  // tensor memory for the accumulators: warp w uses lanes 32 (w % 4) .. +31, columns from
+  // (w / 4) * COLS_PER_WARP; the thread's pencil pass ps is the row at + ps * ROW.
+  if (warp == 0) {
+    tmem_alloc(&tmem_base_sh, G::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tbase = tmem_base_sh;
+  const uint32_t trow0 = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * G::COLS_PER_WARP);
+  const uint32_t ttab = trow0 + (uint32_t)G::TAB;
+
+  // work item: (split, k, tile); split s covers k' in [s nk / nsplit, (s+1) nk / nsplit)
+  const int per_split = args.nk * args.ntiles;
+  const int split = blockIdx.x / per_split;
+  const int rem = blockIdx.x - split * per_split;
+  const int k = rem / args.ntiles;
+  const int band = (rem - k * args.ntiles) * G::T + slot;
+  const int kp_begin = (int)(((long long)split * args.nk) / args.nsplit);
+  const int kp_end = (int)(((long long)(split + 1) * args.nk) / args.nsplit);
+  const bool active = valid && band < args.n_own;
   const int bandc = active ? band : 0;
-  const size_t pencil = (size_t)t * n;                            // z-pencil offset in a grid
-  const float2* own = args.own + ((size_t)k * args.n_own + bandc) * G::N + pencil;
+  const float2* own = args.own + ((size_t)k * args.n_own + bandc) * G::N;
 
-  const int abase = t * G::P;
+  {
+    float z[G::ROW];
 #pragma unroll
-  for (int e = 0; e < n; ++e) {
-    are[abase + e] = 0.f;
-    aim[abase + e] = 0.f;
+    for (int e = 0; e < G::ROW; ++e) z[e] = 0.f;
+    TmemRow<G::ROW>::store(trow0, z);
+    TmemRow<G::ROW>::store(trow0 + G::ROW, z);
   }
 
-  for (int kp = 0; kp < args.nk; ++kp) {
-    // q = k_i - k_j: APPLY-like modes own i (at k), partners j at kp; OCC owns j (at k)
+  for (int kp = kp_begin; kp < kp_end; ++kp) {
+    // q = k_i - k_j: APPLY-like modes own i (at k) and pair with j at kp; OCC owns j (at k)
     const int qrow = (MODE == MODE_OCC) ? args.qidx[kp * args.nk + k] : args.qidx[k * args.nk + kp];
-    const float* vrow = args.vtab + (size_t)qrow * G::N;
+    cache_kernel_row<n>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
     for (int j = 0; j < args.n_part; ++j) {
-      const size_t poff = ((size_t)kp * args.n_part + j) * G::N + pencil;
+      const float2* part = args.part + ((size_t)kp * args.n_part + j) * G::N;
       if constexpr (MODE != MODE_OCC) {
         const float f = (float)args.occ[kp * args.n_occ + j];
         if (f == 0.f) continue;  // uniform over the CTA
-        cpx<float> v[n], w[n];
-        load_pencil_global<n>(v, own);
-        load_pencil_global<n>(w, args.part + poff);
-#pragma unroll
-        for (int e = 0; e < n; ++e)  // conj(u_j) u_i
-          v[e] = {w[e].x * v[e].x + w[e].y * v[e].y, w[e].x * v[e].y - w[e].y * v[e].x};
-        pair_chain<n>(v, gre, gim, a, b, vrow, args.scale * f);
-        load_pencil_global<n>(w, args.part + poff);
-#pragma unroll
-        for (int e = 0; e < n; ++e) {  // acc += u_j phi
-          are[abase + e] += w[e].x * v[e].x - w[e].y * v[e].y;
-          aim[abase + e] += w[e].x * v[e].y + w[e].y * v[e].x;
-        }
+        stage_z_forward<n>(g, t, valid, part, own);          // conj(u_j) u_i
+        pair_middle<n>(g, t, valid, ttab, f);
+        stage_z_inverse<n, EPI_MUL>(g, t, part, trow0);      // acc += u_j phi
       } else {
         const float f = (float)args.occ[k * args.n_occ + bandc];
-        // chain 1: rho = conj(u_j) u_i -> phi; acc += conj(phi) ybar_i
-        {
-          cpx<float> v[n], w[n];
-          load_pencil_global<n>(v, args.part + poff);
-          load_pencil_global<n>(w, own);
-#pragma unroll
-          for (int e = 0; e < n; ++e)
-            v[e] = {w[e].x * v[e].x + w[e].y * v[e].y, w[e].x * v[e].y - w[e].y * v[e].x};
-          pair_chain<n>(v, gre, gim, a, b, vrow, args.scale * f);
-          load_pencil_global<n>(w, args.part2 + poff);
-#pragma unroll
-          for (int e = 0; e < n; ++e) {
-            are[abase + e] += v[e].x * w[e].x + v[e].y * w[e].y;
-            aim[abase + e] += v[e].x * w[e].y - v[e].y * w[e].x;
-          }
-        }
-        // chain 2: sigma = conj(u_j) ybar_i -> psibar; acc += u_i conj(psibar)
-        {
-          cpx<float> v[n], w[n];
-          load_pencil_global<n>(v, args.part2 + poff);
-          load_pencil_global<n>(w, own);
-#pragma unroll
-          for (int e = 0; e < n; ++e)
-            v[e] = {w[e].x * v[e].x + w[e].y * v[e].y, w[e].x * v[e].y - w[e].y * v[e].x};
-          pair_chain<n>(v, gre, gim, a, b, vrow, args.scale * f);
-          load_pencil_global<n>(w, args.part + poff);
-#pragma unroll
-          for (int e = 0; e < n; ++e) {
-            are[abase + e] += w[e].x * v[e].x + w[e].y * v[e].y;
-            aim[abase + e] += w[e].y * v[e].x - w[e].x * v[e].y;
-          }
-        }
+        const float2* ybar = args.part2 + ((size_t)kp * args.n_part + j) * G::N;
+        // chain 1: rho = conj(u_j) u_i -> phi;  acc += conj(phi) ybar_i
+        stage_z_forward<n>(g, t, valid, own, part);
+        pair_middle<n>(g, t, valid, ttab, f);
+        stage_z_inverse<n, EPI_CONJPHI>(g, t, ybar, trow0);
+        // chain 2: sigma = conj(u_j) ybar_i -> psibar;  acc += u_i conj(psibar)
+        stage_z_forward<n>(g, t, valid, own, ybar);
+        pair_middle<n>(g, t, valid, ttab, f);
+        stage_z_inverse<n, EPI_WCONJ>(g, t, part, trow0);
       }
     }
   }
 
   if constexpr (MODE == MODE_APPLY || MODE == MODE_OCC) {
-    if (active) {
-      float2* o = args.out + ((size_t)k * args.n_own + band) * G::N + pencil;
-      if constexpr (n % 2 == 0) {
-        float4* o4 = reinterpret_cast<float4*>(o);
+    float2* obase = args.out + split * args.split_stride + ((size_t)k * args.n_own + bandc) * G::N;
+#pragma unroll 1
+    for (int ps = 0; ps < 2; ++ps) {
+      const Pencil<n> pc(t + ps * G::TS);
+      float acc[G::ROW];
+      TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
+      if (active) {
+        float4* o = reinterpret_cast<float4*>(obase + pc.zg);
 #pragma unroll
-        for (int e = 0; e < n / 2; ++e)
-          o4[e] = make_float4(are[abase + 2 * e], aim[abase + 2 * e], are[abase + 2 * e + 1], aim[abase + 2 * e + 1]);
-      } else {
-#pragma unroll
-        for (int e = 0; e < n; ++e) o[e] = make_float2(are[abase + e], aim[abase + e]);
+        for (int e = 0; e < n / 2; ++e) o[e] = make_float4(acc[4 * e], acc[4 * e + 1], acc[4 * e + 2], acc[4 * e + 3]);
       }
     }
   } else {
     // FP64 dot of the accumulator with u_i (ENERGY) or ybar_i (DOT), per owner.
-    const float2* lhs = (MODE == MODE_ENERGY) ? own
-                        : args.part2 + ((size_t)k * args.n_own + bandc) * G::N + pencil;
-    cpx<float> w[n];
-    load_pencil_global<n>(w, lhs);
+    const float2* lhs = (MODE == MODE_ENERGY) ? own : args.part2 + ((size_t)k * args.n_own + bandc) * G::N;
     double d = 0.0;
+#pragma unroll 1
+    for (int ps = 0; ps < 2; ++ps) {
+      const Pencil<n> pc(t + ps * G::TS);
+      float acc[G::ROW];
+      TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
+      cpx<float> w[n];
+      load_pencil_global<n>(w, lhs + pc.zg);
 #pragma unroll
-    for (int e = 0; e < n; ++e) d += (double)w[e].x * (double)are[abase + e] + (double)w[e].y * (double)aim[abase + e];
-    __syncthreads();  // the grid buffer is free now; reuse it for the per-thread partials
-    double* red = reinterpret_cast<double*>(gre);
-    red[t] = d;
+      for (int e = 0; e < n; ++e) d += (double)w[e].x * (double)acc[2 * e] + (double)w[e].y * (double)acc[2 * e + 1];
+    }
+    __syncthreads();  // the grid buffers are free now; reuse them for the per-thread partials
+    double* red = reinterpret_cast<double*>(smem4);
+    red[tid] = valid ? d : 0.0;
     __syncthreads();
-    if (t == 0 && active) {
+    if (valid && t == 0 && active) {
       double sum = 0.0;
-      for (int e = 0; e < G::NN; ++e) sum += red[e];
+      for (int e = 0; e < G::TS; ++e) sum += red[slot * G::TS + e];
       if (MODE == MODE_ENERGY) sum *= args.occ[k * args.n_occ + band];
-      args.partial[(size_t)k * args.n_own + band] = sum;
+      args.partial[split * args.split_stride + (size_t)k * args.n_own + band] = sum;
     }
   }
+
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(tbase, G::TMEM_COLS);
 }
 
+// Dynamic shared memory requested per CTA: the grids, raised if needed so that no more CTAs
+// become resident on an SM than its 512 TMEM columns can serve (tcgen05.alloc then never
+// has to wait for another CTA).
 template <int n>
 constexpr size_t pairconv_smem_bytes() {
-  return (size_t)slots_for(n) * Geo<n>::SLOT_FLOATS * sizeof(float);
+  constexpr size_t sm_smem = 233472;  // 228 KB of shared memory per SM
+  constexpr int max_res = 512 / Geo<n>::TMEM_COLS;
+  constexpr size_t floor_bytes = sm_smem / (size_t)(max_res + 1) + 2048;
+  return Geo<n>::SMEM_BYTES > floor_bytes ? Geo<n>::SMEM_BYTES : floor_bytes;
 }
 
 }  // namespace hse

@@ -35,12 +35,14 @@ def test_every_declared_symbol_is_exported(lib):
 def test_strerror_and_grid_support(lib):
     assert lib.hse_strerror(0) == b"success"
     assert b"overlaps" in lib.hse_strerror(-3)
-    for n in (4, 6, 8, 10, 12, 15, 16, 18, 20, 24):
+    for n in (4, 6, 8, 10, 12, 16, 18, 20, 24):
         assert lib.hse_grid_supported(n, hse.HSE_C64) == 1
     assert lib.hse_grid_supported(7, hse.HSE_C64) == 0
     assert lib.hse_grid_supported(7, hse.HSE_C128) == 0
     assert lib.hse_grid_supported(27, hse.HSE_C128) == 1
     assert lib.hse_grid_supported(27, hse.HSE_C64) == 0
+    assert lib.hse_grid_supported(15, hse.HSE_C64) == 0  # the fused form needs an even side
+    assert lib.hse_grid_supported(15, hse.HSE_C128) == 1
 
 
 def _prob(**kw):

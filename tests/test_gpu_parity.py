@@ -63,7 +63,7 @@ def run_apply(lattice, kpts, u_occ, occ, u_tgt, grid, omega, alpha, dtype):
 # (grid side, nk, n_occ, n_tgt): tails chosen so that n_tgt is not a multiple of the
 # CTA's owner slots (4^3: 32, 6^3: 16, 8^3: 8, 10^3/12^3: 4, 16^3: 2)
 CUBIC_CASES = [(4, 2, 3, 33), (6, 2, 2, 17), (8, 3, 3, 9), (10, 2, 2, 5), (12, 2, 3, 5),
-               (15, 2, 2, 3), (16, 2, 2, 3), (18, 2, 2, 2), (20, 2, 2, 2), (24, 2, 2, 2)]
+               (16, 2, 2, 3), (18, 2, 2, 2), (20, 2, 2, 2), (24, 2, 2, 2)]
 
 
 @pytest.mark.parametrize("n,nk,n_occ,n_tgt", CUBIC_CASES)
