@@ -8,6 +8,8 @@
 //   * reduction scratch: one double per owner orbital;
 //   * for complex128 problems, the staged work batch and an FP64 result buffer;
 //   * a status word that kernels set on a failed device-side check.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,6 +60,28 @@ __global__ void reduce_splits(float4* __restrict__ out, const float4* __restrict
 }
 
 static std::atomic<uint64_t> g_launches{0};
+
+// The driver's tensor-map encoder, obtained through the runtime (no link against libcuda).
+cudaError_t make_partner_tmap(CUtensorMap* map, const void* base, int n, long long rows, int sp, int box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return cudaErrorNotSupported;
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  if (rows <= 0 || rows > ((long long)1 << 32)) return cudaErrorInvalidValue;
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * n), (cuuint64_t)rows};  // floats of a pencil, pencils
+  const cuuint64_t strides[1] = {(cuuint64_t)(2 * n) * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * sp), (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 bool pairconv_c64_supported(int n) {
@@ -179,7 +203,7 @@ struct hse_plan_s {
   double2* work = nullptr;   // [batch][N]
   size_t work_pairs = 0;
   double2* vx64 = nullptr;   // [nk][max(n_occ, n_tgt)][N]
-  int blocks_per_sm = 2;     // occupancy variant of the fused kernel
+  int blocks_per_sm = 0;     // fused-kernel variant: 0 staged partner (TMA), 1/2 pencil loads
   int nsplit[2] = {1, 1};    // k'-loop splits of the fused kernel for owners = targets / occupied
   float2* split_buf = nullptr;  // [nsplit][nk][n_own][N] partial outputs when nsplit > 1
   size_t split_buf_elems = 0;
@@ -297,7 +321,10 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   plan->kpts.assign(p->kpts, p->kpts + 3 * p->nk);
   plan->p.kpts = plan->kpts.data();
   cudaGetDevice(&plan->device);
-  if (const char* env = std::getenv("HSE_BLOCKS_PER_SM")) plan->blocks_per_sm = std::atoi(env) >= 2 ? 2 : 1;
+  if (const char* env = std::getenv("HSE_BLOCKS_PER_SM")) {
+    const int v = std::atoi(env);
+    plan->blocks_per_sm = v <= 0 ? 0 : (v >= 2 ? 2 : 1);
+  }
   const int n1 = p->grid[0], n2 = p->grid[1], n3 = p->grid[2];
   plan->N = n1 * n2 * n3;
   // b_i = 2 pi (A^-1)^T rows: b_i[c] = 2 pi ainv[c][i]
@@ -451,6 +478,7 @@ PairArgs base_args(hse_plan plan) {
   a.nk = plan->p.nk;
   a.n_occ = plan->p.n_occ;
   a.scale = (float)(-plan->p.alpha / ((double)plan->p.nk * plan->N));
+  a.status = plan->status;
   return a;
 }
 

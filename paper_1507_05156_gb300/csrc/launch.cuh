@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "pairconv_c64.cuh"
+#include "pairconv_tma.cuh"
 #include "staged_f64.cuh"
 
 namespace hse {
@@ -59,14 +60,50 @@ int pairconv_occupancy_variant() {
   return blocks;
 }
 
+// Staged-partner kernel (pairconv_tma.cuh): one CTA per SM.
+// Encodes the tensor map of a partner array for the staged-partner kernel of side n.
+cudaError_t make_partner_tmap(CUtensorMap* map, const void* base, int n, long long rows, int sp, int box_rows);
+
+template <int n, int MODE>
+cudaError_t launch_pairconv_tma(const PairArgs& args, cudaStream_t stream) {
+  using S = GeoS<n>;
+  static bool attr_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr_done[dev]) {
+    cudaError_t err = cudaFuncSetAttribute(pairconv_tma_kernel<n, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)S::SMEM_REQUEST);
+    if (err != cudaSuccess) return err;
+    attr_done[dev] = true;
+  }
+  CUtensorMap tmap;
+  cudaError_t err = make_partner_tmap(&tmap, args.part, n, (long long)args.nk * args.n_part * Geo<n>::NN, S::SP, S::BR);
+  if (err != cudaSuccess) return err;
+  const dim3 grid((unsigned)((size_t)args.nsplit * args.nk * args.ntiles));
+  pairconv_tma_kernel<n, MODE><<<grid, Geo<n>::THREADS, S::SMEM_REQUEST, stream>>>(args, tmap);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// blocks_per_sm: 0 selects the staged-partner kernel where it exists for (n, mode); 1 or 2
+// select the pencil-load kernel with that occupancy.
 template <int n, int MODE>
 cudaError_t launch_pairconv_mode(const PairArgs& args, int blocks_per_sm, cudaStream_t stream) {
+  if constexpr (GeoS<n>::FITS && (MODE == MODE_APPLY || MODE == MODE_ENERGY || MODE == MODE_DOT)) {
+    if (blocks_per_sm == 0) return launch_pairconv_tma<n, MODE>(args, stream);
+  }
+  if (blocks_per_sm == 0) blocks_per_sm = 2;
   if (blocks_per_sm >= 2 && Geo<n>::MAXB >= 2) return launch_pairconv_variant<n, MODE, Geo<n>::MAXB>(args, stream);
   return launch_pairconv_variant<n, MODE, 1>(args, stream);
 }
 
 template <int n, int MODE>
 int pairconv_occupancy_mode(int blocks_per_sm) {
+  if constexpr (GeoS<n>::FITS && (MODE == MODE_APPLY || MODE == MODE_ENERGY || MODE == MODE_DOT)) {
+    if (blocks_per_sm == 0) return 1;
+  }
+  if (blocks_per_sm == 0) blocks_per_sm = 2;
   if (blocks_per_sm >= 2 && Geo<n>::MAXB >= 2) return pairconv_occupancy_variant<n, MODE, Geo<n>::MAXB>();
   return pairconv_occupancy_variant<n, MODE, 1>();
 }

@@ -163,7 +163,8 @@ extern "C" int hse_exchange_energy_noalloc(const hse_problem* p, const void* u_o
   a.ntiles = (p->n_occ + T - 1) / T;
   a.nsplit = 1;
   a.split_stride = 0;
-  if (launch_pairconv_c64(n, MODE_ENERGY, a, 2, st) != cudaSuccess) return HSE_ERR_CUDA;
+  a.status = nullptr;
+  if (launch_pairconv_c64(n, MODE_ENERGY, a, 0, st) != cudaSuccess) return HSE_ERR_CUDA;
 
   const double dV = std::fabs(det) / (double)N;
   const double factor = 0.5 * p->spin_degeneracy * dV / p->nk;

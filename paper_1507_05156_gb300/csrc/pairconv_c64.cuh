@@ -101,6 +101,7 @@ struct PairArgs {
   float scale;          // -alpha / (N_k * N): per-pair scale is scale * f
   int nsplit;           // the k' loop is split into nsplit work items per owner tile
   size_t split_stride;  // elements between the per-split outputs (out: float2, partial: double)
+  int* status;          // device status word for failed device-side waits (may be null)
 };
 
 template <int n>
