@@ -390,9 +390,14 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
     for (int o = 0; o < 2; ++o) {
       const int T = slots_for(n1);
       const long long items = (long long)nk * ((owners[o] + T - 1) / T);
+      // the staged-partner kernel caches an item's occupations: at most kOccCache partners
+      const int ns_cap = std::min(8, nk);
+      const int ns_min = (plan->blocks_per_sm == 0 && o == 0)
+                             ? std::min(ns_cap, std::max(1, (int)(((long long)nk * p->n_occ + kOccCache - 1) / kOccCache)))
+                             : 1;
       double best_eff = 0.0;
-      int best = 1;
-      for (int ns = 1; ns <= std::min(8, nk); ++ns) {
+      int best = ns_min;
+      for (int ns = ns_min; ns <= ns_cap; ++ns) {
         const long long it = items * ns;
         const long long waves = (it + slots - 1) / slots;
         const double eff = (double)it / (double)(waves * slots);

@@ -100,13 +100,20 @@ __device__ __forceinline__ void stage_z_inverse_staged(const float2* g, int t, c
   }
 }
 
-// Next partner index q' >= q (q = (kp - kp_begin) * n_part + j) with nonzero occupation.
-__device__ __forceinline__ int next_partner(const PairArgs& a, int kp_begin, int q, int npairs) {
-  while (q < npairs) {
-    const int kp = kp_begin + q / a.n_part, j = q - (q / a.n_part) * a.n_part;
-    if (a.occ[kp * a.n_occ + j] != 0.0) break;
-    ++q;
-  }
+// Occupations of one work item's partners, cached in shared memory when they fit.
+constexpr int kOccCache = 1024;
+
+// Occupation of partner q of the item (q = (kp - kp_begin) * n_part + j): from the shared
+// cache, or from global memory past its end.
+__device__ __forceinline__ float item_occ(const float* occ_sh, const PairArgs& a, int kp_begin, int q) {
+  if (q < kOccCache) return occ_sh[q];
+  const int kp = kp_begin + q / a.n_part, j = q - (q / a.n_part) * a.n_part;
+  return (float)a.occ[kp * a.n_occ + j];
+}
+
+// Next partner index q' >= q with nonzero occupation.
+__device__ __forceinline__ int next_partner(const float* occ_sh, const PairArgs& a, int kp_begin, int q, int npairs) {
+  while (q < npairs && item_occ(occ_sh, a, kp_begin, q) == 0.f) ++q;
   return q;
 }
 
@@ -121,6 +128,7 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
   __shared__ uint32_t tmem_base_sh;
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ int abort_sh;
+  __shared__ float occ_sh[kOccCache];
 
   const int tid = threadIdx.x;
   // TMA destinations must be 128-byte aligned: align the dynamic shared memory base (128 bytes
@@ -183,7 +191,13 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
     __syncwarp();
   };
 
-  int q = next_partner(args, kp_begin, 0, npairs);
+  // the item's partner occupations, once (work items are sized so that they fit)
+  for (int i = tid; i < npairs && i < kOccCache; i += blockDim.x) {
+    const int kp = kp_begin + i / args.n_part, j = i - (i / args.n_part) * args.n_part;
+    occ_sh[i] = (float)args.occ[kp * args.n_occ + j];
+  }
+  __syncthreads();
+  int q = next_partner(occ_sh, args, kp_begin, 0, npairs);
   if (warp == 0 && q < npairs) fill(q, 0);
 
   // owner orbital into TMEM, accumulators to zero
@@ -208,8 +222,8 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
   int buf = 0;
   int cur_kp = -1;
   while (q < npairs) {
-    const int kp = kp_begin + q / args.n_part, j = q - (q / args.n_part) * args.n_part;
-    const float f = (float)args.occ[kp * args.n_occ + j];
+    const int kp = kp_begin + q / args.n_part;
+    const float f = item_occ(occ_sh, args, kp_begin, q);
     if (kp != cur_kp) {
       const int qrow = args.qidx[k * args.nk + kp];
       cache_kernel_row<n>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
@@ -228,7 +242,7 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
     stage_z_forward_staged<n>(g, t, valid, stg, town);
     __syncthreads();
     // every thread is past its last read of stage[buf ^ 1]: refill it with the next partner
-    const int qn = next_partner(args, kp_begin, q + 1, npairs);
+    const int qn = next_partner(occ_sh, args, kp_begin, q + 1, npairs);
     if (warp == 0 && qn < npairs && !abort_sh) {
       fence_proxy_async_smem();
       fill(qn, buf ^ 1);

@@ -171,3 +171,19 @@ def test_bench_workload_sampled_targets():
     ref = oracle.fock_apply(u, c.occ, u, c.kpts, c.lattice, c.grid, c.omega, c.alpha, targets=targets)
     g = np.stack([got[k, i] for k, i in targets])
     assert rel_err(g, ref) <= 1e-5
+
+
+def test_many_partners_beyond_occupation_cache():
+    """One k-point with 1100 occupied bands: a work item then has more partners than the
+    staged kernel caches in shared memory (1024), exercising its global-memory path; the
+    orbitals need not be orthonormal for the operator."""
+    grid = (4, 4, 4)
+    lattice = inputs.cubic_lattice(inputs.A_SI)
+    kpts = np.array([[0.03, -0.02, 0.01]])
+    u_occ = rounded(inputs.random_orbitals(51, (1, 1100) + grid) * 0.06, torch.complex64)
+    u_tgt = rounded(inputs.random_orbitals(52, (1, 3) + grid) * 0.06, torch.complex64)
+    occ = np.random.default_rng(53).random((1, 1100))
+    occ[0, ::7] = 0.0
+    got = run_apply(lattice, kpts, u_occ, occ, u_tgt, grid, 0.106, 0.25, torch.complex64)
+    ref = oracle.fock_apply(u_occ, occ, u_tgt, kpts, lattice, grid, 0.106, 0.25)
+    assert rel_err(got, ref) <= 1e-5
