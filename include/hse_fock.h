@@ -118,6 +118,15 @@ int hse_fock_apply_vjp(hse_plan plan, const void *u_occ, const double *occ, cons
 int hse_fock_apply_batched(hse_plan plan, const void *const *u_occ, const double *const *occ,
                            const void *const *u_tgt, void *const *vx_out, hse_stream_t stream);
 
+/* Kinetic term of the velocity-gauge Kohn-Sham Hamiltonian (Sec. II A, Eq. "tdks-h": the
+ * (-i grad + e A(t)/c)^2 / 2m term, atomic units with e/c absorbed into A) on the periodic
+ * parts:  out_{b,k}(r) = sum_G 1/2 |G + k + A|^2 u~_{b,k}(G) e^{iG.r}.  Used with V_x by the
+ * Taylor propagator of Sec. II C.
+ *   u, out  device [nk][nbands][N] (the plan's dtype); must not overlap
+ *   A       HOST [3] vector potential (bohr^-1) */
+int hse_kinetic_apply(hse_plan plan, const void *u, int nbands, const double *A, void *out,
+                      hse_stream_t stream);
+
 /* Synchronises the stream, then returns HSE_OK, HSE_ERR_TIMEOUT or HSE_ERR_DEVICE from
  * the plan's device status word (and clears it), or HSE_ERR_CUDA. */
 int hse_status(hse_plan plan, hse_stream_t stream);

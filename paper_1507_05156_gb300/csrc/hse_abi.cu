@@ -193,6 +193,7 @@ struct hse_plan_s {
   double b[9] = {};
   int* qidx = nullptr;       // device [nk][nk]
   double* qvec = nullptr;    // device [nq][3]
+  double* dkpts = nullptr;   // device [nk][3]
   double* v64 = nullptr;     // device [nq][N]
   double* dv64 = nullptr;
   float* v32 = nullptr;
@@ -293,6 +294,7 @@ int hse_plan_destroy(hse_plan plan) {
   cudaSetDevice(plan->device);
   cudaFree(plan->qidx);
   cudaFree(plan->qvec);
+  cudaFree(plan->dkpts);
   cudaFree(plan->v64);
   cudaFree(plan->dv64);
   cudaFree(plan->v32);
@@ -424,13 +426,16 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   HSE_TRY(cudaMemset(plan->status, 0, sizeof(int)));
   HSE_TRY(cudaMemcpy(plan->qidx, qidx.data(), qidx.size() * sizeof(int), cudaMemcpyHostToDevice));
   HSE_TRY(cudaMemcpy(plan->qvec, qvec.data(), qvec.size() * sizeof(double), cudaMemcpyHostToDevice));
+  HSE_TRY(cudaMalloc(&plan->dkpts, (size_t)nk * 3 * sizeof(double)));
+  HSE_TRY(cudaMemcpy(plan->dkpts, plan->kpts.data(), (size_t)nk * 3 * sizeof(double), cudaMemcpyHostToDevice));
   if (p->dtype == HSE_C128) {
     // staged batch: all (i, k', j) of one k in chunks of k' up to ~512 MB
     // the energy path runs the staged form with the occupied set as targets
     const size_t per_kp = (size_t)nown * p->n_occ;
     size_t nkp = std::max<size_t>(1, ((size_t)512 << 20) / (per_kp * N * sizeof(double2)));
     nkp = std::min<size_t>(nkp, (size_t)nk);
-    plan->work_pairs = nkp * per_kp;
+    // at least two occupied x target batches: the VJP w.r.t. u_occ runs two at a time
+    plan->work_pairs = std::max(nkp * per_kp, 2 * (size_t)p->n_occ * p->n_tgt);
     HSE_TRY(cudaMalloc(&plan->work, plan->work_pairs * N * sizeof(double2)));
     HSE_TRY(cudaMalloc(&plan->vx64, (size_t)nk * nown * N * sizeof(double2)));
   }
@@ -571,6 +576,72 @@ int staged_apply(hse_plan plan, const double2* u_occ, const double* occ, const d
   return HSE_OK;
 }
 
+// Staged FP64 VJP: grad_u_tgt = V_x ybar; grad_omega = Re <ybar, V_x' u_tgt> (V_x' with
+// d v / d omega rows); grad_u_occ by occupied-owner batches.
+int staged_vjp(hse_plan plan, const double2* u_occ, const double* occ, const double2* u_tgt, const double2* ybar,
+               double2* g_occ, double2* g_tgt, double* g_om, cudaStream_t st) {
+  const hse_problem& p = plan->p;
+  const int N = plan->N;
+  int rc = HSE_OK;
+  if (g_tgt) {
+    rc = staged_apply(plan, u_occ, occ, ybar, p.n_tgt, plan->v64, g_tgt, st);
+    if (rc) return rc;
+  }
+  if (g_om) {
+    rc = staged_apply(plan, u_occ, occ, u_tgt, p.n_tgt, plan->dv64, plan->vx64, st);
+    if (rc) return rc;
+    dot_per_owner_f64<<<p.nk * p.n_tgt, 256, 0, st>>>(ybar, plan->vx64, N, nullptr, plan->partial);
+    count_launch();
+    rc = cuda_fail(cudaGetLastError());
+    if (rc) return rc;
+    rc = reduce(plan, p.nk * p.n_tgt, 1.0, g_om, st);
+    if (rc) return rc;
+  }
+  if (g_occ) {
+    // the work buffer holds two pair batches of work_pairs / 2 each
+    const size_t per_k = (size_t)p.n_occ * p.n_tgt;
+    const size_t half = plan->work_pairs / 2;
+    if (per_k > half) return HSE_ERR_NOMEM;
+    const int nkc_max = (int)std::min<size_t>(half / per_k, (size_t)p.nk);
+    StagedOccArgs a{};
+    a.u_occ = u_occ;
+    a.u_tgt = u_tgt;
+    a.ybar = ybar;
+    a.occ = occ;
+    a.vtab = plan->v64;
+    a.qidx = plan->qidx;
+    a.w1 = plan->work;
+    a.w2 = plan->work + half * N;
+    a.nk = p.nk;
+    a.n_occ = p.n_occ;
+    a.n_tgt = p.n_tgt;
+    a.N = N;
+    a.scale = -p.alpha / ((double)p.nk * N);
+    const int inner[3] = {p.grid[1] * p.grid[2], p.grid[2], 1};
+    for (int kp = 0; kp < p.nk; ++kp) {
+      for (int k0 = 0; k0 < p.nk; k0 += nkc_max) {
+        a.kp = kp;
+        a.k0 = k0;
+        a.nkc = std::min(nkc_max, p.nk - k0);
+        const size_t nb = per_k * a.nkc;
+        cudaError_t e = launch_staged_occ_products(a, st);
+        for (int d = 2; d >= 0 && e == cudaSuccess; --d) {
+          e = launch_staged_fft(p.grid[d], -1, a.w1, nb, N, inner[d], st);
+          if (e == cudaSuccess) e = launch_staged_fft(p.grid[d], -1, a.w2, nb, N, inner[d], st);
+        }
+        if (e == cudaSuccess) e = launch_staged_occ_scale(a, st);
+        for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+          e = launch_staged_fft(p.grid[d], +1, a.w1, nb, N, inner[d], st);
+          if (e == cudaSuccess) e = launch_staged_fft(p.grid[d], +1, a.w2, nb, N, inner[d], st);
+        }
+        if (e == cudaSuccess) e = launch_staged_occ_acc(a, g_occ, k0 == 0, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+      }
+    }
+  }
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -645,7 +716,9 @@ int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, cons
   }
   if (overlaps(grad_u_occ, occ_bytes, grad_u_tgt, tgt_bytes)) return HSE_ERR_ALIAS;
   cudaStream_t st = S(stream);
-  if (p.dtype != HSE_C64) return HSE_ERR_INVALID_ARG;  // complex128 VJP: see hse_fock_apply_vjp in the staged form
+  if (p.dtype == HSE_C128)
+    return staged_vjp(plan, (const double2*)u_occ, occ, (const double2*)u_tgt, (const double2*)grad_vx,
+                      (double2*)grad_u_occ, (double2*)grad_u_tgt, grad_omega, st);
   int rc = HSE_OK;
   if (grad_u_tgt) {
     PairArgs a = base_args(plan);
@@ -682,6 +755,32 @@ int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, cons
     rc = run_pairconv(plan, MODE_OCC, a, p.n_occ, st);
   }
   return rc;
+}
+
+int hse_kinetic_apply(hse_plan plan, const void* u, int nbands, const double* A, void* out, hse_stream_t stream) {
+  if (!plan || !u || !out || !A || nbands < 1) return HSE_ERR_INVALID_ARG;
+  for (int c = 0; c < 3; ++c)
+    if (!std::isfinite(A[c])) return HSE_ERR_INVALID_ARG;
+  if (!aligned16(u) || !aligned16(out)) return HSE_ERR_INVALID_ARG;
+  const hse_problem& p = plan->p;
+  const size_t bytes = (size_t)p.nk * nbands * plan->N * elem_bytes(p.dtype);
+  if (overlaps(out, bytes, u, bytes)) return HSE_ERR_ALIAS;
+  KinArgs a{};
+  a.n1 = p.grid[0];
+  a.n2 = p.grid[1];
+  a.n3 = p.grid[2];
+  a.nk = p.nk;
+  a.nbands = nbands;
+  std::memcpy(a.b, plan->b, sizeof(a.b));
+  for (int c = 0; c < 3; ++c) a.A[c] = A[c];
+  a.kpts = plan->dkpts;
+  cudaStream_t st = S(stream);
+  if (p.dtype == HSE_C64) {
+    const int T = slots_for(p.grid[0]);
+    a.ntiles = (nbands + T - 1) / T;
+    return cuda_fail(launch_kinetic_c64(p.grid[0], (const float2*)u, (float2*)out, a, st));
+  }
+  return cuda_fail(launch_kinetic_f64((const double2*)u, (double2*)out, a, st));
 }
 
 int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells) {

@@ -11,10 +11,20 @@ namespace hse {
 
 void count_launch(int n = 1);
 
+// Kinetic term 1/2 |G + k + A|^2 on nk x nbands orbitals (kinetic.cu).
+struct KinArgs {
+  int n1, n2, n3, nk, nbands, ntiles;
+  double b[9];          // reciprocal rows b1, b2, b3
+  double A[3];          // vector potential (bohr^-1)
+  const double* kpts;   // device [nk][3]
+};
+cudaError_t launch_kinetic_f64(const double2* u, double2* out, const KinArgs& a, cudaStream_t stream);
+
 // Fused complex64 pair-convolution launch for a cubic grid of side n (one TU per size
 // group keeps the build parallel).  Returns a cudaError_t.
 cudaError_t launch_pairconv_c64(int n, int mode, const PairArgs& args, int blocks_per_sm, cudaStream_t stream);
 bool pairconv_c64_supported(int n);
+cudaError_t launch_kinetic_c64(int n, const float2* u, float2* out, const KinArgs& a, cudaStream_t stream);
 int pairconv_c64_occupancy(int n, int mode, int blocks_per_sm);
 
 // One staged FP64 1-D transform pass along an axis of length L with element stride inner.

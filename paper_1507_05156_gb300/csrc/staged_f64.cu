@@ -58,6 +58,68 @@ __global__ void staged_mul_acc(const StagedArgs a, double2* __restrict__ out, in
   }
 }
 
+// b = (j, kl, i), i fastest
+__global__ void staged_occ_products(const StagedOccArgs a) {
+  const size_t total = (size_t)a.n_occ * a.nkc * a.n_tgt * a.N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % a.N);
+    const size_t b = idx / a.N;
+    const int i = (int)(b % a.n_tgt);
+    const int kl = (int)((b / a.n_tgt) % a.nkc);
+    const int j = (int)(b / ((size_t)a.n_tgt * a.nkc));
+    const int k = a.k0 + kl;
+    const double2 uj = a.u_occ[((size_t)a.kp * a.n_occ + j) * a.N + r];
+    const double2 ui = a.u_tgt[((size_t)k * a.n_tgt + i) * a.N + r];
+    const double2 yi = a.ybar[((size_t)k * a.n_tgt + i) * a.N + r];
+    a.w1[idx] = make_double2(uj.x * ui.x + uj.y * ui.y, uj.x * ui.y - uj.y * ui.x);
+    a.w2[idx] = make_double2(uj.x * yi.x + uj.y * yi.y, uj.x * yi.y - uj.y * yi.x);
+  }
+}
+
+__global__ void staged_occ_scale(const StagedOccArgs a) {
+  const size_t total = (size_t)a.n_occ * a.nkc * a.n_tgt * a.N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % a.N);
+    const size_t b = idx / a.N;
+    const int kl = (int)((b / a.n_tgt) % a.nkc);
+    const int j = (int)(b / ((size_t)a.n_tgt * a.nkc));
+    const int k = a.k0 + kl;
+    const double s = a.vtab[(size_t)a.qidx[k * a.nk + a.kp] * a.N + r] * a.scale * a.occ[a.kp * a.n_occ + j];
+    double2 w = a.w1[idx];
+    a.w1[idx] = make_double2(w.x * s, w.y * s);
+    w = a.w2[idx];
+    a.w2[idx] = make_double2(w.x * s, w.y * s);
+  }
+}
+
+// g_occ[kp][j][r] (+)= sum_{kl, i} conj(W1) ybar_i + u_i conj(W2)   (fixed order)
+__global__ void staged_occ_acc(const StagedOccArgs a, double2* __restrict__ g_occ, int first) {
+  const size_t total = (size_t)a.n_occ * a.N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % a.N);
+    const int j = (int)(idx / a.N);
+    double sx = 0.0, sy = 0.0;
+    for (int kl = 0; kl < a.nkc; ++kl) {
+      const int k = a.k0 + kl;
+      for (int i = 0; i < a.n_tgt; ++i) {
+        const size_t b = ((size_t)j * a.nkc + kl) * a.n_tgt + i;
+        const double2 p = a.w1[b * a.N + r];
+        const double2 q = a.w2[b * a.N + r];
+        const double2 y = a.ybar[((size_t)k * a.n_tgt + i) * a.N + r];
+        const double2 u = a.u_tgt[((size_t)k * a.n_tgt + i) * a.N + r];
+        sx += p.x * y.x + p.y * y.y + u.x * q.x + u.y * q.y;
+        sy += p.x * y.y - p.y * y.x + u.y * q.x - u.x * q.y;
+      }
+    }
+    double2* o = g_occ + ((size_t)a.kp * a.n_occ + j) * a.N + r;
+    if (first) {
+      *o = make_double2(sx, sy);
+    } else {
+      const double2 c = *o;
+      *o = make_double2(c.x + sx, c.y + sy);
+    }
+  }
+}
 
 namespace {
 unsigned stage_blocks(size_t total) {
@@ -81,6 +143,24 @@ cudaError_t launch_staged_kernel_scale(const StagedArgs& a, cudaStream_t stream)
 
 cudaError_t launch_staged_mul_acc(const StagedArgs& a, double2* out, int first, cudaStream_t stream) {
   staged_mul_acc<<<stage_blocks((size_t)a.n_tgt * a.N), 256, 0, stream>>>(a, out, first);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_staged_occ_products(const StagedOccArgs& a, cudaStream_t stream) {
+  staged_occ_products<<<stage_blocks((size_t)a.n_occ * a.nkc * a.n_tgt * a.N), 256, 0, stream>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_staged_occ_scale(const StagedOccArgs& a, cudaStream_t stream) {
+  staged_occ_scale<<<stage_blocks((size_t)a.n_occ * a.nkc * a.n_tgt * a.N), 256, 0, stream>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_staged_occ_acc(const StagedOccArgs& a, double2* g_occ, int first, cudaStream_t stream) {
+  staged_occ_acc<<<stage_blocks((size_t)a.n_occ * a.N), 256, 0, stream>>>(a, g_occ, first);
   count_launch();
   return cudaGetLastError();
 }

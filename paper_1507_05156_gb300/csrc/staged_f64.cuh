@@ -52,9 +52,31 @@ __global__ void staged_fft_axis(double2* __restrict__ work, size_t nbatch, int N
   }
 }
 
+// VJP w.r.t. the occupied orbitals (owner j at k-point kp, partners (k, i) for k in a chunk):
+//   W1[b] = conj(u_j) u_i,  W2[b] = conj(u_j) ybar_i,  b = (j, kl, i), i fastest;
+//   both transformed, scaled by v(|G+q|) (-alpha f_j / (N_k N)), q = k - kp, transformed back;
+//   g_occ[kp][j] (+)= sum_{kl, i} conj(W1) ybar_i + u_i conj(W2).
+struct StagedOccArgs {
+  const double2* u_occ;  // [nk][n_occ][N]
+  const double2* u_tgt;  // [nk][n_tgt][N]
+  const double2* ybar;   // [nk][n_tgt][N]
+  const double* occ;
+  const double* vtab;
+  const int* qidx;
+  double2* w1;           // [nbatch][N]
+  double2* w2;           // [nbatch][N]
+  int nk, n_occ, n_tgt, N;
+  int kp;                // owner k-point
+  int k0, nkc;           // partner k range
+  double scale;          // -alpha / (N_k N)
+};
+
 // Non-template stage kernels live in staged_f64.cu; these launch them on `stream`.
 cudaError_t launch_staged_pair_product(const StagedArgs& a, cudaStream_t stream);
 cudaError_t launch_staged_kernel_scale(const StagedArgs& a, cudaStream_t stream);
 cudaError_t launch_staged_mul_acc(const StagedArgs& a, double2* out, int first, cudaStream_t stream);
+cudaError_t launch_staged_occ_products(const StagedOccArgs& a, cudaStream_t stream);
+cudaError_t launch_staged_occ_scale(const StagedOccArgs& a, cudaStream_t stream);
+cudaError_t launch_staged_occ_acc(const StagedOccArgs& a, double2* g_occ, int first, cudaStream_t stream);
 
 }  // namespace hse

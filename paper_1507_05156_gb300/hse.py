@@ -32,7 +32,8 @@ ERRORS = {
 #: every symbol include/hse_fock.h declares
 EXPORTS = ("hse_plan_create", "hse_plan_create_batched", "hse_plan_destroy", "hse_fock_apply",
            "hse_exchange_energy", "hse_fock_apply_vjp", "hse_fock_apply_batched", "hse_status",
-           "hse_grid_supported", "hse_kernel_launches", "hse_strerror", "hse_exchange_energy_noalloc")
+           "hse_grid_supported", "hse_kernel_launches", "hse_strerror", "hse_exchange_energy_noalloc",
+           "hse_kinetic_apply")
 
 
 class HseError(RuntimeError):
@@ -84,6 +85,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hse_kernel_launches.restype = ctypes.c_uint64
         lib.hse_exchange_energy_noalloc.argtypes = [ctypes.POINTER(HseProblem), vp, vp, vp, vp]
         lib.hse_exchange_energy_noalloc.restype = i
+        lib.hse_kinetic_apply.argtypes = [vp, vp, i, ctypes.POINTER(ctypes.c_double), vp, vp]
+        lib.hse_kinetic_apply.restype = i
         lib.hse_strerror.argtypes = [i]
         lib.hse_strerror.restype = ctypes.c_char_p
         for name in ("hse_plan_create", "hse_plan_create_batched", "hse_plan_destroy", "hse_fock_apply",
@@ -244,6 +247,22 @@ def hse_fock_apply_vjp(plan: Plan, u_occ, occ, u_tgt, grad_vx, need_occ=True, ne
     _check(lib.hse_fock_apply_vjp(plan.handle, _ptr(u_occ), _ptr(occ), _ptr(u_tgt), _ptr(grad_vx), _ptr(g_occ),
                                   _ptr(g_tgt), _ptr(g_om), _stream(stream)), "hse_fock_apply_vjp")
     return g_occ, g_tgt, g_om
+
+
+def hse_kinetic_apply(plan: Plan, u: torch.Tensor, A, out: Optional[torch.Tensor] = None,
+                      stream=None) -> torch.Tensor:
+    """1/2 |G + k + A|^2 applied to the orbitals u [nk][nbands][grid] (the plan's dtype)."""
+    lib = load_library()
+    if u.dim() != 5 or u.shape[0] != plan.nk or tuple(u.shape[2:]) != plan.grid:
+        raise ValueError(f"u has shape {tuple(u.shape)}, expected ({plan.nk}, nbands) + {plan.grid}")
+    nb = int(u.shape[1])
+    _dev(u, plan, plan.shape(nb), plan.dtype, "u")
+    if out is None:
+        out = torch.empty_like(u)
+    _dev(out, plan, plan.shape(nb), plan.dtype, "out")
+    a = (ctypes.c_double * 3)(*[float(x) for x in np.asarray(A, dtype=np.float64).reshape(3)])
+    _check(lib.hse_kinetic_apply(plan.handle, _ptr(u), nb, a, _ptr(out), _stream(stream)), "hse_kinetic_apply")
+    return out
 
 
 def hse_status(plan: Plan, stream=None) -> None:

@@ -1,0 +1,112 @@
+"""Differentiable Fock-like exchange and a Taylor-series TDKS propagator on the GPU.
+
+* ``FockApply`` is the autograd form of hse_fock_apply: forward runs the fused (complex64) or
+  staged (complex128) kernels, backward runs hse_fock_apply_vjp for the gradients with
+  respect to the occupied orbitals, the target orbitals and omega.  Passing the same tensor
+  as occupied and target set (the self-consistent case) gives the summed gradient.
+* ``KineticApply`` applies 1/2 |G + k + A|^2 (hse_kinetic_apply); the operator is Hermitian,
+  so its vector-Jacobian product is the same operator applied to the cotangent.
+* ``taylor_step`` / ``propagate`` follow Sec. II C of arXiv:1507.05156: psi(t + dt) =
+  sum_{n<=4} (-i dt h)^n / n! psi(t), with h = T[A(t)] + V_x[psi(t)] frozen over the step.
+  ``propagate`` recomputes each step in the backward pass (activation checkpointing), so
+  only one set of orbitals per step is kept.
+
+Every operator application runs in the CUDA library; PyTorch only holds the tensors, forms
+the Taylor sum and drives autograd.
+"""
+from __future__ import annotations
+
+from typing import Sequence
+
+import numpy as np
+import torch
+from torch.utils.checkpoint import checkpoint
+
+from . import hse
+
+
+class Geometry:
+    """Cell, k-points and HSE parameters shared by every call of one problem."""
+
+    def __init__(self, grid, lattice, kpts, alpha=0.25, spin_degeneracy=2.0):
+        self.grid = tuple(int(g) for g in grid)
+        self.lattice = np.asarray(lattice, dtype=np.float64)
+        self.kpts = np.asarray(kpts, dtype=np.float64).reshape(-1, 3)
+        self.alpha = float(alpha)
+        self.spin_degeneracy = float(spin_degeneracy)
+
+    def plan(self, n_occ, n_tgt, omega, dtype):
+        return hse.get_plan(self.grid, self.lattice, self.kpts, n_occ, n_tgt, float(omega), self.alpha,
+                            self.spin_degeneracy, dtype=dtype)
+
+
+class FockApply(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, u_occ, u_tgt, omega, occ, geom: Geometry):
+        plan = geom.plan(u_occ.shape[1], u_tgt.shape[1], float(omega), u_occ.dtype)
+        out = hse.hse_fock_apply(plan, u_occ.contiguous(), occ, u_tgt.contiguous())
+        ctx.save_for_backward(u_occ, u_tgt, occ)
+        ctx.plan = plan
+        ctx.omega_dtype, ctx.omega_device = omega.dtype, omega.device
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        u_occ, u_tgt, occ = ctx.saved_tensors
+        g_occ, g_tgt, g_om = hse.hse_fock_apply_vjp(
+            ctx.plan, u_occ.contiguous(), occ, u_tgt.contiguous(), grad_out.contiguous(),
+            need_occ=ctx.needs_input_grad[0], need_tgt=ctx.needs_input_grad[1], need_omega=ctx.needs_input_grad[2])
+        if g_om is not None:
+            g_om = g_om.to(device=ctx.omega_device, dtype=ctx.omega_dtype)
+        return g_occ, g_tgt, g_om, None, None
+
+
+class KineticApply(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, u, A, geom: Geometry):
+        plan = geom.plan(1, 1, 1.0, u.dtype)  # the kinetic term does not use omega or bands
+        ctx.plan, ctx.A = plan, A
+        return hse.hse_kinetic_apply(plan, u.contiguous(), A)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        return hse.hse_kinetic_apply(ctx.plan, grad_out.contiguous(), ctx.A), None, None
+
+
+def fock_apply(u_occ, occ, u_tgt, omega, geom: Geometry):
+    if not torch.is_tensor(omega):
+        omega = torch.tensor(float(omega), dtype=torch.float64)
+    return FockApply.apply(u_occ, u_tgt, omega, occ, geom)
+
+
+def kinetic_apply(u, A, geom: Geometry):
+    return KineticApply.apply(u, tuple(float(a) for a in A), geom)
+
+
+def hamiltonian_apply(psi_frozen, occ, phi, omega, A, geom: Geometry):
+    """h phi = T[A] phi + V_x[psi_frozen] phi."""
+    return kinetic_apply(phi, A, geom) + fock_apply(psi_frozen, occ, phi, omega, geom)
+
+
+def taylor_step(psi, occ, omega, A, dt, geom: Geometry, order: int = 4):
+    """sum_{n=0}^{order} (-i dt h)^n / n! psi, h frozen at psi (Sec. II C)."""
+    out = psi
+    term = psi
+    for n in range(1, order + 1):
+        term = (-1j * dt / n) * hamiltonian_apply(psi, occ, term, omega, A, geom)
+        out = out + term
+    return out
+
+
+def propagate(psi0, occ, omega, geom: Geometry, dt: float, nsteps: int, efield: Sequence[float],
+              use_checkpoint: bool = True):
+    """nsteps Taylor steps with A(t_s) = -efield t_s, t_s = s dt (field switched on at t = 0)."""
+    E = np.asarray(efield, dtype=np.float64)
+    psi = psi0
+    for s in range(nsteps):
+        A = tuple(float(a) for a in (-E * (s * dt)))
+        if use_checkpoint:
+            psi = checkpoint(taylor_step, psi, occ, omega, A, dt, geom, use_reentrant=False)
+        else:
+            psi = taylor_step(psi, occ, omega, A, dt, geom)
+    return psi

@@ -135,6 +135,21 @@ def test_vjp_complex64():
     assert abs(g_om.item() - r_om) <= 1e-5 * abs(r_om)
 
 
+@pytest.mark.parametrize("grid,nk", [((6, 5, 4), 3), ((8, 8, 8), 1)])
+def test_vjp_complex128(grid, nk):
+    lattice, kpts, u_occ, occ, u_tgt = small_cell(23, grid, nk, 3, 4, lattice=TRICLINIC, occ_pattern=True)
+    ybar = inputs.random_orbitals(24, u_tgt.shape) * np.abs(u_tgt).mean()
+    omega, alpha = 0.2, 0.25
+    d = torch.complex128
+    plan = hse.get_plan(grid, lattice, kpts, 3, 4, omega, alpha, dtype=d)
+    g_occ, g_tgt, g_om = hse.hse_fock_apply_vjp(plan, to_dev(u_occ, d), to_dev(occ, torch.float64),
+                                                to_dev(u_tgt, d), to_dev(ybar, d))
+    r_occ, r_tgt, r_om = oracle.fock_apply_vjp(u_occ, occ, u_tgt, ybar, kpts, lattice, grid, omega, alpha)
+    assert rel_err(g_tgt.cpu().numpy(), r_tgt) <= 1e-10
+    assert rel_err(g_occ.cpu().numpy(), r_occ) <= 1e-10
+    assert abs(g_om.item() - r_om) <= 1e-10 * abs(r_om)
+
+
 def test_deterministic_and_f_zero_skips():
     grid = (12, 12, 12)
     lattice, kpts, u_occ, occ, u_tgt = small_cell(31, grid, 2, 3, 5, occ_pattern=True)
@@ -187,3 +202,33 @@ def test_many_partners_beyond_occupation_cache():
     got = run_apply(lattice, kpts, u_occ, occ, u_tgt, grid, 0.106, 0.25, torch.complex64)
     ref = oracle.fock_apply(u_occ, occ, u_tgt, kpts, lattice, grid, 0.106, 0.25)
     assert rel_err(got, ref) <= 1e-5
+
+
+def test_workload_24cube_k8_sampled_and_energy_consistency():
+    """24^3 grid, 8x8x8 k-mesh (512 k), 16 occupied + 16 empty targets: 134,217,728 pair
+    convolutions in one apply.  Two sampled targets (an occupied and an empty band) are
+    checked element by element against the oracle; the FP64 exchange-energy reduction is
+    checked against an FP64 dot of the full complex64 output computed on the host."""
+    c = inputs.workload(2)
+    d = torch.complex64
+    u_tgt = torch.from_numpy(c.u_tgt.astype(np.complex64)).cuda()
+    u_occ = u_tgt[:, :c.n_occ].contiguous()
+    occ = torch.from_numpy(c.occ).cuda()
+    plan = hse.get_plan(c.grid, c.lattice, c.kpts, c.n_occ, c.n_tgt, c.omega, c.alpha, dtype=d)
+    out = hse.hse_fock_apply(plan, u_occ, occ, u_tgt)
+    hse.hse_status(plan)
+    targets = [(137, 5), (402, 23)]
+    uo = c.u_occ.astype(np.complex64).astype(np.complex128)
+    ut = c.u_tgt.astype(np.complex64).astype(np.complex128)
+    ref = oracle.fock_apply(uo, c.occ, ut, c.kpts, c.lattice, c.grid, c.omega, c.alpha, targets=targets)
+    got = np.stack([out[k, i].cpu().numpy() for k, i in targets])
+    assert rel_err(got, ref) <= 1e-5
+    # E_x from the fused energy epilogue vs an FP64 dot of the apply output (occupied block)
+    plan_e = hse.get_plan(c.grid, c.lattice, c.kpts, c.n_occ, c.n_occ, c.omega, c.alpha, dtype=d)
+    e = hse.hse_exchange_energy(plan_e, u_occ, occ).item()
+    vx = out[:, :c.n_occ].to(torch.complex128)
+    dV = abs(np.linalg.det(c.lattice)) / c.npts
+    dots = (torch.conj(u_occ.to(torch.complex128)) * vx).real.sum(dim=(2, 3, 4))
+    e_ref = 0.5 * 2.0 * dV / c.nk * float((occ * dots).sum())
+    assert e < 0
+    assert abs(e - e_ref) <= 1e-6 * abs(e_ref)
