@@ -44,6 +44,28 @@ int pairconv_c64_occupancy(int n, int mode, int bps) {
   return 0;
 }
 
+// For every cell with a k' split: final_out = sum of its split partials (ascending order).
+__global__ void reduce_splits_batched(const BatchCell* __restrict__ cells, int ncells) {
+  for (int c = 0; c < ncells; ++c) {
+    const BatchCell& bc = cells[c];
+    if (bc.pa.nsplit <= 1) continue;
+    const size_t count4 = bc.pa.split_stride / 2;
+    const float4* buf = reinterpret_cast<const float4*>(bc.pa.out);
+    float4* out = reinterpret_cast<float4*>(bc.final_out);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count4; i += (size_t)gridDim.x * blockDim.x) {
+      float4 a = buf[i];
+      for (int sp = 1; sp < bc.pa.nsplit; ++sp) {
+        const float4 b = buf[(size_t)sp * count4 + i];
+        a.x += b.x;
+        a.y += b.y;
+        a.z += b.z;
+        a.w += b.w;
+      }
+      out[i] = a;
+    }
+  }
+}
+
 // out[i] = sum_s buf[s * count + i], splits in ascending order (deterministic)
 __global__ void reduce_splits(float4* __restrict__ out, const float4* __restrict__ buf, int nsplit, size_t count4) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count4; i += (size_t)gridDim.x * blockDim.x) {
@@ -60,6 +82,7 @@ __global__ void reduce_splits(float4* __restrict__ out, const float4* __restrict
 }
 
 static std::atomic<uint64_t> g_launches{0};
+constexpr int kMaxBatchSplit = 4;
 
 // The driver's tensor-map encoder, obtained through the runtime (no link against libcuda).
 cudaError_t make_partner_tmap(CUtensorMap* map, const void* base, int n, long long rows, int sp, int box_rows) {
@@ -208,6 +231,19 @@ struct hse_plan_s {
   int nsplit[2] = {1, 1};    // k'-loop splits of the fused kernel for owners = targets / occupied
   float2* split_buf = nullptr;  // [nsplit][nk][n_own][N] partial outputs when nsplit > 1
   size_t split_buf_elems = 0;
+  // batched plans (hse_plan_create_batched)
+  bool batched = false;
+  std::vector<hse_plan> cells;          // one sub-plan (kernel tables) per cell
+  std::vector<BatchCell> h_cells;       // launch arguments, pointers refreshed per call
+  std::vector<float2*> cell_split;      // per cell [kMaxBatchSplit][nk][n_tgt][N]
+  BatchCell* d_cells = nullptr;
+  BatchItem* d_items = nullptr;
+  int* d_counter = nullptr;
+  int nitems = 0;
+  int batch_split = 0;                  // autotuned k' split (0: not tuned yet)
+  int sms = 0;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
@@ -292,6 +328,13 @@ int hse_plan_destroy(hse_plan plan) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(plan->device);
+  for (hse_plan c : plan->cells) hse_plan_destroy(c);
+  for (float2* b : plan->cell_split) cudaFree(b);
+  cudaFree(plan->d_cells);
+  cudaFree(plan->d_items);
+  cudaFree(plan->d_counter);
+  if (plan->graph) cudaGraphExecDestroy(plan->graph);
+  if (plan->capture_stream) cudaStreamDestroy(plan->capture_stream);
   cudaFree(plan->qidx);
   cudaFree(plan->qvec);
   cudaFree(plan->dkpts);
@@ -576,6 +619,49 @@ int staged_apply(hse_plan plan, const double2* u_occ, const double* occ, const d
   return HSE_OK;
 }
 
+// Work list of a batched plan for a k' split factor: items (cell, split, k, tile) sorted by
+// cost (partners x grid points x log2 grid points), largest first; sets each cell's split.
+void build_batch(hse_plan plan, int split, void* const* vx_out) {
+  struct Entry {
+    double cost;
+    BatchItem it;
+  };
+  std::vector<Entry> list;
+  for (size_t c = 0; c < plan->cells.size(); ++c) {
+    const hse_problem& q = plan->cells[c]->p;
+    BatchCell& bc = plan->h_cells[c];
+    const int ns = std::min(split, std::min(kMaxBatchSplit, q.nk));
+    bc.pa.nsplit = ns;
+    bc.pa.out = ns > 1 ? plan->cell_split[c] : (float2*)vx_out[c];
+    const int T = slots_for(q.grid[0]);
+    const int ntiles = (q.n_tgt + T - 1) / T;
+    const double n = q.grid[0];
+    for (int sp = 0; sp < ns; ++sp) {
+      const int kp0 = (int)(((long long)sp * q.nk) / ns), kp1 = (int)(((long long)(sp + 1) * q.nk) / ns);
+      const double cost = (double)(kp1 - kp0) * q.n_occ * n * n * n * std::log2(n);
+      for (int r = 0; r < q.nk * ntiles; ++r) list.push_back({cost, {(int)c, sp * q.nk * ntiles + r}});
+    }
+  }
+  std::stable_sort(list.begin(), list.end(), [](const Entry& x, const Entry& y) { return x.cost > y.cost; });
+  std::vector<BatchItem> items(list.size());
+  for (size_t i = 0; i < list.size(); ++i) items[i] = list[i].it;
+  plan->nitems = (int)items.size();
+  cudaMemcpy(plan->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+}
+
+// counter reset + persistent kernel + reduction of split cells (graph-capturable)
+cudaError_t run_batch(hse_plan plan, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(plan->d_counter, 0, sizeof(int), st);
+  BatchArgs b{plan->d_cells, plan->d_items, plan->nitems, plan->d_counter};
+  if (e == cudaSuccess) e = launch_pairconv_batched(b, plan->sms, st);
+  if (e == cudaSuccess && plan->batch_split != 1) {
+    reduce_splits_batched<<<plan->sms * 4, 256, 0, st>>>(plan->d_cells, (int)plan->cells.size());
+    count_launch();
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
 // Staged FP64 VJP: grad_u_tgt = V_x ybar; grad_omega = Re <ybar, V_x' u_tgt> (V_x' with
 // d v / d omega rows); grad_u_occ by occupied-owner batches.
 int staged_vjp(hse_plan plan, const double2* u_occ, const double* occ, const double2* u_tgt, const double2* ybar,
@@ -784,16 +870,134 @@ int hse_kinetic_apply(hse_plan plan, const void* u, int nbands, const double* A,
 }
 
 int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells) {
-  (void)cells;
-  (void)ncells;
-  if (out) *out = nullptr;
-  return HSE_ERR_INVALID_ARG;
+  if (!out) return HSE_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cells || ncells < 1 || ncells > 65536) return HSE_ERR_INVALID_ARG;
+  for (int c = 0; c < ncells; ++c) {
+    const int rc = validate_problem(&cells[c]);
+    if (rc) return rc;
+    if (cells[c].dtype != HSE_C64 || !batched_side_supported(cells[c].grid[0])) return HSE_ERR_UNSUPPORTED_GRID;
+  }
+  hse_plan plan = new (std::nothrow) hse_plan_s();
+  if (!plan) return HSE_ERR_NOMEM;
+  plan->batched = true;
+  plan->p = cells[0];
+  cudaGetDevice(&plan->device);
+  int rc = HSE_OK;
+  cudaError_t e = cudaDeviceGetAttribute(&plan->sms, cudaDevAttrMultiProcessorCount, plan->device);
+  size_t max_items = 0;
+  for (int c = 0; c < ncells && rc == HSE_OK && e == cudaSuccess; ++c) {
+    hse_plan sub = nullptr;
+    rc = hse_plan_create(&sub, &cells[c]);
+    if (rc) break;
+    sub->blocks_per_sm = 1;
+    plan->cells.push_back(sub);
+    const hse_problem& q = sub->p;
+    const int T = slots_for(q.grid[0]);
+    const int ntiles = (q.n_tgt + T - 1) / T;
+    max_items += (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * ntiles;
+    float2* buf = nullptr;
+    if (q.nk > 1) e = cudaMalloc(&buf, (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * q.n_tgt * sub->N * sizeof(float2));
+    plan->cell_split.push_back(buf);
+  }
+  if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_cells, (size_t)ncells * sizeof(BatchCell));
+  if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_items, max_items * sizeof(BatchItem));
+  if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_counter, sizeof(int));
+  if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->status, sizeof(int));
+  if (rc == HSE_OK && e == cudaSuccess) e = cudaMemset(plan->status, 0, sizeof(int));
+  if (rc == HSE_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking);
+  if (rc == HSE_OK && e != cudaSuccess) rc = cuda_fail(e);
+  if (rc) {
+    hse_plan_destroy(plan);
+    return rc;
+  }
+  plan->h_cells.resize(ncells);
+  *out = plan;
+  return HSE_OK;
 }
 
 int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double* const* occ, const void* const* u_tgt,
                            void* const* vx_out, hse_stream_t stream) {
-  (void)plan; (void)u_occ; (void)occ; (void)u_tgt; (void)vx_out; (void)stream;
-  return HSE_ERR_INVALID_ARG;
+  if (!plan || !plan->batched || !u_occ || !occ || !u_tgt || !vx_out) return HSE_ERR_INVALID_ARG;
+  const int ncells = (int)plan->cells.size();
+  for (int c = 0; c < ncells; ++c) {
+    const hse_plan sub = plan->cells[c];
+    const hse_problem& q = sub->p;
+    if (!u_occ[c] || !occ[c] || !u_tgt[c] || !vx_out[c]) return HSE_ERR_INVALID_ARG;
+    if (!aligned16(u_occ[c]) || !aligned16(u_tgt[c]) || !aligned16(vx_out[c])) return HSE_ERR_INVALID_ARG;
+    const size_t ob = (size_t)q.nk * q.n_occ * sub->N * 8, tb = (size_t)q.nk * q.n_tgt * sub->N * 8;
+    if (overlaps(vx_out[c], tb, u_occ[c], ob) || overlaps(vx_out[c], tb, u_tgt[c], tb) ||
+        overlaps(vx_out[c], tb, occ[c], (size_t)q.nk * q.n_occ * sizeof(double)))
+      return HSE_ERR_ALIAS;
+    for (int d = 0; d < c; ++d) {
+      const hse_problem& r = plan->cells[d]->p;
+      if (overlaps(vx_out[c], tb, vx_out[d], (size_t)r.nk * r.n_tgt * plan->cells[d]->N * 8)) return HSE_ERR_ALIAS;
+    }
+  }
+  cudaStream_t st = S(stream);
+  // per-call pointers into the cell table; the split structure is set by build_batch
+  for (int c = 0; c < ncells; ++c) {
+    BatchCell& bc = plan->h_cells[c];
+    const hse_plan sub = plan->cells[c];
+    PairArgs a = base_args(sub);
+    a.own = (const float2*)u_tgt[c];
+    a.part = (const float2*)u_occ[c];
+    a.occ = occ[c];
+    a.n_part = sub->p.n_occ;
+    a.n_own = sub->p.n_tgt;
+    const int T = slots_for(sub->p.grid[0]);
+    a.ntiles = (a.n_own + T - 1) / T;
+    a.status = plan->status;
+    a.nsplit = bc.pa.nsplit > 0 ? bc.pa.nsplit : 1;
+    a.split_stride = (size_t)sub->p.nk * a.n_own * sub->N;
+    a.out = a.nsplit > 1 ? plan->cell_split[c] : (float2*)vx_out[c];
+    bc.pa = a;
+    bc.final_out = (float2*)vx_out[c];
+    bc.n = sub->p.grid[0];
+  }
+  cudaError_t e = cudaSuccess;
+  if (plan->batch_split == 0) {
+    // autotune the k'-split granularity of the work items on this first call
+    float best_ms = 0.f;
+    int best = 1;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    const int cands[3] = {1, 2, 4};
+    for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
+      build_batch(plan, cands[ci], vx_out);
+      e = cudaMemcpyAsync(plan->d_cells, plan->h_cells.data(), ncells * sizeof(BatchCell), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+      if (e == cudaSuccess) e = run_batch(plan, st);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+      if (e == cudaSuccess && (ci == 0 || ms < best_ms)) {
+        best_ms = ms;
+        best = cands[ci];
+      }
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (e != cudaSuccess) return cuda_fail(e);
+    plan->batch_split = best;
+    build_batch(plan, best, vx_out);
+    // capture counter reset + persistent kernel + split reduction as one graph
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t er = run_batch(plan, plan->capture_stream);
+      e = cudaStreamEndCapture(plan->capture_stream, &g);
+      if (e == cudaSuccess) e = er;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  e = cudaMemcpyAsync(plan->d_cells, plan->h_cells.data(), ncells * sizeof(BatchCell), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(plan->graph, st);
+  return cuda_fail(e);
 }
 
 }  // extern "C"

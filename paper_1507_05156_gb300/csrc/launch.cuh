@@ -27,6 +27,25 @@ bool pairconv_c64_supported(int n);
 cudaError_t launch_kinetic_c64(int n, const float2* u, float2* out, const KinArgs& a, cudaStream_t stream);
 int pairconv_c64_occupancy(int n, int mode, int blocks_per_sm);
 
+// Batched launch over cells of unequal grid sides (batched.cu).
+struct BatchCell {
+  PairArgs pa;          // the cell's launch arguments (pa.out: final output or split buffer)
+  float2* final_out;    // the cell's V_x u output
+  int n;                // grid side
+};
+struct BatchItem {
+  int cell;             // index into the cell table
+  int item;             // (split, k, tile) index within the cell
+};
+struct BatchArgs {
+  const BatchCell* cells;
+  const BatchItem* items;
+  int nitems;
+  int* counter;         // zeroed before each launch
+};
+bool batched_side_supported(int n);
+cudaError_t launch_pairconv_batched(const BatchArgs& b, int sms, cudaStream_t stream);
+
 // One staged FP64 1-D transform pass along an axis of length L with element stride inner.
 cudaError_t launch_staged_fft(int L, int dir, double2* work, size_t nbatch, int N, int inner, cudaStream_t stream);
 bool staged_fft_supported(int L);

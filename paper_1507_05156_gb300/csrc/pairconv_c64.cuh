@@ -282,21 +282,24 @@ __device__ __forceinline__ void stage_z_inverse(const float2* g, int t, const fl
 
 // One pair chain between the Z stages; all threads of the CTA call it together.
 template <int n>
-__device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32_t ttab, float f) {
+__device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32_t ttab, float f, bool warp_on = true) {
   __syncthreads();
-  stage_y<n, -1>(g, t, valid);
+  if (warp_on) stage_y<n, -1>(g, t, valid);
   __syncthreads();
-  stage_x<n>(g, t, valid, ttab, f);
+  if (warp_on) stage_x<n>(g, t, valid, ttab, f);
   __syncthreads();
-  stage_y<n, +1>(g, t, valid);
+  if (warp_on) stage_y<n, +1>(g, t, valid);
   __syncthreads();
 }
 
-template <int n, int MODE, int MINB>
-__global__ void __launch_bounds__(Geo<n>::THREADS, MINB) pairconv_c64_kernel(const PairArgs args) {
+// One work item `item` = (split, k, tile) of a launch.  The CTA may have more threads than
+// the item needs (the batched kernel runs every grid side in one block shape): warps with
+// warp_on == false skip all work and TMEM traffic but pass every barrier.  tbase: the CTA's
+// TMEM allocation, at least Geo<n>::TMEM_COLS columns for this block's warp count.
+template <int n, int MODE>
+__device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, float4* smem4, uint32_t tbase,
+                                              bool warp_on) {
   using G = Geo<n>;
-  extern __shared__ __align__(16) float4 smem4[];
-  __shared__ uint32_t tmem_base_sh;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -307,21 +310,13 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, MINB) pairconv_c64_kernel(con
 
   // tensor memory for the accumulators: warp w uses lanes 32 (w % 4) .. +31, columns from
   // (w / 4) * COLS_PER_WARP; the thread's pencil pass ps is the row at + ps * ROW.
-  if (warp == 0) {
-    tmem_alloc(&tmem_base_sh, G::TMEM_COLS);
-    tmem_relinquish();
-  }
-  tmem_fence_before_sync();
-  __syncthreads();
-  tmem_fence_after_sync();
-  const uint32_t tbase = tmem_base_sh;
   const uint32_t trow0 = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * G::COLS_PER_WARP);
   const uint32_t ttab = trow0 + (uint32_t)G::TAB;
 
   // work item: (split, k, tile); split s covers k' in [s nk / nsplit, (s+1) nk / nsplit)
   const int per_split = args.nk * args.ntiles;
-  const int split = blockIdx.x / per_split;
-  const int rem = blockIdx.x - split * per_split;
+  const int split = item / per_split;
+  const int rem = item - split * per_split;
   const int k = rem / args.ntiles;
   const int band = (rem - k * args.ntiles) * G::T + slot;
   const int kp_begin = (int)(((long long)split * args.nk) / args.nsplit);
@@ -330,7 +325,7 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, MINB) pairconv_c64_kernel(con
   const int bandc = active ? band : 0;
   const float2* own = args.own + ((size_t)k * args.n_own + bandc) * G::N;
 
-  {
+  if (warp_on) {
     float z[G::ROW];
 #pragma unroll
     for (int e = 0; e < G::ROW; ++e) z[e] = 0.f;
@@ -341,31 +336,32 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, MINB) pairconv_c64_kernel(con
   for (int kp = kp_begin; kp < kp_end; ++kp) {
     // q = k_i - k_j: APPLY-like modes own i (at k) and pair with j at kp; OCC owns j (at k)
     const int qrow = (MODE == MODE_OCC) ? args.qidx[kp * args.nk + k] : args.qidx[k * args.nk + kp];
-    cache_kernel_row<n>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
+    if (warp_on) cache_kernel_row<n>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
     for (int j = 0; j < args.n_part; ++j) {
       const float2* part = args.part + ((size_t)kp * args.n_part + j) * G::N;
       if constexpr (MODE != MODE_OCC) {
         const float f = (float)args.occ[kp * args.n_occ + j];
         if (f == 0.f) continue;  // uniform over the CTA
-        stage_z_forward<n>(g, t, valid, part, own);          // conj(u_j) u_i
-        pair_middle<n>(g, t, valid, ttab, f);
-        stage_z_inverse<n, EPI_MUL>(g, t, part, trow0);      // acc += u_j phi
+        if (warp_on) stage_z_forward<n>(g, t, valid, part, own);          // conj(u_j) u_i
+        pair_middle<n>(g, t, valid, ttab, f, warp_on);
+        if (warp_on) stage_z_inverse<n, EPI_MUL>(g, t, part, trow0);      // acc += u_j phi
       } else {
         const float f = (float)args.occ[k * args.n_occ + bandc];
         const float2* ybar = args.part2 + ((size_t)kp * args.n_part + j) * G::N;
         // chain 1: rho = conj(u_j) u_i -> phi;  acc += conj(phi) ybar_i
-        stage_z_forward<n>(g, t, valid, own, part);
-        pair_middle<n>(g, t, valid, ttab, f);
-        stage_z_inverse<n, EPI_CONJPHI>(g, t, ybar, trow0);
+        if (warp_on) stage_z_forward<n>(g, t, valid, own, part);
+        pair_middle<n>(g, t, valid, ttab, f, warp_on);
+        if (warp_on) stage_z_inverse<n, EPI_CONJPHI>(g, t, ybar, trow0);
         // chain 2: sigma = conj(u_j) ybar_i -> psibar;  acc += u_i conj(psibar)
-        stage_z_forward<n>(g, t, valid, own, ybar);
-        pair_middle<n>(g, t, valid, ttab, f);
-        stage_z_inverse<n, EPI_WCONJ>(g, t, part, trow0);
+        if (warp_on) stage_z_forward<n>(g, t, valid, own, ybar);
+        pair_middle<n>(g, t, valid, ttab, f, warp_on);
+        if (warp_on) stage_z_inverse<n, EPI_WCONJ>(g, t, part, trow0);
       }
     }
   }
 
   if constexpr (MODE == MODE_APPLY || MODE == MODE_OCC) {
+    if (!warp_on) return;
     float2* obase = args.out + split * args.split_stride + ((size_t)k * args.n_own + bandc) * G::N;
 #pragma unroll 1
     for (int ps = 0; ps < 2; ++ps) {
@@ -383,7 +379,7 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, MINB) pairconv_c64_kernel(con
     const float2* lhs = (MODE == MODE_ENERGY) ? own : args.part2 + ((size_t)k * args.n_own + bandc) * G::N;
     double d = 0.0;
 #pragma unroll 1
-    for (int ps = 0; ps < 2; ++ps) {
+    for (int ps = 0; ps < 2 && warp_on; ++ps) {
       const Pencil<n> pc(t + ps * G::TS);
       float acc[G::ROW];
       TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
@@ -394,7 +390,7 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, MINB) pairconv_c64_kernel(con
     }
     __syncthreads();  // the grid buffers are free now; reuse them for the per-thread partials
     double* red = reinterpret_cast<double*>(smem4);
-    red[tid] = valid ? d : 0.0;
+    red[tid] = (valid && warp_on) ? d : 0.0;
     __syncthreads();
     if (valid && t == 0 && active) {
       double sum = 0.0;
@@ -403,7 +399,23 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, MINB) pairconv_c64_kernel(con
       args.partial[split * args.split_stride + (size_t)k * args.n_own + band] = sum;
     }
   }
+}
 
+template <int n, int MODE, int MINB>
+__global__ void __launch_bounds__(Geo<n>::THREADS, MINB) pairconv_c64_kernel(const PairArgs args) {
+  using G = Geo<n>;
+  extern __shared__ __align__(16) float4 smem4[];
+  __shared__ uint32_t tmem_base_sh;
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base_sh, G::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tbase = tmem_base_sh;
+  pairconv_item<n, MODE>(args, blockIdx.x, smem4, tbase, true);
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();

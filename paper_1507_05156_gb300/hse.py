@@ -77,8 +77,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hse_fock_apply.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.hse_exchange_energy.argtypes = [vp, vp, vp, vp, vp]
         lib.hse_fock_apply_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
-        lib.hse_fock_apply_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
-                                               ctypes.POINTER(vp), vp]
+        lib.hse_fock_apply_batched.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.hse_status.argtypes = [vp, vp]
         lib.hse_grid_supported.argtypes = [i, i]
         lib.hse_kernel_launches.argtypes = []
@@ -247,6 +246,57 @@ def hse_fock_apply_vjp(plan: Plan, u_occ, occ, u_tgt, grad_vx, need_occ=True, ne
     _check(lib.hse_fock_apply_vjp(plan.handle, _ptr(u_occ), _ptr(occ), _ptr(u_tgt), _ptr(grad_vx), _ptr(g_occ),
                                   _ptr(g_tgt), _ptr(g_om), _stream(stream)), "hse_fock_apply_vjp")
     return g_occ, g_tgt, g_om
+
+
+class BatchedPlan:
+    """An hse_plan over many cells (hse_plan_create_batched): one persistent, graph-captured
+    launch applies V_x to every cell; the work-item granularity is autotuned on first use."""
+
+    def __init__(self, cells, omega=None, alpha=None, dtype=torch.complex64):
+        """cells: objects with grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy."""
+        lib = load_library()
+        self.cells = list(cells)
+        probs = (HseProblem * len(self.cells))()
+        self._keep = []
+        for c, cell in enumerate(self.cells):
+            pr, kp = _problem(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt,
+                              cell.omega if omega is None else omega, cell.alpha if alpha is None else alpha,
+                              getattr(cell, "spin_degeneracy", 2.0), dtype)
+            probs[c] = pr
+            self._keep.append(kp)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        _check(lib.hse_plan_create_batched(ctypes.byref(h), probs, len(self.cells)), "hse_plan_create_batched")
+        self.handle = h
+        self.dtype = dtype
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.hse_plan_destroy(h)
+            self.handle = None
+
+
+def hse_fock_apply_batched(plan: BatchedPlan, u_occ, occ, u_tgt, out=None, stream=None):
+    """V_x for every cell of a batched plan; lists of per-cell device tensors."""
+    lib = load_library()
+    n = len(plan.cells)
+    if not (len(u_occ) == len(occ) == len(u_tgt) == n):
+        raise ValueError("one tensor per cell is required")
+    if out is None:
+        out = [torch.empty_like(t) for t in u_tgt]
+    for c, cell in enumerate(plan.cells):
+        nk = len(cell.kpts)
+        for name, t, shape, dt in (("u_occ", u_occ[c], (nk, cell.n_occ) + tuple(cell.grid), plan.dtype),
+                                   ("u_tgt", u_tgt[c], (nk, cell.n_tgt) + tuple(cell.grid), plan.dtype),
+                                   ("out", out[c], (nk, cell.n_tgt) + tuple(cell.grid), plan.dtype),
+                                   ("occ", occ[c], (nk, cell.n_occ), torch.float64)):
+            if not t.is_cuda or t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"cell {c}: {name} must be a contiguous CUDA {dt} tensor of shape {shape}")
+    arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+    _check(lib.hse_fock_apply_batched(plan.handle, arr(u_occ), arr(occ), arr(u_tgt), arr(out), _stream(stream)),
+           "hse_fock_apply_batched")
+    return out
 
 
 def hse_kinetic_apply(plan: Plan, u: torch.Tensor, A, out: Optional[torch.Tensor] = None,
