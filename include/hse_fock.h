@@ -128,7 +128,11 @@ int hse_kinetic_apply(hse_plan plan, const void *u, int nbands, const double *A,
                       hse_stream_t stream);
 
 /* Synchronises the stream, then returns HSE_OK, HSE_ERR_TIMEOUT or HSE_ERR_DEVICE from
- * the plan's device status word (and clears it), or HSE_ERR_CUDA. */
+ * the plan's device status word (and clears it), or HSE_ERR_CUDA.  Every device-side wait of
+ * the library is bounded (about one second); on expiry the kernel records HSE_ERR_TIMEOUT,
+ * stops waiting and returns, so the context stays usable.  Test hook: a plan created while
+ * the environment variable HSE_INJECT_SKIP_FILL=1 is set never issues the first asynchronous
+ * partner copy of its complex64 kernels, so that wait runs out (its results are garbage). */
 int hse_status(hse_plan plan, hse_stream_t stream);
 
 /* 1 if this build has a kernel for axis length n (and dtype), else 0. */

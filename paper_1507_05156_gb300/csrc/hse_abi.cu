@@ -228,6 +228,7 @@ struct hse_plan_s {
   size_t work_pairs = 0;
   double2* vx64 = nullptr;   // [nk][max(n_occ, n_tgt)][N]
   int blocks_per_sm = 0;     // fused-kernel variant: 0 staged partner (TMA), 1/2 pencil loads
+  int inject = 0;            // test hook (HSE_INJECT_SKIP_FILL=1 at plan creation)
   int nsplit[2] = {1, 1};    // k'-loop splits of the fused kernel for owners = targets / occupied
   float2* split_buf = nullptr;  // [nsplit][nk][n_own][N] partial outputs when nsplit > 1
   size_t split_buf_elems = 0;
@@ -366,6 +367,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   plan->kpts.assign(p->kpts, p->kpts + 3 * p->nk);
   plan->p.kpts = plan->kpts.data();
   cudaGetDevice(&plan->device);
+  if (const char* env = std::getenv("HSE_INJECT_SKIP_FILL")) plan->inject = std::atoi(env) == 1 ? 1 : 0;
   if (const char* env = std::getenv("HSE_BLOCKS_PER_SM")) {
     const int v = std::atoi(env);
     plan->blocks_per_sm = v <= 0 ? 0 : (v >= 2 ? 2 : 1);
@@ -532,6 +534,7 @@ PairArgs base_args(hse_plan plan) {
   a.n_occ = plan->p.n_occ;
   a.scale = (float)(-plan->p.alpha / ((double)plan->p.nk * plan->N));
   a.status = plan->status;
+  a.inject = plan->inject;
   return a;
 }
 

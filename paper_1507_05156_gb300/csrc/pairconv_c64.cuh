@@ -102,6 +102,7 @@ struct PairArgs {
   int nsplit;           // the k' loop is split into nsplit work items per owner tile
   size_t split_stride;  // elements between the per-split outputs (out: float2, partial: double)
   int* status;          // device status word for failed device-side waits (may be null)
+  int inject;           // test hook: 1 = the staged kernel never issues its first partner copy
 };
 
 template <int n>

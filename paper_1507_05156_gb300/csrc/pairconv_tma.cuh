@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
   }
   __syncthreads();
   int q = next_partner(occ_sh, args, kp_begin, 0, npairs);
-  if (warp == 0 && q < npairs) fill(q, 0);
+  if (warp == 0 && q < npairs && args.inject != 1) fill(q, 0);
 
   // owner orbital into TMEM, accumulators to zero
 #pragma unroll 1
