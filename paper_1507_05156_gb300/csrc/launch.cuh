@@ -93,16 +93,16 @@ int pairconv_occupancy_variant() {
 // Encodes the tensor map of a partner array for the staged-partner kernel of side n.
 cudaError_t make_partner_tmap(CUtensorMap* map, const void* base, int n, long long rows, int sp, int box_rows);
 
-template <int n, int MODE>
+template <int n, int MODE, template <int> class L>
 cudaError_t launch_pairconv_tma(const PairArgs& args, cudaStream_t stream) {
-  using S = GeoS<n>;
+  using S = GeoS<n, L<n>>;
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_done[dev]) {
-    cudaError_t err = cudaFuncSetAttribute(pairconv_tma_kernel<n, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)S::SMEM_REQUEST);
+    cudaError_t err = cudaFuncSetAttribute(pairconv_tma_kernel<n, MODE, L>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM_REQUEST);
     if (err != cudaSuccess) return err;
     attr_done[dev] = true;
   }
@@ -110,29 +110,61 @@ cudaError_t launch_pairconv_tma(const PairArgs& args, cudaStream_t stream) {
   cudaError_t err = make_partner_tmap(&tmap, args.part, n, (long long)args.nk * args.n_part * Geo<n>::NN, S::SP, S::BR);
   if (err != cudaSuccess) return err;
   const dim3 grid((unsigned)((size_t)args.nsplit * args.nk * args.ntiles));
-  pairconv_tma_kernel<n, MODE><<<grid, Geo<n>::THREADS, S::SMEM_REQUEST, stream>>>(args, tmap);
+  pairconv_tma_kernel<n, MODE, L><<<grid, L<n>::THREADS, S::SMEM_REQUEST, stream>>>(args, tmap);
   count_launch();
   return cudaGetLastError();
 }
 
-// blocks_per_sm: 0 selects the staged-partner kernel where it exists for (n, mode); 1 or 2
-// select the pencil-load kernel with that occupancy.
-template <int n, int MODE>
-cudaError_t launch_pairconv_mode(const PairArgs& args, int blocks_per_sm, cudaStream_t stream) {
-  if constexpr (GeoS<n>::FITS && (MODE == MODE_APPLY || MODE == MODE_ENERGY || MODE == MODE_DOT)) {
-    if (blocks_per_sm == 0) return launch_pairconv_tma<n, MODE>(args, stream);
+// The staged-partner kernel exists for the owner = target modes and the layouts that fit.
+template <int n, int MODE, template <int> class L>
+constexpr bool tma_fits() {
+  if constexpr (L<n>::OK && (MODE == MODE_APPLY || MODE == MODE_ENERGY || MODE == MODE_DOT)) {
+    return GeoS<n, L<n>>::FITS;
+  } else {
+    return false;
   }
-  if (blocks_per_sm == 0) blocks_per_sm = 2;
+}
+
+// Kernel variant: 0 the default (the staged-partner kernel with its default layout where it
+// exists for (n, mode), else the pencil-load kernel at the occupancy the size allows);
+// -1 / -2 / -3 the staged-partner kernel with LayoutSeq / LayoutWide / LayoutOne; 1 or 2 the
+// pencil-load kernel with that occupancy.  A staged layout that does not fit falls back to
+// the default.
+template <int n, int MODE>
+constexpr int staged_layout(int variant) {
+  if (variant > 0) return 0;
+  const bool seq = tma_fits<n, MODE, LayoutSeq>(), wide = tma_fits<n, MODE, LayoutWide>(),
+             one = tma_fits<n, MODE, LayoutOne>();
+  if (variant == -1 && seq) return -1;
+  if (variant == -2 && wide) return -2;
+  if (variant == -3 && one) return -3;
+  // default: one pencil per thread where it fits, else two
+  return one ? -3 : (seq ? -1 : 0);
+}
+
+template <int n, int MODE>
+cudaError_t launch_pairconv_mode(const PairArgs& args, int variant, cudaStream_t stream) {
+  switch (staged_layout<n, MODE>(variant)) {
+    case -1:
+      if constexpr (tma_fits<n, MODE, LayoutSeq>()) return launch_pairconv_tma<n, MODE, LayoutSeq>(args, stream);
+      break;
+    case -2:
+      if constexpr (tma_fits<n, MODE, LayoutWide>()) return launch_pairconv_tma<n, MODE, LayoutWide>(args, stream);
+      break;
+    case -3:
+      if constexpr (tma_fits<n, MODE, LayoutOne>()) return launch_pairconv_tma<n, MODE, LayoutOne>(args, stream);
+      break;
+    default: break;
+  }
+  const int blocks_per_sm = variant <= 0 ? 2 : variant;
   if (blocks_per_sm >= 2 && Geo<n>::MAXB >= 2) return launch_pairconv_variant<n, MODE, Geo<n>::MAXB>(args, stream);
   return launch_pairconv_variant<n, MODE, 1>(args, stream);
 }
 
 template <int n, int MODE>
-int pairconv_occupancy_mode(int blocks_per_sm) {
-  if constexpr (GeoS<n>::FITS && (MODE == MODE_APPLY || MODE == MODE_ENERGY || MODE == MODE_DOT)) {
-    if (blocks_per_sm == 0) return 1;
-  }
-  if (blocks_per_sm == 0) blocks_per_sm = 2;
+int pairconv_occupancy_mode(int variant) {
+  if (staged_layout<n, MODE>(variant) != 0) return 1;
+  const int blocks_per_sm = variant <= 0 ? 2 : variant;
   if (blocks_per_sm >= 2 && Geo<n>::MAXB >= 2) return pairconv_occupancy_variant<n, MODE, Geo<n>::MAXB>();
   return pairconv_occupancy_variant<n, MODE, 1>();
 }

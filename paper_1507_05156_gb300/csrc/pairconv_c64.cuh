@@ -169,13 +169,13 @@ struct Pencil {
   }
 };
 
-// Stage Y (DIR) for both pencils of the thread: load, FFT, store.
-template <int n, int DIR>
+// Stage Y (DIR) for the PPT pencils of the thread (pencil t + ps NN/PPT): load, FFT, store.
+template <int n, int DIR, int PPT = 2>
 __device__ __forceinline__ void stage_y(float2* g, int t, bool valid) {
   using G = Geo<n>;
 #pragma unroll 1
-  for (int ps = 0; ps < 2; ++ps) {
-    const Pencil<n> pc(t + ps * G::TS);
+  for (int ps = 0; ps < PPT; ++ps) {
+    const Pencil<n> pc(t + ps * (G::NN / PPT));
     cpx<float> v[n];
     load_s<n, 1>(v, g, pc.ys, G::P);
     fft<n, DIR, float>(v);
@@ -184,13 +184,13 @@ __device__ __forceinline__ void stage_y(float2* g, int t, bool valid) {
 }
 
 // Stage X: FFT, multiply by the kernel row (cached in TMEM, already times -alpha/(N_k N))
-// times the occupation f, inverse FFT, for both pencils.  Warp-wide (TMEM loads).
-template <int n>
+// times the occupation f, inverse FFT, for the PPT pencils.  Warp-wide (TMEM loads).
+template <int n, int PPT = 2>
 __device__ __forceinline__ void stage_x(float2* g, int t, bool valid, uint32_t ttab, float f) {
   using G = Geo<n>;
 #pragma unroll 1
-  for (int ps = 0; ps < 2; ++ps) {
-    const Pencil<n> pc(t + ps * G::TS);
+  for (int ps = 0; ps < PPT; ++ps) {
+    const Pencil<n> pc(t + ps * (G::NN / PPT));
     float tv[n];
     TmemRow<n>::load(ttab + (uint32_t)(ps * n), tv);
     cpx<float> v[n];
@@ -207,13 +207,13 @@ __device__ __forceinline__ void stage_x(float2* g, int t, bool valid, uint32_t t
   }
 }
 
-// Kernel row v(|G+q|) * scale of this thread's two X-pencils into the TMEM cache.
-template <int n>
+// Kernel row v(|G+q|) * scale of this thread's PPT X-pencils into the TMEM cache.
+template <int n, int PPT = 2>
 __device__ __forceinline__ void cache_kernel_row(int t, uint32_t ttab, const float* __restrict__ vrow, float scale) {
   using G = Geo<n>;
 #pragma unroll 1
-  for (int ps = 0; ps < 2; ++ps) {
-    const int p = t + ps * G::TS;
+  for (int ps = 0; ps < PPT; ++ps) {
+    const int p = t + ps * (G::NN / PPT);
     float tv[n];
 #pragma unroll
     for (int e = 0; e < n; ++e) tv[e] = __ldg(vrow + e * G::NN + p) * scale;

@@ -28,8 +28,9 @@ namespace hse {
 constexpr int kStatusTimeout = -5;  // HSE_ERR_TIMEOUT
 constexpr int kStatusDevice = -7;   // HSE_ERR_DEVICE
 
+// Stage buffer of one partner orbital: NB tensor boxes of BR z-pencils at pitch SP.
 template <int n>
-struct GeoS {
+struct StageGeo {
   using G = Geo<n>;
   static constexpr int SP = ((n / 2) % 2 == 1) ? n : n + 2;    // stage pencil pitch (complex)
   static constexpr int NB = (G::NN + 255) / 256;                // tensor boxes per fill
@@ -37,26 +38,36 @@ struct GeoS {
   static constexpr int STAGE_ROWS = NB * BR;
   static constexpr int STAGE_CPX = STAGE_ROWS * SP;             // one stage buffer
   static constexpr int STAGE_TX = STAGE_ROWS * SP * 8;          // bytes one fill delivers
-  static constexpr size_t GRIDS_BYTES = ((size_t)G::T * G::GRID_CPX * sizeof(float2) + 127) / 128 * 128;
-  static constexpr int TAB = 2 * G::ROW;                        // [acc0 acc1 | tab0 tab1 | own0 own1]
-  static constexpr int OWN = TAB + 2 * n;
-  static constexpr int COLS_PER_WARP = OWN + 2 * G::ROW;
-  static constexpr int TMEM_COLS = pow2_at_least(((G::WARPS + 3) / 4) * COLS_PER_WARP);
-  static constexpr size_t SMEM_BYTES = GRIDS_BYTES + 2 * (size_t)STAGE_CPX * sizeof(float2);
+};
+
+// Shared and tensor memory of the staged kernel for pencil layout Lay (below).  TMEM columns
+// of one warp: [acc (PPT pencils) | kernel rows (PPT) | owner u_i (PPT)].
+template <int n, class Lay>
+struct GeoS : StageGeo<n> {
+  using G = Geo<n>;
+  using SG = StageGeo<n>;
+  static constexpr size_t GRIDS_BYTES = ((size_t)G::T * Lay::GRID_CPX * sizeof(float2) + 127) / 128 * 128;
+  static constexpr int TAB = Lay::PPT * G::ROW;
+  static constexpr int OWN = TAB + Lay::PPT * n;
+  static constexpr int COLS_PER_WARP = OWN + Lay::PPT * G::ROW;
+  static constexpr int TMEM_COLS = pow2_at_least(((Lay::WARPS + 3) / 4) * COLS_PER_WARP);
+  static constexpr size_t SMEM_BYTES = GRIDS_BYTES + 2 * (size_t)SG::STAGE_CPX * sizeof(float2);
   // + 128 bytes to align the base at run time; at least enough that a second CTA (which would
   // need TMEM too) never fits
   static constexpr size_t SMEM_REQUEST = SMEM_BYTES + 128 > 118784 ? SMEM_BYTES + 128 : 118784;
-  static constexpr bool FITS = TMEM_COLS <= 512 && SMEM_REQUEST + 1024 <= 232448 && G::ZFAST_Y == 1;
+  // 4.5 KB of static shared memory (occupation cache, barriers) sit beside the dynamic part
+  static constexpr bool FITS =
+      Lay::OK && TMEM_COLS <= 512 && SMEM_REQUEST + 4608 <= 232448 && Lay::THREADS <= 1024;
 };
 
-// Z forward for both pencils: rho = conj(u_j) u_i with u_j from the stage and u_i from TMEM.
-template <int n>
+// Z forward for the PPT pencils: rho = conj(u_j) u_i with u_j from the stage, u_i from TMEM.
+template <int n, int PPT>
 __device__ __forceinline__ void stage_z_forward_staged(float2* g, int t, bool valid, const float2* stg, uint32_t town) {
   using G = Geo<n>;
-  using S = GeoS<n>;
+  using S = StageGeo<n>;
 #pragma unroll 1
-  for (int ps = 0; ps < 2; ++ps) {
-    const Pencil<n> pc(t + ps * G::TS);
+  for (int ps = 0; ps < PPT; ++ps) {
+    const Pencil<n> pc(t + ps * (G::NN / PPT));
     float uo[G::ROW];
     TmemRow<G::ROW>::load(town + (uint32_t)(ps * G::ROW), uo);
     const float4* s4 = reinterpret_cast<const float4*>(stg + (pc.zg / n) * S::SP);
@@ -72,14 +83,14 @@ __device__ __forceinline__ void stage_z_forward_staged(float2* g, int t, bool va
   }
 }
 
-// Z inverse for both pencils, acc += u_j phi with u_j from the stage.  Warp-wide (TMEM).
-template <int n>
+// Z inverse for the PPT pencils, acc += u_j phi with u_j from the stage.  Warp-wide (TMEM).
+template <int n, int PPT>
 __device__ __forceinline__ void stage_z_inverse_staged(const float2* g, int t, const float2* stg, uint32_t trow0) {
   using G = Geo<n>;
-  using S = GeoS<n>;
+  using S = StageGeo<n>;
 #pragma unroll 1
-  for (int ps = 0; ps < 2; ++ps) {
-    const Pencil<n> pc(t + ps * G::TS);
+  for (int ps = 0; ps < PPT; ++ps) {
+    const Pencil<n> pc(t + ps * (G::NN / PPT));
     cpx<float> v[n];
     load_s<n, G::ZVEC>(v, g, pc.zs, 1);
     fft<n, +1, float>(v);
@@ -100,6 +111,192 @@ __device__ __forceinline__ void stage_z_inverse_staged(const float2* g, int t, c
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Pencil layouts of the staged kernel.  A layout says how many pencils each thread owns per
+// stage (PPT), hence the block size, which pencils they are and how the smem grid is laid out;
+// the pipeline is the same.
+//   LayoutSeq:  two pencils per thread (t and t + n^2/2), transformed one after the other,
+//               lanes on consecutive pencils, 64-bit smem accesses in Y and X.
+//   LayoutOne:  one pencil per thread, twice the warps: with n^2 pencils per stage spread over
+//               the four warp schedulers of an SM, the busiest scheduler carries fewer
+//               pencil-passes than with LayoutSeq when n^2 / 128 has a small fractional part
+//               (18^3: 3 instead of 4), and each scheduler has more warps to hide latency.
+//   LayoutWide: two pencils per thread, neighbours in z in stages Y and X, so every smem access
+//               moves both (128 bit) and both are transformed together (ILP).
+// ---------------------------------------------------------------------------------------
+
+template <int n, int PPT_>
+struct LayoutLin {
+  using G = Geo<n>;
+  static constexpr int PPT = PPT_;
+  static constexpr int TS = G::NN / PPT;                          // threads per owner slot
+  static constexpr int THREADS = (G::T * TS + 31) / 32 * 32;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int GRID_CPX = G::GRID_CPX;
+  static constexpr bool OK = G::ZFAST_Y == 1 && THREADS <= 1024;
+  static __device__ __forceinline__ int zg(int t, int ps) { return Pencil<n>(t + ps * TS).zg; }
+  static __device__ __forceinline__ void z_forward(float2* g, int t, bool valid, const float2* stg, uint32_t town) {
+    stage_z_forward_staged<n, PPT>(g, t, valid, stg, town);
+  }
+  static __device__ __forceinline__ void z_inverse(const float2* g, int t, const float2* stg, uint32_t trow0) {
+    stage_z_inverse_staged<n, PPT>(g, t, stg, trow0);
+  }
+  template <int DIR>
+  static __device__ __forceinline__ void y(float2* g, int t, bool valid) {
+    stage_y<n, DIR, PPT>(g, t, valid);
+  }
+  static __device__ __forceinline__ void x(float2* g, int t, bool valid, uint32_t ttab, float f) {
+    stage_x<n, PPT>(g, t, valid, ttab, f);
+  }
+  static __device__ __forceinline__ void cache_row(int t, uint32_t ttab, const float* vrow, float scale) {
+    cache_kernel_row<n, PPT>(t, ttab, vrow, scale);
+  }
+};
+
+template <int n>
+struct LayoutSeq : LayoutLin<n, 2> {};
+template <int n>
+struct LayoutOne : LayoutLin<n, 1> {};
+
+// (P, Q, Z pairing) of the wide layout: 0 = (a, 2j), (a, 2j+1); 1 = (a, j), (a, j + n/2)
+__host__ __device__ constexpr int wide_cfg(int n, int which) {
+  return n == 4    ? (which == 0 ? 4 : which == 1 ? 20 : 0)
+         : n == 6  ? (which == 0 ? 6 : which == 1 ? 38 : 0)
+         : n == 8  ? (which == 0 ? 10 : which == 1 ? 88 : 1)
+         : n == 10 ? (which == 0 ? 10 : which == 1 ? 106 : 0)
+         : n == 12 ? (which == 0 ? 18 : which == 1 ? 220 : 1)
+         : n == 18 ? (which == 0 ? 18 : which == 1 ? 338 : 1)
+         : n == 20 ? (which == 0 ? 26 : which == 1 ? 532 : 1)
+                   : -1;
+}
+
+template <int n>
+struct LayoutWide {
+  using G = Geo<n>;
+  using S = StageGeo<n>;
+  static constexpr int P = wide_cfg(n, 0), Q = wide_cfg(n, 1), ZM = wide_cfg(n, 2);
+  static constexpr int H = n / 2;
+  static constexpr int PPT = 2, TS = G::TS, THREADS = G::THREADS, WARPS = G::WARPS;
+  static constexpr int GRID_CPX = n * (Q > 0 ? Q : 2);
+  static constexpr bool OK = P > 0;
+  // Z-stage pencil ps of thread t: (zx, zy)
+  static __device__ __forceinline__ void zxy(int t, int ps, int& zx, int& zy) {
+    const int a = t / H, j = t - a * H;
+    zx = a;
+    zy = ZM == 0 ? 2 * j + ps : j + ps * H;
+  }
+  static __device__ __forceinline__ int zg(int t, int ps) {
+    int zx, zy;
+    zxy(t, ps, zx, zy);
+    return (zx * n + zy) * n;
+  }
+  static __device__ __forceinline__ void z_forward(float2* g, int t, bool valid, const float2* stg, uint32_t town) {
+#pragma unroll 1
+    for (int ps = 0; ps < 2; ++ps) {
+      int zx, zy;
+      zxy(t, ps, zx, zy);
+      float uo[G::ROW];
+      TmemRow<G::ROW>::load(town + (uint32_t)(ps * G::ROW), uo);
+      const float4* s4 = reinterpret_cast<const float4*>(stg + (zx * n + zy) * S::SP);
+      cpx<float> v[n];
+#pragma unroll
+      for (int e = 0; e < n / 2; ++e) {
+        const float4 w = s4[e];
+        v[2 * e] = {w.x * uo[4 * e] + w.y * uo[4 * e + 1], w.x * uo[4 * e + 1] - w.y * uo[4 * e]};
+        v[2 * e + 1] = {w.z * uo[4 * e + 2] + w.w * uo[4 * e + 3], w.z * uo[4 * e + 3] - w.w * uo[4 * e + 2]};
+      }
+      fft<n, -1, float>(v);
+      if (valid) store_s<n, 2>(v, g, zx * Q + zy * P, 1);
+    }
+  }
+  static __device__ __forceinline__ void z_inverse(const float2* g, int t, const float2* stg, uint32_t trow0) {
+#pragma unroll 1
+    for (int ps = 0; ps < 2; ++ps) {
+      int zx, zy;
+      zxy(t, ps, zx, zy);
+      cpx<float> v[n];
+      load_s<n, 2>(v, g, zx * Q + zy * P, 1);
+      fft<n, +1, float>(v);
+      float acc[G::ROW];
+      const uint32_t trow = trow0 + (uint32_t)(ps * G::ROW);
+      TmemRow<G::ROW>::load(trow, acc);
+      const float4* s4 = reinterpret_cast<const float4*>(stg + (zx * n + zy) * S::SP);
+#pragma unroll
+      for (int e = 0; e < n / 2; ++e) {
+        const float4 w = s4[e];
+        float* a = acc + 4 * e;
+        a[0] = fmaf(w.x, v[2 * e].x, fmaf(-w.y, v[2 * e].y, a[0]));
+        a[1] = fmaf(w.x, v[2 * e].y, fmaf(w.y, v[2 * e].x, a[1]));
+        a[2] = fmaf(w.z, v[2 * e + 1].x, fmaf(-w.w, v[2 * e + 1].y, a[2]));
+        a[3] = fmaf(w.z, v[2 * e + 1].y, fmaf(w.w, v[2 * e + 1].x, a[3]));
+      }
+      TmemRow<G::ROW>::store(trow, acc);
+    }
+  }
+  // Y: pencils (x = t / H, z = 2 (t % H) + {0, 1}); one 128-bit access per element holds both
+  template <int DIR>
+  static __device__ __forceinline__ void y(float2* g, int t, bool valid) {
+    const int ya = t / H, yp = t - ya * H;
+    const int base = ya * Q + 2 * yp;
+    cpx<float> a[n], b[n];
+#pragma unroll
+    for (int e = 0; e < n; ++e) {
+      const float4 w = *reinterpret_cast<const float4*>(g + base + e * P);
+      a[e] = {w.x, w.y};
+      b[e] = {w.z, w.w};
+    }
+    fft<n, DIR, float>(a);
+    fft<n, DIR, float>(b);
+    if (valid) {
+#pragma unroll
+      for (int e = 0; e < n; ++e) *reinterpret_cast<float4*>(g + base + e * P) = make_float4(a[e].x, a[e].y, b[e].x, b[e].y);
+    }
+  }
+  // X: pencils (y = t / H, z = 2 (t % H) + {0, 1}); kernel rows from the TMEM cache
+  static __device__ __forceinline__ void x(float2* g, int t, bool valid, uint32_t ttab, float f) {
+    const int ya = t / H, yp = t - ya * H;
+    const int base = ya * P + 2 * yp;
+    float ta[n], tb[n];
+    TmemRow<n>::load(ttab, ta);
+    TmemRow<n>::load(ttab + (uint32_t)n, tb);
+    cpx<float> a[n], b[n];
+#pragma unroll
+    for (int e = 0; e < n; ++e) {
+      const float4 w = *reinterpret_cast<const float4*>(g + base + e * Q);
+      a[e] = {w.x, w.y};
+      b[e] = {w.z, w.w};
+    }
+    fft<n, -1, float>(a);
+    fft<n, -1, float>(b);
+#pragma unroll
+    for (int e = 0; e < n; ++e) {
+      const float wa = ta[e] * f, wb = tb[e] * f;
+      a[e].x *= wa;
+      a[e].y *= wa;
+      b[e].x *= wb;
+      b[e].y *= wb;
+    }
+    fft<n, +1, float>(a);
+    fft<n, +1, float>(b);
+    if (valid) {
+#pragma unroll
+      for (int e = 0; e < n; ++e) *reinterpret_cast<float4*>(g + base + e * Q) = make_float4(a[e].x, a[e].y, b[e].x, b[e].y);
+    }
+  }
+  static __device__ __forceinline__ void cache_row(int t, uint32_t ttab, const float* __restrict__ vrow, float scale) {
+    const int ya = t / H, yp = t - ya * H;
+    float ta[n], tb[n];
+#pragma unroll
+    for (int e = 0; e < n; ++e) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(vrow + e * G::NN + ya * n + 2 * yp));
+      ta[e] = v.x * scale;
+      tb[e] = v.y * scale;
+    }
+    TmemRow<n>::store(ttab, ta);
+    TmemRow<n>::store(ttab + (uint32_t)n, tb);
+  }
+};
+
 // Occupations of one work item's partners, cached in shared memory when they fit.
 constexpr int kOccCache = 1024;
 
@@ -117,12 +314,14 @@ __device__ __forceinline__ int next_partner(const float* occ_sh, const PairArgs&
   return q;
 }
 
-// tmap: the partner array as rows of z-pencils, box {2 SP floats, BR rows}.
-template <int n, int MODE>
-__global__ void __launch_bounds__(Geo<n>::THREADS, 1)
+// tmap: the partner array as rows of z-pencils, box {2 SP floats, BR rows}.  L: the pencil
+// layout (LayoutSeq or LayoutWide).
+template <int n, int MODE, template <int> class L>
+__global__ void __launch_bounds__(L<n>::THREADS, 1)
     pairconv_tma_kernel(const PairArgs args, const __grid_constant__ CUtensorMap tmap) {
   using G = Geo<n>;
-  using S = GeoS<n>;
+  using Lay = L<n>;
+  using S = GeoS<n, Lay>;
   static_assert(MODE == MODE_APPLY || MODE == MODE_ENERGY || MODE == MODE_DOT, "owner = target modes only");
   extern __shared__ __align__(128) float4 smem4[];
   __shared__ uint32_t tmem_base_sh;
@@ -141,11 +340,11 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
   }
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  const bool valid = tid < G::T * G::TS;
-  const int slot = valid ? tid / G::TS : 0;
-  const int t = valid ? tid - slot * G::TS : 0;
+  const bool valid = tid < G::T * Lay::TS;
+  const int slot = valid ? tid / Lay::TS : 0;
+  const int t = valid ? tid - slot * Lay::TS : 0;
   float2* grids = reinterpret_cast<float2*>(sbase);
-  float2* g = grids + slot * G::GRID_CPX;
+  float2* g = grids + slot * Lay::GRID_CPX;
   float2* stage = reinterpret_cast<float2*>(sbase + S::GRIDS_BYTES);
 
   if (tid == 0) {
@@ -202,10 +401,9 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
 
   // owner orbital into TMEM, accumulators to zero
 #pragma unroll 1
-  for (int ps = 0; ps < 2; ++ps) {
-    const Pencil<n> pc(t + ps * G::TS);
+  for (int ps = 0; ps < Lay::PPT; ++ps) {
     cpx<float> w[n];
-    load_pencil_global<n>(w, own + pc.zg);
+    load_pencil_global<n>(w, own + Lay::zg(t, ps));
     float r[G::ROW];
 #pragma unroll
     for (int e = 0; e < n; ++e) {
@@ -226,7 +424,7 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
     const float f = item_occ(occ_sh, args, kp_begin, q);
     if (kp != cur_kp) {
       const int qrow = args.qidx[k * args.nk + kp];
-      cache_kernel_row<n>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
+      Lay::cache_row(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
       cur_kp = kp;
     }
     // partner u_j has landed in stage[buf]
@@ -239,7 +437,7 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
     }
     if (buf) phase1 ^= 1u; else phase0 ^= 1u;
     const float2* stg = stage + buf * S::STAGE_CPX;
-    stage_z_forward_staged<n>(g, t, valid, stg, town);
+    Lay::z_forward(g, t, valid, stg, town);
     __syncthreads();
     // every thread is past its last read of stage[buf ^ 1]: refill it with the next partner
     const int qn = next_partner(occ_sh, args, kp_begin, q + 1, npairs);
@@ -247,13 +445,13 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
       fence_proxy_async_smem();
       fill(qn, buf ^ 1);
     }
-    stage_y<n, -1>(g, t, valid);
+    Lay::template y<-1>(g, t, valid);
     __syncthreads();
-    stage_x<n>(g, t, valid, ttab, f);
+    Lay::x(g, t, valid, ttab, f);
     __syncthreads();
-    stage_y<n, +1>(g, t, valid);
+    Lay::template y<+1>(g, t, valid);
     __syncthreads();
-    stage_z_inverse_staged<n>(g, t, stg, trow0);
+    Lay::z_inverse(g, t, stg, trow0);
     q = qn;
     buf ^= 1;
   }
@@ -267,12 +465,11 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
   if constexpr (MODE == MODE_APPLY) {
     float2* obase = args.out + split * args.split_stride + ((size_t)k * args.n_own + bandc) * G::N;
 #pragma unroll 1
-    for (int ps = 0; ps < 2; ++ps) {
-      const Pencil<n> pc(t + ps * G::TS);
+    for (int ps = 0; ps < Lay::PPT; ++ps) {
       float acc[G::ROW];
       TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
       if (active) {
-        float4* o = reinterpret_cast<float4*>(obase + pc.zg);
+        float4* o = reinterpret_cast<float4*>(obase + Lay::zg(t, ps));
 #pragma unroll
         for (int e = 0; e < n / 2; ++e) o[e] = make_float4(acc[4 * e], acc[4 * e + 1], acc[4 * e + 2], acc[4 * e + 3]);
       }
@@ -281,12 +478,11 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
     const float2* lhs = (MODE == MODE_ENERGY) ? own : args.part2 + ((size_t)k * args.n_own + bandc) * G::N;
     double d = 0.0;
 #pragma unroll 1
-    for (int ps = 0; ps < 2; ++ps) {
-      const Pencil<n> pc(t + ps * G::TS);
+    for (int ps = 0; ps < Lay::PPT; ++ps) {
       float acc[G::ROW];
       TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
       cpx<float> w[n];
-      load_pencil_global<n>(w, lhs + pc.zg);
+      load_pencil_global<n>(w, lhs + Lay::zg(t, ps));
 #pragma unroll
       for (int e = 0; e < n; ++e) d += (double)w[e].x * (double)acc[2 * e] + (double)w[e].y * (double)acc[2 * e + 1];
     }
@@ -296,7 +492,7 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, 1)
     __syncthreads();
     if (valid && t == 0 && active) {
       double sum = 0.0;
-      for (int e = 0; e < G::TS; ++e) sum += red[slot * G::TS + e];
+      for (int e = 0; e < Lay::TS; ++e) sum += red[slot * Lay::TS + e];
       if (MODE == MODE_ENERGY) sum *= args.occ[k * args.n_occ + band];
       args.partial[split * args.split_stride + (size_t)k * args.n_own + band] = sum;
     }
