@@ -127,19 +127,19 @@ constexpr bool tma_fits() {
 
 // Kernel variant: 0 the default (the staged-partner kernel with its default layout where it
 // exists for (n, mode), else the pencil-load kernel at the occupancy the size allows);
-// -1 / -2 / -3 the staged-partner kernel with LayoutSeq / LayoutWide / LayoutOne; 1 or 2 the
+// -1 / -2 / -3 the staged-partner kernel with LayoutSeq / LayoutOne / LayoutSplit; 1 or 2 the
 // pencil-load kernel with that occupancy.  A staged layout that does not fit falls back to
 // the default.
 template <int n, int MODE>
 constexpr int staged_layout(int variant) {
   if (variant > 0) return 0;
-  const bool seq = tma_fits<n, MODE, LayoutSeq>(), wide = tma_fits<n, MODE, LayoutWide>(),
-             one = tma_fits<n, MODE, LayoutOne>();
+  const bool seq = tma_fits<n, MODE, LayoutSeq>(), one = tma_fits<n, MODE, LayoutOne>(),
+             split = tma_fits<n, MODE, LayoutSplit>();
   if (variant == -1 && seq) return -1;
-  if (variant == -2 && wide) return -2;
-  if (variant == -3 && one) return -3;
-  // default: one pencil per thread where it fits, else two
-  return one ? -3 : (seq ? -1 : 0);
+  if (variant == -2 && one) return -2;
+  if (variant == -3 && split) return -3;
+  // default: split pencils where they apply, else one pencil per thread, else two
+  return split ? -3 : (one ? -2 : (seq ? -1 : 0));
 }
 
 template <int n, int MODE>
@@ -149,10 +149,10 @@ cudaError_t launch_pairconv_mode(const PairArgs& args, int variant, cudaStream_t
       if constexpr (tma_fits<n, MODE, LayoutSeq>()) return launch_pairconv_tma<n, MODE, LayoutSeq>(args, stream);
       break;
     case -2:
-      if constexpr (tma_fits<n, MODE, LayoutWide>()) return launch_pairconv_tma<n, MODE, LayoutWide>(args, stream);
+      if constexpr (tma_fits<n, MODE, LayoutOne>()) return launch_pairconv_tma<n, MODE, LayoutOne>(args, stream);
       break;
     case -3:
-      if constexpr (tma_fits<n, MODE, LayoutOne>()) return launch_pairconv_tma<n, MODE, LayoutOne>(args, stream);
+      if constexpr (tma_fits<n, MODE, LayoutSplit>()) return launch_pairconv_tma<n, MODE, LayoutSplit>(args, stream);
       break;
     default: break;
   }

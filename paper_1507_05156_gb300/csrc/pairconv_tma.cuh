@@ -40,16 +40,13 @@ struct StageGeo {
   static constexpr int STAGE_TX = STAGE_ROWS * SP * 8;          // bytes one fill delivers
 };
 
-// Shared and tensor memory of the staged kernel for pencil layout Lay (below).  TMEM columns
-// of one warp: [acc (PPT pencils) | kernel rows (PPT) | owner u_i (PPT)].
+// Shared and tensor memory of the staged kernel for pencil layout Lay (below).
 template <int n, class Lay>
 struct GeoS : StageGeo<n> {
   using G = Geo<n>;
   using SG = StageGeo<n>;
   static constexpr size_t GRIDS_BYTES = ((size_t)G::T * Lay::GRID_CPX * sizeof(float2) + 127) / 128 * 128;
-  static constexpr int TAB = Lay::PPT * G::ROW;
-  static constexpr int OWN = TAB + Lay::PPT * n;
-  static constexpr int COLS_PER_WARP = OWN + Lay::PPT * G::ROW;
+  static constexpr int COLS_PER_WARP = Lay::COLS_PER_WARP;
   static constexpr int TMEM_COLS = pow2_at_least(((Lay::WARPS + 3) / 4) * COLS_PER_WARP);
   static constexpr size_t SMEM_BYTES = GRIDS_BYTES + 2 * (size_t)SG::STAGE_CPX * sizeof(float2);
   // + 128 bytes to align the base at run time; at least enough that a second CTA (which would
@@ -113,16 +110,22 @@ __device__ __forceinline__ void stage_z_inverse_staged(const float2* g, int t, c
 
 // ---------------------------------------------------------------------------------------
 // Pencil layouts of the staged kernel.  A layout says how many pencils each thread owns per
-// stage (PPT), hence the block size, which pencils they are and how the smem grid is laid out;
-// the pipeline is the same.
-//   LayoutSeq:  two pencils per thread (t and t + n^2/2), transformed one after the other,
-//               lanes on consecutive pencils, 64-bit smem accesses in Y and X.
-//   LayoutOne:  one pencil per thread, twice the warps: with n^2 pencils per stage spread over
-//               the four warp schedulers of an SM, the busiest scheduler carries fewer
-//               pencil-passes than with LayoutSeq when n^2 / 128 has a small fractional part
-//               (18^3: 3 instead of 4), and each scheduler has more warps to hide latency.
-//   LayoutWide: two pencils per thread, neighbours in z in stages Y and X, so every smem access
-//               moves both (128 bit) and both are transformed together (ILP).
+// stage (PPT), hence the block size, which pencils they are, and where its TMEM columns sit
+// (relative to the warp's first column trow0); the pipeline is the same.
+//   LayoutSeq:   two pencils per thread (t and t + n^2/2), transformed one after the other.
+//   LayoutOne:   one pencil per thread, twice the warps.  The n^2 pencils of a stage are spread
+//                over the four warp schedulers of the SM; one pencil per thread leaves the
+//                busiest scheduler fewer pencil passes when n^2 / 128 has a small fractional
+//                part (18^3: 3 instead of 4) and gives each scheduler more warps to hide
+//                shared-memory latency.
+//   LayoutSplit: one pencil per thread for the first R = 128 floor(n^2 / 128) pencils (whole
+//                warps, the same count on every scheduler), plus four warps, one per scheduler,
+//                that transform the L = n^2 - R pencils left over with their DFT split over
+//                lanes (below), L / 4 each.  For 20^3 (R = 384, L = 16) this replaces a thirteenth
+//                warp, which gave one scheduler four full pencil passes per stage against three
+//                on the others, by warps whose pass costs a fraction of one and runs beside the
+//                regular ones.
+// TMEM columns of a warp: [acc (PPT pencils) | kernel rows (PPT) | owner u_i (PPT) | extra].
 // ---------------------------------------------------------------------------------------
 
 template <int n, int PPT_>
@@ -134,9 +137,12 @@ struct LayoutLin {
   static constexpr int WARPS = THREADS / 32;
   static constexpr int GRID_CPX = G::GRID_CPX;
   static constexpr bool OK = G::ZFAST_Y == 1 && THREADS <= 1024;
+  static constexpr int TAB = PPT * G::ROW;
+  static constexpr int OWN = TAB + PPT * n;
+  static constexpr int COLS_PER_WARP = OWN + PPT * G::ROW;
   static __device__ __forceinline__ int zg(int t, int ps) { return Pencil<n>(t + ps * TS).zg; }
-  static __device__ __forceinline__ void z_forward(float2* g, int t, bool valid, const float2* stg, uint32_t town) {
-    stage_z_forward_staged<n, PPT>(g, t, valid, stg, town);
+  static __device__ __forceinline__ void z_forward(float2* g, int t, bool valid, const float2* stg, uint32_t trow0) {
+    stage_z_forward_staged<n, PPT>(g, t, valid, stg, trow0 + (uint32_t)OWN);
   }
   static __device__ __forceinline__ void z_inverse(const float2* g, int t, const float2* stg, uint32_t trow0) {
     stage_z_inverse_staged<n, PPT>(g, t, stg, trow0);
@@ -145,12 +151,17 @@ struct LayoutLin {
   static __device__ __forceinline__ void y(float2* g, int t, bool valid) {
     stage_y<n, DIR, PPT>(g, t, valid);
   }
-  static __device__ __forceinline__ void x(float2* g, int t, bool valid, uint32_t ttab, float f) {
-    stage_x<n, PPT>(g, t, valid, ttab, f);
+  static __device__ __forceinline__ void x(float2* g, int t, bool valid, uint32_t trow0, float f) {
+    stage_x<n, PPT>(g, t, valid, trow0 + (uint32_t)TAB, f);
   }
-  static __device__ __forceinline__ void cache_row(int t, uint32_t ttab, const float* vrow, float scale) {
-    cache_kernel_row<n, PPT>(t, ttab, vrow, scale);
+  static __device__ __forceinline__ void cache_row(int t, uint32_t trow0, const float* vrow, float scale) {
+    cache_kernel_row<n, PPT>(t, trow0 + (uint32_t)TAB, vrow, scale);
   }
+  // pencils beyond the regular ones (LayoutSplit): none here
+  static __device__ __forceinline__ bool regular(int) { return true; }
+  static __device__ __forceinline__ void extra_init(int, const float2*, uint32_t) {}
+  static __device__ __forceinline__ void extra_store(int, float2*, uint32_t, bool) {}
+  static __device__ __forceinline__ double extra_dot(int, const float2*, uint32_t) { return 0.0; }
 };
 
 template <int n>
@@ -158,142 +169,276 @@ struct LayoutSeq : LayoutLin<n, 2> {};
 template <int n>
 struct LayoutOne : LayoutLin<n, 1> {};
 
-// (P, Q, Z pairing) of the wide layout: 0 = (a, 2j), (a, 2j+1); 1 = (a, j), (a, j + n/2)
-__host__ __device__ constexpr int wide_cfg(int n, int which) {
-  return n == 4    ? (which == 0 ? 4 : which == 1 ? 20 : 0)
-         : n == 6  ? (which == 0 ? 6 : which == 1 ? 38 : 0)
-         : n == 8  ? (which == 0 ? 10 : which == 1 ? 88 : 1)
-         : n == 10 ? (which == 0 ? 10 : which == 1 ? 106 : 0)
-         : n == 12 ? (which == 0 ? 18 : which == 1 ? 220 : 1)
-         : n == 18 ? (which == 0 ? 18 : which == 1 ? 338 : 1)
-         : n == 20 ? (which == 0 ? 26 : which == 1 ? 532 : 1)
-                   : -1;
+// --- DFT of one pencil split over lanes (prime-factor form, Sec. "Good-Thomas") -------------
+// n = N1 N2 with gcd(N1, N2) = 1.  With posA(a, b) = (N2 a + N1 b) mod n and
+// crt(k1, k2) the k with k = k1 (mod N1), k = k2 (mod N2), the DFT X[crt(k1, k2)] =
+// sum_b w_N2^(b k2) sum_a w_N1^(a k1) x[posA(a, b)] splits into
+//   pass A: for each b (one lane), the N1-point DFT over a, written back to posA(k1, b);
+//   pass B: for each k1 (one lane), the N2-point DFT over b of the values at posA(k1, b),
+//           written to crt(k1, k2).
+// When N2 = 1 (mod N1) the positions a lane reads in pass B are the ones it writes, so every
+// pass works in place on a set of positions no other lane of the pass touches.
+__host__ __device__ constexpr int inv_mod_c(int a, int m) {
+  int x = 1;
+  while ((a * x) % m != 1 % m) ++x;
+  return x;
 }
 
 template <int n>
-struct LayoutWide {
+struct SplitGeo {
+  static constexpr int N1 = pfa_n1(n);
+  static constexpr int N2 = N1 > 0 ? n / N1 : 1;
+  static constexpr int NN = n * n;
+  static constexpr int R = NN / 128 * 128;                 // regular pencils (whole warps)
+  static constexpr int L = NN - R;                         // split pencils
+  static constexpr int PER = L / 4;                        // split pencils per scheduler
+  static constexpr int E1 = N1 > 1 ? (N2 * inv_mod_c(N2 % N1, N1)) % n : 0;
+  static constexpr int E2 = N1 > 1 ? (N1 * inv_mod_c(N1 % N2, N2)) % n : 0;
+  static constexpr bool OK = N1 > 1 && R > 0 && L > 0 && L % 4 == 0 && PER * N2 <= 32 && N2 % N1 == 1 &&
+                             Geo<n>::T == 1 && Geo<n>::ZFAST_Y == 1;
+  static constexpr int HOST0 = R / 32;                     // warps HOST0 .. HOST0 + 3 take them
+  // extra TMEM columns of a hosting lane: owner u_i at its pass-A positions (2 N1 floats),
+  // accumulator there (2 N1), kernel values at its pass-B positions (N2, padded)
+  static constexpr int C_OWN = 0, C_ACC = 2 * N1, C_KER = 4 * N1;
+  static constexpr int KW = N2 <= 4 ? 4 : (N2 <= 6 ? 6 : 8);
+  static constexpr int COLS = (4 * N1 + KW + 7) / 8 * 8;
+  static __host__ __device__ __forceinline__ int posA(int a, int b) {  // a, b < n: one wrap at most
+    const int v = N2 * a + N1 * b;
+    return v >= n ? v - n : v;
+  }
+  static __host__ __device__ __forceinline__ int crt(int k1e1, int k2) {  // k1e1 = (k1 E1) mod n
+    const int v = k1e1 + (k2 * E2) % n;
+    return v >= n ? v - n : v;
+  }
+};
+
+template <int n>
+struct LayoutSplit {
   using G = Geo<n>;
+  using SG = SplitGeo<n>;
   using S = StageGeo<n>;
-  static constexpr int P = wide_cfg(n, 0), Q = wide_cfg(n, 1), ZM = wide_cfg(n, 2);
-  static constexpr int H = n / 2;
-  static constexpr int PPT = 2, TS = G::TS, THREADS = G::THREADS, WARPS = G::WARPS;
-  static constexpr int GRID_CPX = n * (Q > 0 ? Q : 2);
-  static constexpr bool OK = P > 0;
-  // Z-stage pencil ps of thread t: (zx, zy)
-  static __device__ __forceinline__ void zxy(int t, int ps, int& zx, int& zy) {
-    const int a = t / H, j = t - a * H;
-    zx = a;
-    zy = ZM == 0 ? 2 * j + ps : j + ps * H;
-  }
-  static __device__ __forceinline__ int zg(int t, int ps) {
-    int zx, zy;
-    zxy(t, ps, zx, zy);
-    return (zx * n + zy) * n;
-  }
-  static __device__ __forceinline__ void z_forward(float2* g, int t, bool valid, const float2* stg, uint32_t town) {
-#pragma unroll 1
-    for (int ps = 0; ps < 2; ++ps) {
-      int zx, zy;
-      zxy(t, ps, zx, zy);
-      float uo[G::ROW];
-      TmemRow<G::ROW>::load(town + (uint32_t)(ps * G::ROW), uo);
-      const float4* s4 = reinterpret_cast<const float4*>(stg + (zx * n + zy) * S::SP);
-      cpx<float> v[n];
-#pragma unroll
-      for (int e = 0; e < n / 2; ++e) {
-        const float4 w = s4[e];
-        v[2 * e] = {w.x * uo[4 * e] + w.y * uo[4 * e + 1], w.x * uo[4 * e + 1] - w.y * uo[4 * e]};
-        v[2 * e + 1] = {w.z * uo[4 * e + 2] + w.w * uo[4 * e + 3], w.z * uo[4 * e + 3] - w.w * uo[4 * e + 2]};
-      }
-      fft<n, -1, float>(v);
-      if (valid) store_s<n, 2>(v, g, zx * Q + zy * P, 1);
+  static constexpr int PPT = 1;
+  static constexpr int TS = SG::OK ? SG::R + 128 : G::NN;
+  static constexpr int THREADS = TS, WARPS = TS / 32;
+  static constexpr int GRID_CPX = G::GRID_CPX;
+  static constexpr bool OK = SG::OK && THREADS <= 1024;
+  static constexpr int TAB = G::ROW;
+  static constexpr int OWN = TAB + n;
+  static constexpr int EXTRA = OWN + G::ROW;
+  static constexpr int COLS_PER_WARP = EXTRA + SG::COLS;
+  using Reg = LayoutLin<n, 1>;  // the regular pencils 0 .. R-1 (pencil = thread)
+  static __device__ __forceinline__ bool regular(int t) { return t < SG::R; }
+
+  // role of this lane in the hosting warp: s = scheduler, A: (pencil, b), B: (pencil, k1)
+  struct Roles {
+    bool host, a_on, b_on;
+    int pa, b, pb, k1, k1e1;
+    __device__ __forceinline__ explicit Roles(int t) {
+      const int warp = t >> 5, lane = t & 31;
+      host = warp >= SG::HOST0;
+      const int first = SG::R + (warp - SG::HOST0) * SG::PER;
+      a_on = host && lane < SG::PER * SG::N2;
+      b_on = host && lane < SG::PER * SG::N1;
+      pa = first + lane / SG::N2;
+      b = lane % SG::N2;
+      pb = first + lane / SG::N1;
+      k1 = lane % SG::N1;
+      k1e1 = (k1 * SG::E1) % n;
     }
-  }
-  static __device__ __forceinline__ void z_inverse(const float2* g, int t, const float2* stg, uint32_t trow0) {
-#pragma unroll 1
-    for (int ps = 0; ps < 2; ++ps) {
-      int zx, zy;
-      zxy(t, ps, zx, zy);
-      cpx<float> v[n];
-      load_s<n, 2>(v, g, zx * Q + zy * P, 1);
-      fft<n, +1, float>(v);
-      float acc[G::ROW];
-      const uint32_t trow = trow0 + (uint32_t)(ps * G::ROW);
-      TmemRow<G::ROW>::load(trow, acc);
-      const float4* s4 = reinterpret_cast<const float4*>(stg + (zx * n + zy) * S::SP);
+  };
+
+  template <int DIR>
+  static __device__ __forceinline__ void pass_a(float2* g, int base, int stride, int b) {
+    cpx<float> v[SG::N1];
 #pragma unroll
-      for (int e = 0; e < n / 2; ++e) {
-        const float4 w = s4[e];
-        float* a = acc + 4 * e;
-        a[0] = fmaf(w.x, v[2 * e].x, fmaf(-w.y, v[2 * e].y, a[0]));
-        a[1] = fmaf(w.x, v[2 * e].y, fmaf(w.y, v[2 * e].x, a[1]));
-        a[2] = fmaf(w.z, v[2 * e + 1].x, fmaf(-w.w, v[2 * e + 1].y, a[2]));
-        a[3] = fmaf(w.z, v[2 * e + 1].y, fmaf(w.w, v[2 * e + 1].x, a[3]));
-      }
-      TmemRow<G::ROW>::store(trow, acc);
+    for (int a = 0; a < SG::N1; ++a) {
+      const float2 w = g[base + SG::posA(a, b) * stride];
+      v[a] = {w.x, w.y};
     }
+    fft<SG::N1, DIR, float>(v);
+#pragma unroll
+    for (int a = 0; a < SG::N1; ++a) g[base + SG::posA(a, b) * stride] = make_float2(v[a].x, v[a].y);
   }
-  // Y: pencils (x = t / H, z = 2 (t % H) + {0, 1}); one 128-bit access per element holds both
+  template <int DIR>
+  static __device__ __forceinline__ void pass_b(float2* g, int base, int stride, int k1, int k1e1) {
+    cpx<float> v[SG::N2];
+#pragma unroll
+    for (int b = 0; b < SG::N2; ++b) {
+      const float2 w = g[base + SG::posA(k1, b) * stride];
+      v[b] = {w.x, w.y};
+    }
+    fft<SG::N2, DIR, float>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < SG::N2; ++k2) g[base + SG::crt(k1e1, k2) * stride] = make_float2(v[k2].x, v[k2].y);
+  }
+
+  static __device__ __forceinline__ int zg(int t, int ps) { return Reg::zg(t, ps); }
+
+  static __device__ __forceinline__ void z_forward(float2* g, int t, bool valid, const float2* stg, uint32_t trow0) {
+    const Roles r(t);
+    if (r.host) {  // warp-uniform
+      float uo[2 * SG::N1];
+      TmemRow<2 * SG::N1>::load(trow0 + (uint32_t)(EXTRA + SG::C_OWN), uo);
+      if (r.a_on) {
+        const Pencil<n> pc(r.pa);
+        const float2* srow = stg + (pc.zg / n) * S::SP;
+        cpx<float> v[SG::N1];
+#pragma unroll
+        for (int a = 0; a < SG::N1; ++a) {
+          const float2 w = srow[SG::posA(a, r.b)];
+          v[a] = {w.x * uo[2 * a] + w.y * uo[2 * a + 1], w.x * uo[2 * a + 1] - w.y * uo[2 * a]};
+        }
+        fft<SG::N1, -1, float>(v);
+#pragma unroll
+        for (int a = 0; a < SG::N1; ++a) g[pc.zs + SG::posA(a, r.b)] = make_float2(v[a].x, v[a].y);
+      }
+      __syncwarp();
+      if (r.b_on) pass_b<-1>(g, Pencil<n>(r.pb).zs, 1, r.k1, r.k1e1);
+    }
+    if (regular(t)) Reg::z_forward(g, t, valid, stg, trow0);
+  }
+
   template <int DIR>
   static __device__ __forceinline__ void y(float2* g, int t, bool valid) {
-    const int ya = t / H, yp = t - ya * H;
-    const int base = ya * Q + 2 * yp;
-    cpx<float> a[n], b[n];
-#pragma unroll
-    for (int e = 0; e < n; ++e) {
-      const float4 w = *reinterpret_cast<const float4*>(g + base + e * P);
-      a[e] = {w.x, w.y};
-      b[e] = {w.z, w.w};
+    const Roles r(t);
+    if (r.host) {
+      if (r.a_on) pass_a<DIR>(g, Pencil<n>(r.pa).ys, G::P, r.b);
+      __syncwarp();
+      if (r.b_on) pass_b<DIR>(g, Pencil<n>(r.pb).ys, G::P, r.k1, r.k1e1);
     }
-    fft<n, DIR, float>(a);
-    fft<n, DIR, float>(b);
-    if (valid) {
+    if (regular(t)) Reg::template y<DIR>(g, t, valid);
+  }
+
+  static __device__ __forceinline__ void x(float2* g, int t, bool valid, uint32_t trow0, float f) {
+    const Roles r(t);
+    if (r.host) {
+      float kv[SG::KW];
+      TmemRow<SG::KW>::load(trow0 + (uint32_t)(EXTRA + SG::C_KER), kv);
+      const int xa = Pencil<n>(r.pa).xs;
+      if (r.a_on) pass_a<-1>(g, xa, G::Q, r.b);
+      __syncwarp();
+      if (r.b_on) {
+        const int base = Pencil<n>(r.pb).xs;
+        cpx<float> v[SG::N2];
 #pragma unroll
-      for (int e = 0; e < n; ++e) *reinterpret_cast<float4*>(g + base + e * P) = make_float4(a[e].x, a[e].y, b[e].x, b[e].y);
+        for (int b = 0; b < SG::N2; ++b) {
+          const float2 w = g[base + SG::posA(r.k1, b) * G::Q];
+          v[b] = {w.x, w.y};
+        }
+        fft<SG::N2, -1, float>(v);  // v[k2] = X[crt(k1, k2)]
+#pragma unroll
+        for (int k2 = 0; k2 < SG::N2; ++k2) {
+          const float w = kv[k2] * f;
+          v[k2].x *= w;
+          v[k2].y *= w;
+        }
+        fft<SG::N2, +1, float>(v);  // back to b, still at fixed k1
+#pragma unroll
+        for (int b = 0; b < SG::N2; ++b) g[base + SG::posA(r.k1, b) * G::Q] = make_float2(v[b].x, v[b].y);
+      }
+      __syncwarp();
+      if (r.a_on) pass_a<+1>(g, xa, G::Q, r.b);
+    }
+    if (regular(t)) Reg::x(g, t, valid, trow0, f);
+  }
+
+  static __device__ __forceinline__ void z_inverse(const float2* g_, int t, const float2* stg, uint32_t trow0) {
+    const Roles r(t);
+    if (r.host) {
+      float2* g = const_cast<float2*>(g_);  // the split pencils pass through the grid in place
+      if (r.b_on) {
+        // natural order -> (k1, b): inverse N2-point DFTs first, in place on the lane's set
+        const int base = Pencil<n>(r.pb).zs;
+        cpx<float> v[SG::N2];
+#pragma unroll
+        for (int k2 = 0; k2 < SG::N2; ++k2) {
+          const float2 w = g[base + SG::crt(r.k1e1, k2)];
+          v[k2] = {w.x, w.y};
+        }
+        fft<SG::N2, +1, float>(v);
+#pragma unroll
+        for (int b = 0; b < SG::N2; ++b) g[base + SG::posA(r.k1, b)] = make_float2(v[b].x, v[b].y);
+      }
+      __syncwarp();
+      float acc[2 * SG::N1];
+      const uint32_t tacc = trow0 + (uint32_t)(EXTRA + SG::C_ACC);
+      TmemRow<2 * SG::N1>::load(tacc, acc);
+      if (r.a_on) {
+        const Pencil<n> pc(r.pa);
+        cpx<float> v[SG::N1];
+#pragma unroll
+        for (int a = 0; a < SG::N1; ++a) {
+          const float2 w = g[pc.zs + SG::posA(a, r.b)];
+          v[a] = {w.x, w.y};
+        }
+        fft<SG::N1, +1, float>(v);  // v[a] = phi at posA(a, b)
+        const float2* srow = stg + (pc.zg / n) * S::SP;
+#pragma unroll
+        for (int a = 0; a < SG::N1; ++a) {
+          const float2 w = srow[SG::posA(a, r.b)];
+          acc[2 * a] = fmaf(w.x, v[a].x, fmaf(-w.y, v[a].y, acc[2 * a]));
+          acc[2 * a + 1] = fmaf(w.x, v[a].y, fmaf(w.y, v[a].x, acc[2 * a + 1]));
+        }
+      }
+      TmemRow<2 * SG::N1>::store(tacc, acc);
+      __syncwarp();  // the next pair's Z forward rewrites these positions from other lanes
+    }
+    if (regular(t)) Reg::z_inverse(g_, t, stg, trow0);
+  }
+
+  static __device__ __forceinline__ void cache_row(int t, uint32_t trow0, const float* __restrict__ vrow, float scale) {
+    const Roles r(t);
+    if (r.host) {
+      float kv[SG::KW];
+#pragma unroll
+      for (int k2 = 0; k2 < SG::KW; ++k2)
+        kv[k2] = (r.b_on && k2 < SG::N2) ? __ldg(vrow + SG::crt(r.k1e1, k2) * G::NN + r.pb) * scale : 0.f;
+      TmemRow<SG::KW>::store(trow0 + (uint32_t)(EXTRA + SG::C_KER), kv);
+    }
+    if (regular(t)) Reg::cache_row(t, trow0, vrow, scale);
+  }
+
+  static __device__ __forceinline__ void extra_init(int t, const float2* own, uint32_t trow0) {
+    const Roles r(t);
+    if (!r.host) return;
+    float w[2 * SG::N1], z[2 * SG::N1];
+    const int zg0 = Pencil<n>(r.pa).zg;
+#pragma unroll
+    for (int a = 0; a < SG::N1; ++a) {
+      const float2 u = r.a_on ? __ldg(own + zg0 + SG::posA(a, r.b)) : make_float2(0.f, 0.f);
+      w[2 * a] = u.x;
+      w[2 * a + 1] = u.y;
+      z[2 * a] = z[2 * a + 1] = 0.f;
+    }
+    TmemRow<2 * SG::N1>::store(trow0 + (uint32_t)(EXTRA + SG::C_OWN), w);
+    TmemRow<2 * SG::N1>::store(trow0 + (uint32_t)(EXTRA + SG::C_ACC), z);
+  }
+  static __device__ __forceinline__ void extra_store(int t, float2* obase, uint32_t trow0, bool active) {
+    const Roles r(t);
+    if (!r.host) return;
+    float acc[2 * SG::N1];
+    TmemRow<2 * SG::N1>::load(trow0 + (uint32_t)(EXTRA + SG::C_ACC), acc);
+    if (active && r.a_on) {
+      const int zg0 = Pencil<n>(r.pa).zg;
+#pragma unroll
+      for (int a = 0; a < SG::N1; ++a) obase[zg0 + SG::posA(a, r.b)] = make_float2(acc[2 * a], acc[2 * a + 1]);
     }
   }
-  // X: pencils (y = t / H, z = 2 (t % H) + {0, 1}); kernel rows from the TMEM cache
-  static __device__ __forceinline__ void x(float2* g, int t, bool valid, uint32_t ttab, float f) {
-    const int ya = t / H, yp = t - ya * H;
-    const int base = ya * P + 2 * yp;
-    float ta[n], tb[n];
-    TmemRow<n>::load(ttab, ta);
-    TmemRow<n>::load(ttab + (uint32_t)n, tb);
-    cpx<float> a[n], b[n];
+  static __device__ __forceinline__ double extra_dot(int t, const float2* lhs, uint32_t trow0) {
+    const Roles r(t);
+    if (!r.host) return 0.0;
+    float acc[2 * SG::N1];
+    TmemRow<2 * SG::N1>::load(trow0 + (uint32_t)(EXTRA + SG::C_ACC), acc);
+    double d = 0.0;
+    if (r.a_on) {
+      const int zg0 = Pencil<n>(r.pa).zg;
 #pragma unroll
-    for (int e = 0; e < n; ++e) {
-      const float4 w = *reinterpret_cast<const float4*>(g + base + e * Q);
-      a[e] = {w.x, w.y};
-      b[e] = {w.z, w.w};
+      for (int a = 0; a < SG::N1; ++a) {
+        const float2 w = __ldg(lhs + zg0 + SG::posA(a, r.b));
+        d += (double)w.x * (double)acc[2 * a] + (double)w.y * (double)acc[2 * a + 1];
+      }
     }
-    fft<n, -1, float>(a);
-    fft<n, -1, float>(b);
-#pragma unroll
-    for (int e = 0; e < n; ++e) {
-      const float wa = ta[e] * f, wb = tb[e] * f;
-      a[e].x *= wa;
-      a[e].y *= wa;
-      b[e].x *= wb;
-      b[e].y *= wb;
-    }
-    fft<n, +1, float>(a);
-    fft<n, +1, float>(b);
-    if (valid) {
-#pragma unroll
-      for (int e = 0; e < n; ++e) *reinterpret_cast<float4*>(g + base + e * Q) = make_float4(a[e].x, a[e].y, b[e].x, b[e].y);
-    }
-  }
-  static __device__ __forceinline__ void cache_row(int t, uint32_t ttab, const float* __restrict__ vrow, float scale) {
-    const int ya = t / H, yp = t - ya * H;
-    float ta[n], tb[n];
-#pragma unroll
-    for (int e = 0; e < n; ++e) {
-      const float2 v = __ldg(reinterpret_cast<const float2*>(vrow + e * G::NN + ya * n + 2 * yp));
-      ta[e] = v.x * scale;
-      tb[e] = v.y * scale;
-    }
-    TmemRow<n>::store(ttab, ta);
-    TmemRow<n>::store(ttab + (uint32_t)n, tb);
+    return d;
   }
 };
 
@@ -315,7 +460,7 @@ __device__ __forceinline__ int next_partner(const float* occ_sh, const PairArgs&
 }
 
 // tmap: the partner array as rows of z-pencils, box {2 SP floats, BR rows}.  L: the pencil
-// layout (LayoutSeq or LayoutWide).
+// layout (LayoutSeq, LayoutOne or LayoutSplit).
 template <int n, int MODE, template <int> class L>
 __global__ void __launch_bounds__(L<n>::THREADS, 1)
     pairconv_tma_kernel(const PairArgs args, const __grid_constant__ CUtensorMap tmap) {
@@ -362,8 +507,7 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
   tmem_fence_after_sync();
   const uint32_t tbase = tmem_base_sh;
   const uint32_t trow0 = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * S::COLS_PER_WARP);
-  const uint32_t ttab = trow0 + (uint32_t)S::TAB;
-  const uint32_t town = trow0 + (uint32_t)S::OWN;
+  const uint32_t town = trow0 + (uint32_t)Lay::OWN;
 
   const int per_split = args.nk * args.ntiles;
   const int split = blockIdx.x / per_split;
@@ -400,8 +544,9 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
   if (warp == 0 && q < npairs && args.inject != 1) fill(q, 0);
 
   // owner orbital into TMEM, accumulators to zero
+  const bool reg = Lay::regular(t);  // warp-uniform
 #pragma unroll 1
-  for (int ps = 0; ps < Lay::PPT; ++ps) {
+  for (int ps = 0; ps < (reg ? Lay::PPT : 0); ++ps) {
     cpx<float> w[n];
     load_pencil_global<n>(w, own + Lay::zg(t, ps));
     float r[G::ROW];
@@ -415,6 +560,7 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
     for (int e = 0; e < G::ROW; ++e) r[e] = 0.f;
     TmemRow<G::ROW>::store(trow0 + (uint32_t)(ps * G::ROW), r);
   }
+  Lay::extra_init(t, own, trow0);
 
   uint32_t phase0 = 0, phase1 = 0;
   int buf = 0;
@@ -424,7 +570,7 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
     const float f = item_occ(occ_sh, args, kp_begin, q);
     if (kp != cur_kp) {
       const int qrow = args.qidx[k * args.nk + kp];
-      Lay::cache_row(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
+      Lay::cache_row(t, trow0, args.vtab + (size_t)qrow * G::N, args.scale);
       cur_kp = kp;
     }
     // partner u_j has landed in stage[buf]
@@ -437,7 +583,7 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
     }
     if (buf) phase1 ^= 1u; else phase0 ^= 1u;
     const float2* stg = stage + buf * S::STAGE_CPX;
-    Lay::z_forward(g, t, valid, stg, town);
+    Lay::z_forward(g, t, valid, stg, trow0);
     __syncthreads();
     // every thread is past its last read of stage[buf ^ 1]: refill it with the next partner
     const int qn = next_partner(occ_sh, args, kp_begin, q + 1, npairs);
@@ -447,7 +593,7 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
     }
     Lay::template y<-1>(g, t, valid);
     __syncthreads();
-    Lay::x(g, t, valid, ttab, f);
+    Lay::x(g, t, valid, trow0, f);
     __syncthreads();
     Lay::template y<+1>(g, t, valid);
     __syncthreads();
@@ -465,7 +611,7 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
   if constexpr (MODE == MODE_APPLY) {
     float2* obase = args.out + split * args.split_stride + ((size_t)k * args.n_own + bandc) * G::N;
 #pragma unroll 1
-    for (int ps = 0; ps < Lay::PPT; ++ps) {
+    for (int ps = 0; ps < (reg ? Lay::PPT : 0); ++ps) {
       float acc[G::ROW];
       TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
       if (active) {
@@ -474,11 +620,12 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
         for (int e = 0; e < n / 2; ++e) o[e] = make_float4(acc[4 * e], acc[4 * e + 1], acc[4 * e + 2], acc[4 * e + 3]);
       }
     }
+    Lay::extra_store(t, obase, trow0, active);
   } else {
     const float2* lhs = (MODE == MODE_ENERGY) ? own : args.part2 + ((size_t)k * args.n_own + bandc) * G::N;
     double d = 0.0;
 #pragma unroll 1
-    for (int ps = 0; ps < Lay::PPT; ++ps) {
+    for (int ps = 0; ps < (reg ? Lay::PPT : 0); ++ps) {
       float acc[G::ROW];
       TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
       cpx<float> w[n];
@@ -486,6 +633,7 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
 #pragma unroll
       for (int e = 0; e < n; ++e) d += (double)w[e].x * (double)acc[2 * e] + (double)w[e].y * (double)acc[2 * e + 1];
     }
+    d += Lay::extra_dot(t, lhs, trow0);
     __syncthreads();
     double* red = reinterpret_cast<double*>(sbase);
     red[tid] = valid ? d : 0.0;
