@@ -35,6 +35,10 @@ Readings (where the paper is silent, garbled or at odds with itself):
 6. Exchange energy (the Fock part of E_xc in Eq. "Eex01"):
       E_x = 1/2 g_s (1/N_k) sum_k sum_{i occ} f_{i,k} dV sum_r Re[conj(u_{i,k}) (V_x u)_{i,k}],
    with the targets equal to the occupied set.
+7. Down-sampling (Sec. II C, after Eq. "Fock-DS"): the sum over the occupied orbitals'
+   k-points k' runs over a sub-mesh of N_q of the N_k points of the orbital mesh, with the
+   uniform weight 1/N_q in place of 1/N_k ("kocc" below: the indices of the sampled points;
+   None = all).  The targets keep the full mesh.
 
 Every function below works in float64 / complex128.
 """
@@ -135,16 +139,27 @@ def _as_grid(u: np.ndarray, grid) -> np.ndarray:
     return u.reshape(u.shape[:2] + tuple(int(g) for g in grid)).astype(np.complex128, copy=False)
 
 
+def _sampled(kocc, nk):
+    """k' indices of the Fock sum (reading 7): all nk points, or the sampled sub-mesh."""
+    if kocc is None:
+        return list(range(nk))
+    kocc = [int(k) for k in kocc]
+    if not kocc or len(set(kocc)) != len(kocc) or min(kocc) < 0 or max(kocc) >= nk:
+        raise ValueError("kocc must list distinct k-point indices")
+    return kocc
+
+
 def fock_apply(u_occ, occ, u_tgt, kpts, lattice, grid, omega, alpha,
                targets: Optional[Sequence[Tuple[int, int]]] = None,
-               kernel: str = "value") -> np.ndarray:
-    """(V_x u)_{i,k} for every target, reading 4.
+               kernel: str = "value", kocc: Optional[Sequence[int]] = None) -> np.ndarray:
+    """(V_x u)_{i,k} for every target, reading 4 (reading 7 when ``kocc`` is given).
 
     u_occ [nk][n_occ][N1][N2][N3], occ [nk][n_occ], u_tgt [nk][n_tgt][...],
     kpts [nk][3] Cartesian.  ``targets`` optionally restricts the output to a list
     of (k, i); the result is then [len(targets)][N1][N2][N3], otherwise it is
     [nk][n_tgt][N1][N2][N3].  ``kernel='domega'``
-    replaces v~ by d v~/d omega (the omega derivative of the operator).
+    replaces v~ by d v~/d omega (the omega derivative of the operator).  ``kocc`` lists the
+    k-points whose occupied orbitals enter the sum (weight 1 / len(kocc)).
     """
     grid = tuple(int(g) for g in grid)
     u_occ = _as_grid(u_occ, grid)
@@ -152,6 +167,7 @@ def fock_apply(u_occ, occ, u_tgt, kpts, lattice, grid, omega, alpha,
     occ = np.asarray(occ, dtype=np.float64)
     kpts = np.asarray(kpts, dtype=np.float64)
     nk = kpts.shape[0]
+    kps = _sampled(kocc, nk)
     full = targets is None
     if full:
         targets = [(k, i) for k in range(nk) for i in range(u_tgt.shape[1])]
@@ -163,7 +179,7 @@ def fock_apply(u_occ, occ, u_tgt, kpts, lattice, grid, omega, alpha,
         rows = [t for t, _ in items]
         u_i = u_tgt[k, [i for _, i in items]]                  # [T][grid]
         acc = np.zeros_like(u_i)
-        for kp in range(nk):
+        for kp in kps:
             q = kpts[k] - kpts[kp]
             v = kernel_on_grid(grid, lattice, q, omega, derivative=(kernel == "domega"))
             u_j = u_occ[kp]                                    # [J][grid]
@@ -171,18 +187,20 @@ def fock_apply(u_occ, occ, u_tgt, kpts, lattice, grid, omega, alpha,
             rt = forward_transform(rho) * v
             phi = inverse_transform(rt)
             acc += np.einsum("j,j...,jt...->t...", occ[kp], u_j, phi)
-        out[rows] = -alpha / nk * acc
+        out[rows] = -alpha / len(kps) * acc
     if full:
         return out.reshape(u_tgt.shape)
     return out
 
 
-def exchange_energy(u_occ, occ, kpts, lattice, grid, omega, alpha, spin_degeneracy=2.0) -> float:
-    """E_x of reading 6, with the targets equal to the occupied orbitals."""
+def exchange_energy(u_occ, occ, kpts, lattice, grid, omega, alpha, spin_degeneracy=2.0,
+                    kocc: Optional[Sequence[int]] = None) -> float:
+    """E_x of reading 6, with the targets equal to the occupied orbitals (all N_k points);
+    ``kocc`` down-samples the Fock sum inside V_x (reading 7)."""
     grid = tuple(int(g) for g in grid)
     u_occ = _as_grid(u_occ, grid)
     nk, n_occ = u_occ.shape[:2]
-    vx = fock_apply(u_occ, occ, u_occ, kpts, lattice, grid, omega, alpha)
+    vx = fock_apply(u_occ, occ, u_occ, kpts, lattice, grid, omega, alpha, kocc=kocc)
     dV = cell_volume(lattice) / np.prod(grid)
     e = 0.0
     for k in range(nk):
@@ -191,7 +209,8 @@ def exchange_energy(u_occ, occ, kpts, lattice, grid, omega, alpha, spin_degenera
     return 0.5 * spin_degeneracy * e / nk
 
 
-def fock_apply_vjp(u_occ, occ, u_tgt, grad_vx, kpts, lattice, grid, omega, alpha):
+def fock_apply_vjp(u_occ, occ, u_tgt, grad_vx, kpts, lattice, grid, omega, alpha,
+                   kocc: Optional[Sequence[int]] = None):
     """Vector-Jacobian product of y = V_x[u_occ] u_tgt (PyTorch complex convention).
 
     With ybar = grad_vx, c_j = alpha f_{j,k'} / N_k, K_q = F^-1 diag(v~(|G+q|)) F,
@@ -203,7 +222,9 @@ def fock_apply_vjp(u_occ, occ, u_tgt, grad_vx, kpts, lattice, grid, omega, alpha
                         K'_q with v~ replaced by d v~ / d omega.
 
     For a real-linear map dy = A dz + B conj(dz) the gradient is A^H ybar + B^T conj(ybar);
-    K_q is Hermitian because v~ is real.  Returns (g_occ, g_tgt, g_omega).
+    K_q is Hermitian because v~ is real.  With ``kocc`` (reading 7) k' runs over the sampled
+    points, N_k becomes N_q in c_j, and the rows of g_occ at k-points outside the sub-mesh
+    are zero.  Returns (g_occ, g_tgt, g_omega).
     """
     grid = tuple(int(g) for g in grid)
     u_occ = _as_grid(u_occ, grid)
@@ -212,18 +233,19 @@ def fock_apply_vjp(u_occ, occ, u_tgt, grad_vx, kpts, lattice, grid, omega, alpha
     occ = np.asarray(occ, dtype=np.float64)
     kpts = np.asarray(kpts, dtype=np.float64)
     nk = kpts.shape[0]
+    kps = _sampled(kocc, nk)
     g_occ = np.zeros_like(u_occ)
     g_tgt = np.zeros_like(u_tgt)
     g_omega = 0.0
     for k in range(nk):
         u_i = u_tgt[k]
         y_i = ybar[k]
-        for kp in range(nk):
+        for kp in kps:
             q = kpts[k] - kpts[kp]
             v = kernel_on_grid(grid, lattice, q, omega)
             dv = kernel_on_grid(grid, lattice, q, omega, derivative=True)
             u_j = u_occ[kp]
-            c = alpha * occ[kp] / nk                                 # [J]
+            c = alpha * occ[kp] / len(kps)                           # [J]
             rho_t = forward_transform(pair_density(u_j[:, None], u_i[None, :]))
             sig_t = forward_transform(pair_density(u_j[:, None], y_i[None, :]))
             phi = inverse_transform(rho_t * v)                        # [J][T][grid]
@@ -252,8 +274,10 @@ def periodic_kernel_realspace(grid, lattice, q, omega) -> np.ndarray:
     return (np.exp(1j * phase.sum(-1)) @ v).reshape(grid)
 
 
-def fock_apply_realspace(u_occ, occ, u_tgt, kpts, lattice, grid, omega, alpha) -> np.ndarray:
-    """O(N^2) double sum  -alpha/N_k sum_{k',j} f u_j(r) (1/N) sum_{r'} K_q(r-r') rho_ji(r')."""
+def fock_apply_realspace(u_occ, occ, u_tgt, kpts, lattice, grid, omega, alpha,
+                         kocc: Optional[Sequence[int]] = None) -> np.ndarray:
+    """O(N^2) double sum  -alpha/N_k sum_{k',j} f u_j(r) (1/N) sum_{r'} K_q(r-r') rho_ji(r')
+    (N_k -> N_q and k' over the sub-mesh with ``kocc``, reading 7)."""
     grid = tuple(int(g) for g in grid)
     u_occ = _as_grid(u_occ, grid)
     u_tgt = _as_grid(u_tgt, grid)
@@ -261,16 +285,17 @@ def fock_apply_realspace(u_occ, occ, u_tgt, kpts, lattice, grid, omega, alpha) -
     N = int(np.prod(grid))
     idx = np.stack(np.meshgrid(*(np.arange(n) for n in grid), indexing="ij"), -1).reshape(-1, 3)
     diff = (idx[:, None, :] - idx[None, :, :]) % np.array(grid)       # [N][N][3]
+    kps = _sampled(kocc, nk)
     out = np.zeros((nk, n_tgt, N), dtype=np.complex128)
     for k in range(nk):
-        for kp in range(nk):
+        for kp in kps:
             K = periodic_kernel_realspace(grid, lattice, kpts[k] - kpts[kp], omega)
             M = K[diff[..., 0], diff[..., 1], diff[..., 2]] / N          # [N][N]
             for i in range(n_tgt):
                 ui = u_tgt[k, i].reshape(-1)
                 for j in range(u_occ.shape[1]):
                     uj = u_occ[kp, j].reshape(-1)
-                    out[k, i] += -alpha / nk * occ[kp][j] * uj * (M @ (np.conj(uj) * ui))
+                    out[k, i] += -alpha / len(kps) * occ[kp][j] * uj * (M @ (np.conj(uj) * ui))
     return out.reshape((nk, n_tgt) + grid)
 
 

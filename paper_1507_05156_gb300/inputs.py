@@ -68,6 +68,21 @@ def monkhorst_pack(n: tuple, lattice: np.ndarray) -> np.ndarray:
     return np.array(pts, dtype=np.float64)
 
 
+def monkhorst_pack_subset(n: tuple, m: tuple) -> np.ndarray:
+    """Indices, in the ordering of monkhorst_pack(n), of the points of the coarser mesh
+    monkhorst_pack(m) (the q-point sub-mesh of the down-sampled Fock sum).  Each n_d must be
+    an odd multiple s_d of m_d, which makes the coarse mesh an exact subset: along axis d the
+    coarse points are the fine points r = s_d r' + (s_d - 1)/2 (0-based)."""
+    axes = []
+    for nd, md in zip(n, m):
+        if md < 1 or nd % md or (nd // md) % 2 == 0:
+            raise ValueError("each fine mesh side must be an odd multiple of the coarse one")
+        s = nd // md
+        axes.append([s * r + (s - 1) // 2 for r in range(md)])
+    return np.array([(r1 * n[1] + r2) * n[2] + r3 for r1 in axes[0] for r2 in axes[1] for r3 in axes[2]],
+                    dtype=np.int64)
+
+
 def _fft_order(nd: int) -> np.ndarray:
     # integer frequency of array index 0..nd-1 (numpy fftfreq order)
     return np.fft.fftfreq(nd, d=1.0 / nd).round().astype(np.int64)

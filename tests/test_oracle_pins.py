@@ -294,3 +294,102 @@ def test_generated_orbitals_orthonormal():
     u = c.u_occ.reshape(c.nk, c.n_occ, -1)
     S = dV * np.einsum("kan,kbn->kab", u.conj(), u)
     np.testing.assert_allclose(S, np.broadcast_to(np.eye(c.n_occ), S.shape), atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Down-sampled Fock sum (Sec. II C after Eq. "Fock-DS"): k' over a q-point sub-mesh, 1/N_q
+# ---------------------------------------------------------------------------
+
+def test_monkhorst_pack_submesh_is_a_subset():
+    A = TRICLINIC
+    for n, m in (((12, 12, 12), (4, 4, 4)), ((6, 3, 9), (2, 1, 3)), ((3, 3, 3), (1, 1, 1))):
+        idx = inputs.monkhorst_pack_subset(n, m)
+        np.testing.assert_allclose(inputs.monkhorst_pack(n, A)[idx], inputs.monkhorst_pack(m, A), atol=1e-13)
+    with pytest.raises(ValueError):
+        inputs.monkhorst_pack_subset((4, 4, 4), (2, 2, 2))  # even factor: not a subset
+
+
+def test_downsampled_plane_wave_closed_form():
+    """One plane wave per k-point: V_x u_i = -alpha/(N_q Omega) sum_{k' in S} f_k' v~(|G_a - G_b + k - k'|) u_i,
+    evaluated term by term in 50-digit arithmetic, for a strict sub-mesh S with unequal f."""
+    grid = (5, 4, 6)
+    A = TRICLINIC
+    Om = abs(np.linalg.det(A))
+    b = 2 * np.pi * np.linalg.inv(A).T
+    r = _positions(grid, A)
+    kpts = np.array([[0.05, -0.11, 0.02], [-0.2, 0.07, 0.13], [0.11, 0.16, -0.09], [0.0, -0.05, 0.21]])
+    omega, alpha = 0.23, 0.25
+    Ga = 1 * b[0] - 1 * b[1] + 1 * b[2]   # G_a - G_b = (1, -1, 2): inside the 5 x 4 x 6 box
+    Gb = 0 * b[0] + 0 * b[1] - 1 * b[2]
+    ua = np.exp(1j * (r @ Ga)) / np.sqrt(Om)
+    ub = np.exp(1j * (r @ Gb)) / np.sqrt(Om)
+    u_tgt = np.broadcast_to(ua, (4, 1) + grid).copy()
+    u_occ = np.broadcast_to(ub, (4, 1) + grid).copy()
+    occ = np.array([[0.9], [0.3], [0.6], [1.0]])
+    kocc = [3, 1, 2]
+    out = oracle.fock_apply(u_occ, occ, u_tgt, kpts, A, grid, omega, alpha, kocc=kocc)
+    for k in range(4):
+        s = 0.0
+        for kp in kocc:
+            g = Ga - Gb + kpts[k] - kpts[kp]
+            s += occ[kp, 0] * _vtilde_mp(float(g @ g), omega)
+        expect = -alpha / (len(kocc) * Om) * s * ua
+        np.testing.assert_allclose(out[k, 0], expect, rtol=0, atol=1e-13 * np.abs(expect).max())
+
+
+def test_downsampled_fft_form_equals_realspace_double_sum():
+    grid = (3, 4, 3)
+    kpts = np.array([[0.0, 0.0, 0.0], [0.21, -0.1, 0.05], [-0.13, 0.17, 0.09]])
+    u_occ = _small_cell(41, grid, kpts, 2)
+    u_tgt = _small_cell(42, grid, kpts, 2)
+    occ = np.array([[1.0, 0.5], [0.8, 0.2], [0.3, 1.0]])
+    kocc = [2, 0]
+    a = oracle.fock_apply(u_occ, occ, u_tgt, kpts, TRICLINIC, grid, 0.27, 0.25, kocc=kocc)
+    b = oracle.fock_apply_realspace(u_occ, occ, u_tgt, kpts, TRICLINIC, grid, 0.27, 0.25, kocc=kocc)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    # the full sub-mesh is the undown-sampled operator
+    full = oracle.fock_apply(u_occ, occ, u_tgt, kpts, TRICLINIC, grid, 0.27, 0.25)
+    np.testing.assert_array_equal(oracle.fock_apply(u_occ, occ, u_tgt, kpts, TRICLINIC, grid, 0.27, 0.25,
+                                                    kocc=[0, 1, 2]), full)
+
+
+def test_downsampled_hermitian_negative_and_vjp_by_finite_differences():
+    grid = (4, 3, 4)
+    kpts = np.array([[0.0, 0.0, 0.0], [0.15, -0.1, 0.2], [-0.07, 0.12, -0.16]])
+    kocc = [1, 2]
+    u_occ = _small_cell(51, grid, kpts, 2)
+    occ = np.array([[1.0, 0.7], [0.4, 1.0], [0.9, 0.6]])
+    omega, alpha = 0.25, 0.25
+    # Hermitian and negative semidefinite at each k (the occupied set is fixed)
+    a = inputs.random_orbitals(52, (3, 1) + grid)
+    bb = inputs.random_orbitals(53, (3, 1) + grid)
+    va = oracle.fock_apply(u_occ, occ, a, kpts, TRICLINIC, grid, omega, alpha, kocc=kocc)
+    vb = oracle.fock_apply(u_occ, occ, bb, kpts, TRICLINIC, grid, omega, alpha, kocc=kocc)
+    for k in range(3):
+        ab, ba = np.vdot(a[k], vb[k]), np.vdot(bb[k], va[k])
+        assert abs(ab - np.conj(ba)) <= 1e-13 * abs(ab)
+        assert np.vdot(a[k], va[k]).real < 0
+    # VJP against central differences; no gradient reaches the unsampled k-point
+    u_tgt = _small_cell(54, grid, kpts, 2)
+    w = inputs.random_orbitals(55, u_tgt.shape)
+
+    def L(uo, ut, om):
+        return np.real(np.vdot(w, oracle.fock_apply(uo, occ, ut, kpts, TRICLINIC, grid, om, alpha, kocc=kocc)))
+
+    g_occ, g_tgt, g_om = oracle.fock_apply_vjp(u_occ, occ, u_tgt, w, kpts, TRICLINIC, grid, omega, alpha,
+                                               kocc=kocc)
+    assert np.all(g_occ[0] == 0)
+    h = 1e-5
+    for seed, (g, arg) in enumerate(((g_occ, 0), (g_tgt, 1))):
+        d = inputs.random_orbitals(56 + seed, g.shape)
+        args_p = [u_occ, u_tgt]
+        args_m = [u_occ, u_tgt]
+        args_p[arg] = args_p[arg] + h * d
+        args_m[arg] = args_m[arg] - h * d
+        fd = (L(args_p[0], args_p[1], omega) - L(args_m[0], args_m[1], omega)) / (2 * h)
+        an = np.real(np.vdot(g, d))
+        assert abs(fd - an) <= 1e-7 * abs(an)
+    fd = (L(u_occ, u_tgt, omega + h) - L(u_occ, u_tgt, omega - h)) / (2 * h)
+    assert abs(fd - g_om) <= 1e-7 * abs(g_om)
+    # E_x with a down-sampled Fock sum is still negative
+    assert oracle.exchange_energy(u_occ, occ, kpts, TRICLINIC, grid, omega, alpha, kocc=kocc) < 0
