@@ -19,6 +19,8 @@
  *   (V_x u)_{i,k}(r) = -alpha (1/N_k) sum_{k'} sum_{j occ} f_{j,k'} u_{j,k'}(r)
  *                      sum_G v(|G+q|) rho~_{ji}(G) e^{iG.r},
  *   rho~_{ji}(G)     = (1/N) sum_r conj(u_{j,k'}(r)) u_{i,k}(r) e^{-iG.r}.
+ * With down-sampling (hse_problem.nk_occ > 0) k' runs over the sampled points and 1/N_k
+ * becomes 1/nk_occ in V_x (and in c_j below); E_x keeps 1/N_k over its target k-points.
  *
  * Data layout (all device arrays are caller-owned):
  *   orbitals      [nk][nbands][N1][N2][N3], C order, N3 fastest, interleaved complex:
@@ -70,6 +72,14 @@ typedef struct {
   double alpha;           /* Fock mixing fraction, 0.25 in HSE                                   */
   double spin_degeneracy; /* g_s in E_x (2 for a closed shell); not used by V_x                  */
   int dtype;              /* HSE_C64 or HSE_C128                                                 */
+  /* Down-sampled Fock sum (Sec. II C, after Eq. "Fock-DS"): the sum over the occupied
+   * orbitals' k-points k' runs over nk_occ of the nk points, kocc[0..nk_occ) (HOST, distinct
+   * indices into kpts, copied at plan creation), with the weight 1/nk_occ in place of 1/nk.
+   * The orbital arrays keep the full mesh; only the sampled rows of u_occ and occ are read,
+   * and the VJP w.r.t. u_occ is zero at the other k-points.  nk_occ = 0: every k-point
+   * (kocc ignored).  Batched plans require nk_occ = 0. */
+  int nk_occ;
+  const int *kocc;
 } hse_problem;
 
 typedef struct hse_plan_s *hse_plan;
@@ -86,7 +96,8 @@ int hse_plan_create_batched(hse_plan *out, const hse_problem *cells, int ncells)
 
 int hse_plan_destroy(hse_plan plan);
 
-/* V_x applied to the targets (Sec. II C, Eq. "Fock-DS" with the 1/N_k weight).
+/* V_x applied to the targets (Sec. II C, Eq. "Fock-DS" with the 1/N_k weight, or 1/nk_occ
+ * over the sampled k' of a down-sampled plan).
  *   u_occ  device [nk][n_occ][N]   occupied orbitals u_{j,k'}
  *   occ    device [nk][n_occ]      occupations f_{j,k'} (double)
  *   u_tgt  device [nk][n_tgt][N]   target orbitals u_{i,k}; may equal u_occ
@@ -108,7 +119,8 @@ int hse_exchange_energy(hse_plan plan, const void *u_occ, const double *occ, dou
  *   grad_u_occ[k',j] = -sum_{k,i} c_j [conj(phi_ji) ybar_i + u_i conj(psibar_ji)]
  *   grad_omega       = Re sum conj(ybar) (dV_x/domega) u_tgt
  * grad_vx is ybar.  All gradients are overwritten (not accumulated); any of the three
- * outputs may be NULL to skip it.  Outputs must not overlap inputs. */
+ * outputs may be NULL to skip it.  Outputs must not overlap inputs.  A down-sampled plan
+ * writes zeros to the rows of grad_u_occ at k-points outside kocc. */
 int hse_fock_apply_vjp(hse_plan plan, const void *u_occ, const double *occ, const void *u_tgt,
                        const void *grad_vx, void *grad_u_occ, void *grad_u_tgt,
                        double *grad_omega, hse_stream_t stream);

@@ -1,8 +1,11 @@
 // hse_abi.cu - the C ABI of include/hse_fock.h: plans, validation, dispatch, reductions.
 //
 // A plan holds, on the device:
-//   * the q table: every distinct q = k - k' of the k-mesh (exact duplicates merged after
-//     rounding to 1e-10 bohr^-1) and qidx[k][k'] -> row;
+//   * the q table: every distinct q = k - k' (k a target point, k' a point of the Fock sum:
+//     all of them, or the sampled sub-mesh of a down-sampled plan; exact duplicates merged
+//     after rounding to 1e-10 bohr^-1) and qidx[k][k'] -> row;
+//   * for a down-sampled plan, the sampled rows of u_occ and occ gathered per call into
+//     compact buffers (and the VJP w.r.t. them, scattered back to the full mesh);
 //   * v(|G+q|) and d v/d omega per row, evaluated in FP64 (kept in FP64 for the staged
 //     form, rounded once to FP32 for the fused form);
 //   * reduction scratch: one double per owner orbital;
@@ -202,9 +205,36 @@ __global__ void dot_per_owner_f64(const double2* __restrict__ lhs, const double2
   if (threadIdx.x == 0) partial[o] = (weight ? weight[o] : 1.0) * sh[0];
 }
 
+// Sampled rows of the occupied set (down-sampling): dst[r] = src[idx[r]], rows of `words`
+// 8-byte words.
+__global__ void gather_rows(uint64_t* __restrict__ dst, const uint64_t* __restrict__ src, const int* __restrict__ idx,
+                            int nrows, size_t words) {
+  const size_t total = (size_t)nrows * words;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = i / words;
+    dst[i] = src[(size_t)idx[r] * words + (i - r * words)];
+  }
+}
+
+// Back to the full mesh: dst[r] = src[inv[r]] where inv[r] >= 0, else zeros.
+__global__ void scatter_rows(uint64_t* __restrict__ dst, const uint64_t* __restrict__ src, const int* __restrict__ inv,
+                             int nrows, size_t words) {
+  const size_t total = (size_t)nrows * words;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = i / words;
+    const int s = inv[r];
+    dst[i] = s >= 0 ? src[(size_t)s * words + (i - r * words)] : 0ull;
+  }
+}
+
 }  // namespace hse
 
 using namespace hse;
+
+// Roles of the fused kernel's owners, each with its own k' split: targets (apply, VJP
+// w.r.t. u_tgt and omega), occupied orbitals at every target k-point (exchange energy),
+// occupied orbitals at the sampled k' (VJP w.r.t. u_occ).
+enum OwnerRole : int { ROLE_TGT = 0, ROLE_ENERGY = 1, ROLE_OCC = 2 };
 
 struct hse_plan_s {
   hse_problem p;
@@ -214,7 +244,7 @@ struct hse_plan_s {
   int nq = 0;
   double dV = 0.0;
   double b[9] = {};
-  int* qidx = nullptr;       // device [nk][nk]
+  int* qidx = nullptr;       // device [nk][nkq]
   double* qvec = nullptr;    // device [nq][3]
   double* dkpts = nullptr;   // device [nk][3]
   double* v64 = nullptr;     // device [nq][N]
@@ -229,9 +259,18 @@ struct hse_plan_s {
   double2* vx64 = nullptr;   // [nk][max(n_occ, n_tgt)][N]
   int blocks_per_sm = 0;     // fused-kernel variant: 0 default, -1/-2/-3 staged-partner layouts, 1/2 pencil loads
   int inject = 0;            // test hook (HSE_INJECT_SKIP_FILL=1 at plan creation)
-  int nsplit[2] = {1, 1};    // k'-loop splits of the fused kernel for owners = targets / occupied
-  float2* split_buf = nullptr;  // [nsplit][nk][n_own][N] partial outputs when nsplit > 1
+  int nsplit[3] = {1, 1, 1};  // k'-loop splits of the fused kernel per OwnerRole
+  float2* split_buf = nullptr;  // [nsplit][nk_own][n_own][N] partial outputs when nsplit > 1
   size_t split_buf_elems = 0;
+  // down-sampled Fock sum
+  int nkq = 0;                  // k-points of the Fock sum: nk, or nk_occ when sampled
+  bool sampled = false;
+  std::vector<int> kocc;        // host [nkq] sampled k-point indices
+  int* d_kocc = nullptr;        // device [nkq]
+  int* d_kinv = nullptr;        // device [nk]: position in kocc, or -1
+  void* u_sub = nullptr;        // device [nkq][n_occ][N] gathered occupied orbitals
+  double* occ_sub = nullptr;    // device [nkq][n_occ]
+  void* g_sub = nullptr;        // device [nkq][n_occ][N] VJP w.r.t. the sampled orbitals
   // batched plans (hse_plan_create_batched)
   bool batched = false;
   std::vector<hse_plan> cells;          // one sub-plan (kernel tables) per cell
@@ -281,6 +320,15 @@ int validate_problem(const hse_problem* p) {
   if (p->dtype == HSE_C64 && (p->grid[0] != p->grid[1] || p->grid[1] != p->grid[2])) return HSE_ERR_UNSUPPORTED_GRID;
   for (int i = 0; i < 3 * p->nk; ++i)
     if (!std::isfinite(p->kpts[i])) return HSE_ERR_INVALID_ARG;
+  if (p->nk_occ < 0 || p->nk_occ > p->nk || (p->nk_occ > 0 && !p->kocc)) return HSE_ERR_INVALID_ARG;
+  if (p->nk_occ > 0) {
+    std::vector<char> seen(p->nk, 0);
+    for (int i = 0; i < p->nk_occ; ++i) {
+      const int k = p->kocc[i];
+      if (k < 0 || k >= p->nk || seen[k]) return HSE_ERR_INVALID_ARG;
+      seen[k] = 1;
+    }
+  }
   // sizes must stay within int indexing of a single grid and the launch grid
   const double N = (double)p->grid[0] * p->grid[1] * p->grid[2];
   if (N > 1e8 || (double)p->nk * p->nk > 2e9 || (double)p->nk * std::max(p->n_occ, p->n_tgt) > 2e9)
@@ -348,6 +396,11 @@ int hse_plan_destroy(hse_plan plan) {
   cudaFree(plan->work);
   cudaFree(plan->vx64);
   cudaFree(plan->split_buf);
+  cudaFree(plan->d_kocc);
+  cudaFree(plan->d_kinv);
+  cudaFree(plan->u_sub);
+  cudaFree(plan->occ_sub);
+  cudaFree(plan->g_sub);
   cudaSetDevice(prev);
   delete plan;
   return HSE_OK;
@@ -366,6 +419,16 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   plan->p = *p;
   plan->kpts.assign(p->kpts, p->kpts + 3 * p->nk);
   plan->p.kpts = plan->kpts.data();
+  plan->sampled = p->nk_occ > 0;
+  if (plan->sampled) {
+    plan->kocc.assign(p->kocc, p->kocc + p->nk_occ);
+  } else {
+    plan->kocc.resize(p->nk);
+    for (int k = 0; k < p->nk; ++k) plan->kocc[k] = k;
+  }
+  plan->nkq = (int)plan->kocc.size();
+  plan->p.nk_occ = plan->sampled ? plan->nkq : 0;
+  plan->p.kocc = plan->sampled ? plan->kocc.data() : nullptr;
   cudaGetDevice(&plan->device);
   if (const char* env = std::getenv("HSE_INJECT_SKIP_FILL")) plan->inject = std::atoi(env) == 1 ? 1 : 0;
   if (const char* env = std::getenv("HSE_BLOCKS_PER_SM")) {
@@ -382,17 +445,17 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
                                p->lattice[2] * (p->lattice[3] * p->lattice[7] - p->lattice[4] * p->lattice[6]));
   plan->dV = det / plan->N;
 
-  // distinct q = k - k'
-  const int nk = p->nk;
-  std::vector<int> qidx((size_t)nk * nk);
+  // distinct q = k - k' over target points k and the points k' of the Fock sum
+  const int nk = p->nk, nkq = plan->nkq;
+  std::vector<int> qidx((size_t)nk * nkq);
   std::vector<double> qvec;
   std::map<std::array<long long, 3>, int> seen;
   for (int k = 0; k < nk; ++k) {
-    for (int kp = 0; kp < nk; ++kp) {
+    for (int kp = 0; kp < nkq; ++kp) {
       double q[3];
       std::array<long long, 3> key;
       for (int c = 0; c < 3; ++c) {
-        q[c] = plan->kpts[3 * k + c] - plan->kpts[3 * kp + c];
+        q[c] = plan->kpts[3 * k + c] - plan->kpts[3 * plan->kocc[kp] + c];
         key[c] = std::llround(q[c] * 1e10);
       }
       auto it = seen.find(key);
@@ -400,9 +463,9 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
         const int id = (int)(qvec.size() / 3);
         seen.emplace(key, id);
         qvec.insert(qvec.end(), q, q + 3);
-        qidx[(size_t)k * nk + kp] = id;
+        qidx[(size_t)k * nkq + kp] = id;
       } else {
-        qidx[(size_t)k * nk + kp] = it->second;
+        qidx[(size_t)k * nkq + kp] = it->second;
       }
     }
   }
@@ -432,16 +495,22 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
     HSE_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device));
     const int occ_blocks = std::max(1, pairconv_c64_occupancy(n1, MODE_APPLY, plan->blocks_per_sm));
     const long long slots = (long long)sms * occ_blocks;
-    const int owners[2] = {p->n_tgt, p->n_occ};
+    // per OwnerRole: owner bands, owner k-points, partner k-points, partner bands
+    const int owners[3] = {p->n_tgt, p->n_occ, p->n_occ};
+    const int k_own[3] = {nk, nk, nkq};
+    const int k_part[3] = {nkq, nkq, nk};
+    const int b_part[3] = {p->n_occ, p->n_occ, p->n_tgt};
     size_t buf = 0;
-    for (int o = 0; o < 2; ++o) {
+    for (int o = 0; o < 3; ++o) {
       const int T = slots_for(n1);
-      const long long items = (long long)nk * ((owners[o] + T - 1) / T);
-      // the staged-partner kernel caches an item's occupations: at most kOccCache partners
-      const int ns_cap = std::min(8, nk);
-      const int ns_min = (plan->blocks_per_sm <= 0 && o == 0)
-                             ? std::min(ns_cap, std::max(1, (int)(((long long)nk * p->n_occ + kOccCache - 1) / kOccCache)))
-                             : 1;
+      const long long items = (long long)k_own[o] * ((owners[o] + T - 1) / T);
+      // the staged-partner kernel (roles with owner = target) caches an item's occupations:
+      // at most kOccCache partners per item
+      const int ns_cap = std::min(8, k_part[o]);
+      const int ns_min =
+          (plan->blocks_per_sm <= 0 && o != ROLE_OCC)
+              ? std::min(ns_cap, std::max(1, (int)(((long long)k_part[o] * b_part[o] + kOccCache - 1) / kOccCache)))
+              : 1;
       double best_eff = 0.0;
       int best = ns_min;
       for (int ns = ns_min; ns <= ns_cap; ++ns) {
@@ -453,7 +522,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
           best = ns;
         }
       }
-      const size_t need = best > 1 ? (size_t)best * nk * owners[o] * N : 0;
+      const size_t need = (best > 1 && o != ROLE_ENERGY) ? (size_t)best * k_own[o] * owners[o] * N : 0;
       if (need * sizeof(float2) > ((size_t)4 << 30)) best = 1;  // keep split buffers modest
       plan->nsplit[o] = best;
       if (best > 1) buf = std::max(buf, need);
@@ -464,8 +533,21 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
     }
   }
   {
-    const int nsmax = std::max(plan->nsplit[0], plan->nsplit[1]);
-    HSE_TRY(cudaMalloc(&plan->partial, (size_t)nsmax * nk * nown * sizeof(double)));
+    const size_t np = std::max((size_t)plan->nsplit[ROLE_TGT] * nk * p->n_tgt,
+                               (size_t)plan->nsplit[ROLE_ENERGY] * nk * p->n_occ);
+    HSE_TRY(cudaMalloc(&plan->partial, std::max(np, (size_t)nk * nown) * sizeof(double)));
+  }
+  if (plan->sampled) {
+    std::vector<int> kinv(nk, -1);
+    for (int i = 0; i < nkq; ++i) kinv[plan->kocc[i]] = i;
+    const size_t sub_bytes = (size_t)nkq * p->n_occ * N * elem_bytes(p->dtype);
+    HSE_TRY(cudaMalloc(&plan->d_kocc, (size_t)nkq * sizeof(int)));
+    HSE_TRY(cudaMalloc(&plan->d_kinv, (size_t)nk * sizeof(int)));
+    HSE_TRY(cudaMemcpy(plan->d_kocc, plan->kocc.data(), (size_t)nkq * sizeof(int), cudaMemcpyHostToDevice));
+    HSE_TRY(cudaMemcpy(plan->d_kinv, kinv.data(), (size_t)nk * sizeof(int), cudaMemcpyHostToDevice));
+    HSE_TRY(cudaMalloc(&plan->u_sub, sub_bytes));
+    HSE_TRY(cudaMalloc(&plan->g_sub, sub_bytes));
+    HSE_TRY(cudaMalloc(&plan->occ_sub, (size_t)nkq * p->n_occ * sizeof(double)));
   }
   HSE_TRY(cudaMalloc(&plan->status, sizeof(int)));
   HSE_TRY(cudaMemset(plan->status, 0, sizeof(int)));
@@ -478,7 +560,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
     // the energy path runs the staged form with the occupied set as targets
     const size_t per_kp = (size_t)nown * p->n_occ;
     size_t nkp = std::max<size_t>(1, ((size_t)512 << 20) / (per_kp * N * sizeof(double2)));
-    nkp = std::min<size_t>(nkp, (size_t)nk);
+    nkp = std::min<size_t>(nkp, (size_t)nkq);
     // at least two occupied x target batches: the VJP w.r.t. u_occ runs two at a time
     plan->work_pairs = std::max(nkp * per_kp, 2 * (size_t)p->n_occ * p->n_tgt);
     HSE_TRY(cudaMalloc(&plan->work, plan->work_pairs * N * sizeof(double2)));
@@ -525,29 +607,34 @@ int hse_status(hse_plan plan, hse_stream_t stream) {
 
 namespace {
 
+// Owners are targets at every k-point; partners the occupied orbitals of the Fock sum.
 PairArgs base_args(hse_plan plan) {
   PairArgs a{};
   a.occ = nullptr;
+  a.occ_own = nullptr;
   a.vtab = plan->v32;
   a.qidx = plan->qidx;
-  a.nk = plan->p.nk;
+  a.nk_own = plan->p.nk;
+  a.nk_part = plan->nkq;
   a.n_occ = plan->p.n_occ;
-  a.scale = (float)(-plan->p.alpha / ((double)plan->p.nk * plan->N));
+  a.scale = (float)(-plan->p.alpha / ((double)plan->nkq * plan->N));
   a.status = plan->status;
   a.inject = plan->inject;
   return a;
 }
+
+int role_of(int mode) { return mode == MODE_ENERGY ? ROLE_ENERGY : (mode == MODE_OCC ? ROLE_OCC : ROLE_TGT); }
 
 int run_pairconv(hse_plan plan, int mode, PairArgs a, int n_own, cudaStream_t st) {
   const int n = plan->p.grid[0];
   const int T = slots_for(n);
   a.n_own = n_own;
   a.ntiles = (n_own + T - 1) / T;
-  a.nsplit = plan->nsplit[n_own == plan->p.n_tgt ? 0 : 1];
-  const size_t count = (size_t)plan->p.nk * n_own * plan->N;
+  a.nsplit = plan->nsplit[role_of(mode)];
+  const size_t count = (size_t)a.nk_own * n_own * plan->N;
   float2* final_out = a.out;
   if (mode == MODE_ENERGY || mode == MODE_DOT) {
-    a.split_stride = (size_t)plan->p.nk * n_own;  // doubles between the splits' partials
+    a.split_stride = (size_t)a.nk_own * n_own;  // doubles between the splits' partials
   } else {
     a.split_stride = count;
     if (a.nsplit > 1) a.out = plan->split_buf;
@@ -564,9 +651,42 @@ int run_pairconv(hse_plan plan, int mode, PairArgs a, int n_own, cudaStream_t st
   return cuda_fail(e);
 }
 
-// number of partial doubles a reduction over owners of this count must sum
-int partial_count(hse_plan plan, int n_own) {
-  return plan->nsplit[n_own == plan->p.n_tgt ? 0 : 1] * plan->p.nk * n_own;
+// number of partial doubles a reduction over the owners of a mode must sum
+int partial_count(hse_plan plan, int mode, int n_own) {
+  return plan->nsplit[role_of(mode)] * plan->p.nk * n_own;
+}
+
+// Occupied rows of the Fock sum: the caller's arrays, or their sampled rows gathered into
+// the plan's compact buffers (down-sampling).
+int occupied_rows(hse_plan plan, const void* u_occ, const double* occ, const void** u_rows, const double** occ_rows,
+                  cudaStream_t st) {
+  if (!plan->sampled) {
+    *u_rows = u_occ;
+    *occ_rows = occ;
+    return HSE_OK;
+  }
+  const size_t words = (size_t)plan->p.n_occ * plan->N * elem_bytes(plan->p.dtype) / 8;
+  const size_t total = words * plan->nkq;
+  const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
+  gather_rows<<<blocks, 256, 0, st>>>((uint64_t*)plan->u_sub, (const uint64_t*)u_occ, plan->d_kocc, plan->nkq, words);
+  count_launch();
+  gather_rows<<<std::max(1u, (unsigned)((plan->nkq * plan->p.n_occ + 255) / 256)), 256, 0, st>>>(
+      (uint64_t*)plan->occ_sub, (const uint64_t*)occ, plan->d_kocc, plan->nkq, (size_t)plan->p.n_occ);
+  count_launch();
+  *u_rows = plan->u_sub;
+  *occ_rows = plan->occ_sub;
+  return cuda_fail(cudaGetLastError());
+}
+
+// The VJP w.r.t. the sampled occupied orbitals, back on the full mesh (zeros elsewhere).
+int scatter_occ_grad(hse_plan plan, void* grad_u_occ, cudaStream_t st) {
+  const size_t words = (size_t)plan->p.n_occ * plan->N * elem_bytes(plan->p.dtype) / 8;
+  const size_t total = words * plan->p.nk;
+  const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
+  scatter_rows<<<blocks, 256, 0, st>>>((uint64_t*)grad_u_occ, (const uint64_t*)plan->g_sub, plan->d_kinv, plan->p.nk,
+                                       words);
+  count_launch();
+  return cuda_fail(cudaGetLastError());
 }
 
 int reduce(hse_plan plan, int n, double factor, double* out, cudaStream_t st) {
@@ -575,12 +695,13 @@ int reduce(hse_plan plan, int n, double factor, double* out, cudaStream_t st) {
   return cuda_fail(cudaGetLastError());
 }
 
-// Staged FP64 V_x: out[k][i] for every target; table = v64 or dv64.
+// Staged FP64 V_x: out[k][i] for every target; table = v64 or dv64.  u_occ / occ are the
+// occupied rows of the Fock sum ([nkq][n_occ]).
 int staged_apply(hse_plan plan, const double2* u_occ, const double* occ, const double2* u_tgt, int n_tgt,
                  const double* table, double2* out, cudaStream_t st) {
   const hse_problem& p = plan->p;
   const int N = plan->N;
-  const int nk = p.nk;
+  const int nk = p.nk, nkq = plan->nkq;
   const size_t per_kp = (size_t)n_tgt * p.n_occ;
   if (per_kp > plan->work_pairs) return HSE_ERR_INVALID_ARG;  // cannot happen: sized for max(n_occ, n_tgt)
   const int nkp_chunk = (int)(plan->work_pairs / per_kp);
@@ -591,17 +712,17 @@ int staged_apply(hse_plan plan, const double2* u_occ, const double* occ, const d
   a.vtab = table;
   a.qidx = plan->qidx;
   a.work = plan->work;
-  a.nk = nk;
+  a.nk_occ = nkq;
   a.n_occ = p.n_occ;
   a.n_tgt = n_tgt;
   a.N = N;
-  a.scale = -p.alpha / ((double)nk * N);
+  a.scale = -p.alpha / ((double)nkq * N);
   const int inner[3] = {p.grid[1] * p.grid[2], p.grid[2], 1};
   for (int k = 0; k < nk; ++k) {
-    for (int kp0 = 0; kp0 < nk; kp0 += nkp_chunk) {
+    for (int kp0 = 0; kp0 < nkq; kp0 += nkp_chunk) {
       a.k = k;
       a.kp0 = kp0;
-      a.nkp = std::min(nkp_chunk, nk - kp0);
+      a.nkp = std::min(nkp_chunk, nkq - kp0);
       const size_t nb = (size_t)n_tgt * a.nkp * p.n_occ;
       cudaError_t e = launch_staged_pair_product(a, st);
       if (e != cudaSuccess) return cuda_fail(e);
@@ -666,7 +787,8 @@ cudaError_t run_batch(hse_plan plan, cudaStream_t st) {
 }
 
 // Staged FP64 VJP: grad_u_tgt = V_x ybar; grad_omega = Re <ybar, V_x' u_tgt> (V_x' with
-// d v / d omega rows); grad_u_occ by occupied-owner batches.
+// d v / d omega rows); grad_u_occ by occupied-owner batches.  u_occ / occ / g_occ are the
+// occupied rows of the Fock sum ([nkq][n_occ]).
 int staged_vjp(hse_plan plan, const double2* u_occ, const double* occ, const double2* u_tgt, const double2* ybar,
                double2* g_occ, double2* g_tgt, double* g_om, cudaStream_t st) {
   const hse_problem& p = plan->p;
@@ -692,6 +814,7 @@ int staged_vjp(hse_plan plan, const double2* u_occ, const double* occ, const dou
     const size_t half = plan->work_pairs / 2;
     if (per_k > half) return HSE_ERR_NOMEM;
     const int nkc_max = (int)std::min<size_t>(half / per_k, (size_t)p.nk);
+    const int nkq = plan->nkq;
     StagedOccArgs a{};
     a.u_occ = u_occ;
     a.u_tgt = u_tgt;
@@ -701,13 +824,13 @@ int staged_vjp(hse_plan plan, const double2* u_occ, const double* occ, const dou
     a.qidx = plan->qidx;
     a.w1 = plan->work;
     a.w2 = plan->work + half * N;
-    a.nk = p.nk;
+    a.nk_occ = nkq;
     a.n_occ = p.n_occ;
     a.n_tgt = p.n_tgt;
     a.N = N;
-    a.scale = -p.alpha / ((double)p.nk * N);
+    a.scale = -p.alpha / ((double)nkq * N);
     const int inner[3] = {p.grid[1] * p.grid[2], p.grid[2], 1};
-    for (int kp = 0; kp < p.nk; ++kp) {
+    for (int kp = 0; kp < nkq; ++kp) {
       for (int k0 = 0; k0 < p.nk; k0 += nkc_max) {
         a.kp = kp;
         a.k0 = k0;
@@ -747,16 +870,21 @@ int hse_fock_apply(hse_plan plan, const void* u_occ, const double* occ, const vo
       overlaps(vx_out, tgt_bytes, occ, (size_t)p.nk * p.n_occ * sizeof(double)))
     return HSE_ERR_ALIAS;
   cudaStream_t st = S(stream);
+  const void* u_rows = nullptr;
+  const double* occ_rows = nullptr;
+  int rc = occupied_rows(plan, u_occ, occ, &u_rows, &occ_rows, st);
+  if (rc) return rc;
   if (p.dtype == HSE_C64) {
     PairArgs a = base_args(plan);
     a.own = (const float2*)u_tgt;
-    a.part = (const float2*)u_occ;
+    a.part = (const float2*)u_rows;
     a.out = (float2*)vx_out;
-    a.occ = occ;
+    a.occ = occ_rows;
     a.n_part = p.n_occ;
     return run_pairconv(plan, MODE_APPLY, a, p.n_tgt, st);
   }
-  return staged_apply(plan, (const double2*)u_occ, occ, (const double2*)u_tgt, p.n_tgt, plan->v64, (double2*)vx_out, st);
+  return staged_apply(plan, (const double2*)u_rows, occ_rows, (const double2*)u_tgt, p.n_tgt, plan->v64,
+                      (double2*)vx_out, st);
 }
 
 int hse_exchange_energy(hse_plan plan, const void* u_occ, const double* occ, double* e_x, hse_stream_t stream) {
@@ -766,24 +894,30 @@ int hse_exchange_energy(hse_plan plan, const void* u_occ, const double* occ, dou
   cudaStream_t st = S(stream);
   const int nown = p.nk * p.n_occ;
   const double factor = 0.5 * p.spin_degeneracy * plan->dV / p.nk;
-  int rc;
+  // targets: the occupied orbitals at every k-point; partners: the rows of the Fock sum
+  const void* u_rows = nullptr;
+  const double* occ_rows = nullptr;
+  int rc = occupied_rows(plan, u_occ, occ, &u_rows, &occ_rows, st);
+  if (rc) return rc;
   if (p.dtype == HSE_C64) {
     PairArgs a = base_args(plan);
     a.own = (const float2*)u_occ;
-    a.part = (const float2*)u_occ;
+    a.part = (const float2*)u_rows;
     a.partial = plan->partial;
-    a.occ = occ;
+    a.occ = occ_rows;
+    a.occ_own = occ;
     a.n_part = p.n_occ;
     rc = run_pairconv(plan, MODE_ENERGY, a, p.n_occ, st);
   } else {
-    rc = staged_apply(plan, (const double2*)u_occ, occ, (const double2*)u_occ, p.n_occ, plan->v64, plan->vx64, st);
+    rc = staged_apply(plan, (const double2*)u_rows, occ_rows, (const double2*)u_occ, p.n_occ, plan->v64, plan->vx64,
+                      st);
     if (rc) return rc;
     dot_per_owner_f64<<<nown, 256, 0, st>>>((const double2*)u_occ, plan->vx64, plan->N, occ, plan->partial);
     count_launch();
     rc = cuda_fail(cudaGetLastError());
   }
   if (rc) return rc;
-  return reduce(plan, p.dtype == HSE_C64 ? partial_count(plan, p.n_occ) : nown, factor, e_x, st);
+  return reduce(plan, p.dtype == HSE_C64 ? partial_count(plan, MODE_ENERGY, p.n_occ) : nown, factor, e_x, st);
 }
 
 int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, const void* u_tgt, const void* grad_vx,
@@ -805,16 +939,24 @@ int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, cons
   }
   if (overlaps(grad_u_occ, occ_bytes, grad_u_tgt, tgt_bytes)) return HSE_ERR_ALIAS;
   cudaStream_t st = S(stream);
-  if (p.dtype == HSE_C128)
-    return staged_vjp(plan, (const double2*)u_occ, occ, (const double2*)u_tgt, (const double2*)grad_vx,
-                      (double2*)grad_u_occ, (double2*)grad_u_tgt, grad_omega, st);
-  int rc = HSE_OK;
+  const void* u_rows = nullptr;
+  const double* occ_rows = nullptr;
+  int rc = occupied_rows(plan, u_occ, occ, &u_rows, &occ_rows, st);
+  if (rc) return rc;
+  // the VJP w.r.t. the sampled rows goes to the plan's compact buffer, then to the full mesh
+  void* g_rows = (grad_u_occ && plan->sampled) ? plan->g_sub : grad_u_occ;
+  if (p.dtype == HSE_C128) {
+    rc = staged_vjp(plan, (const double2*)u_rows, occ_rows, (const double2*)u_tgt, (const double2*)grad_vx,
+                    (double2*)g_rows, (double2*)grad_u_tgt, grad_omega, st);
+    if (rc == HSE_OK && grad_u_occ && plan->sampled) rc = scatter_occ_grad(plan, grad_u_occ, st);
+    return rc;
+  }
   if (grad_u_tgt) {
     PairArgs a = base_args(plan);
     a.own = (const float2*)grad_vx;
-    a.part = (const float2*)u_occ;
+    a.part = (const float2*)u_rows;
     a.out = (float2*)grad_u_tgt;
-    a.occ = occ;
+    a.occ = occ_rows;
     a.n_part = p.n_occ;
     rc = run_pairconv(plan, MODE_APPLY, a, p.n_tgt, st);
     if (rc) return rc;
@@ -822,26 +964,30 @@ int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, cons
   if (grad_omega) {
     PairArgs a = base_args(plan);
     a.own = (const float2*)u_tgt;
-    a.part = (const float2*)u_occ;
+    a.part = (const float2*)u_rows;
     a.part2 = (const float2*)grad_vx;
     a.partial = plan->partial;
-    a.occ = occ;
+    a.occ = occ_rows;
     a.vtab = plan->dv32;
     a.n_part = p.n_occ;
     rc = run_pairconv(plan, MODE_DOT, a, p.n_tgt, st);
     if (rc) return rc;
-    rc = reduce(plan, partial_count(plan, p.n_tgt), 1.0, grad_omega, st);
+    rc = reduce(plan, partial_count(plan, MODE_DOT, p.n_tgt), 1.0, grad_omega, st);
     if (rc) return rc;
   }
   if (grad_u_occ) {
+    // owners: the occupied orbitals of the Fock sum (nkq k-points); partners: all targets
     PairArgs a = base_args(plan);
-    a.own = (const float2*)u_occ;
+    a.own = (const float2*)u_rows;
     a.part = (const float2*)u_tgt;
     a.part2 = (const float2*)grad_vx;
-    a.out = (float2*)grad_u_occ;
-    a.occ = occ;
+    a.out = (float2*)g_rows;
+    a.occ = occ_rows;
+    a.nk_own = plan->nkq;
+    a.nk_part = p.nk;
     a.n_part = p.n_tgt;
     rc = run_pairconv(plan, MODE_OCC, a, p.n_occ, st);
+    if (rc == HSE_OK && plan->sampled) rc = scatter_occ_grad(plan, grad_u_occ, st);
   }
   return rc;
 }
@@ -880,6 +1026,7 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
     const int rc = validate_problem(&cells[c]);
     if (rc) return rc;
     if (cells[c].dtype != HSE_C64 || !batched_side_supported(cells[c].grid[0])) return HSE_ERR_UNSUPPORTED_GRID;
+    if (cells[c].nk_occ != 0) return HSE_ERR_INVALID_ARG;  // down-sampling: single-cell plans only
   }
   hse_plan plan = new (std::nothrow) hse_plan_s();
   if (!plan) return HSE_ERR_NOMEM;

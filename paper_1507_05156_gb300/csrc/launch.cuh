@@ -72,7 +72,7 @@ template <int n, int MODE, int MINB>
 cudaError_t launch_pairconv_variant(const PairArgs& args, cudaStream_t stream) {
   cudaError_t err = pairconv_set_attr<n, MODE, MINB>();
   if (err != cudaSuccess) return err;
-  const dim3 grid((unsigned)((size_t)args.nsplit * args.nk * args.ntiles));
+  const dim3 grid((unsigned)((size_t)args.nsplit * args.nk_own * args.ntiles));
   pairconv_c64_kernel<n, MODE, MINB><<<grid, Geo<n>::THREADS, pairconv_smem_bytes<n>(), stream>>>(args);
   count_launch();
   return cudaGetLastError();
@@ -107,9 +107,9 @@ cudaError_t launch_pairconv_tma(const PairArgs& args, cudaStream_t stream) {
     attr_done[dev] = true;
   }
   CUtensorMap tmap;
-  cudaError_t err = make_partner_tmap(&tmap, args.part, n, (long long)args.nk * args.n_part * Geo<n>::NN, S::SP, S::BR);
+  cudaError_t err = make_partner_tmap(&tmap, args.part, n, (long long)args.nk_part * args.n_part * Geo<n>::NN, S::SP, S::BR);
   if (err != cudaSuccess) return err;
-  const dim3 grid((unsigned)((size_t)args.nsplit * args.nk * args.ntiles));
+  const dim3 grid((unsigned)((size_t)args.nsplit * args.nk_own * args.ntiles));
   pairconv_tma_kernel<n, MODE, L><<<grid, L<n>::THREADS, S::SMEM_REQUEST, stream>>>(args, tmap);
   count_launch();
   return cudaGetLastError();

@@ -89,6 +89,7 @@ extern "C" int hse_exchange_energy_noalloc(const hse_problem* p, const void* u_o
       !std::isfinite(p->spin_degeneracy))
     return HSE_ERR_INVALID_ARG;
   if ((((uintptr_t)u_occ) & 15u) != 0) return HSE_ERR_INVALID_ARG;
+  if (p->nk_occ != 0) return HSE_ERR_INVALID_ARG;  // no down-sampling in the allocation-free form
   for (int i = 0; i < 3 * p->nk; ++i)
     if (!std::isfinite(p->kpts[i])) return HSE_ERR_INVALID_ARG;
   const double* A = p->lattice;
@@ -152,9 +153,11 @@ extern "C" int hse_exchange_energy_noalloc(const hse_problem* p, const void* u_o
   a.part = (const float2*)u_occ;
   a.partial = d_partial;
   a.occ = occ;
+  a.occ_own = occ;
   a.vtab = d_vtab;
   a.qidx = d_qidx;
-  a.nk = p->nk;
+  a.nk_own = p->nk;
+  a.nk_part = p->nk;
   a.n_own = p->n_occ;
   a.n_part = p->n_occ;
   a.n_occ = p->n_occ;

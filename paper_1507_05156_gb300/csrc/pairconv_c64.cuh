@@ -93,10 +93,13 @@ struct PairArgs {
   const float2* part2;  // MODE_OCC: ybar [nk][n_part][N];  MODE_DOT: ybar [nk][n_own][N]
   float2* out;          // APPLY / OCC: [nk][n_own][N]
   double* partial;      // ENERGY / DOT: [nk][n_own]
-  const double* occ;    // [nk][n_occ] occupations
+  const double* occ;    // [nk_occ][n_occ] occupations of the occupied orbitals
+  const double* occ_own;  // MODE_ENERGY: [nk_own][n_occ] occupations of the owners
   const float* vtab;    // [nq][N] kernel rows v(|G+q|) (or d v / d omega)
-  const int* qidx;      // [nk][nk] row of q = k - k' (first index k, second k')
-  int nk, n_own, n_part, n_occ;
+  const int* qidx;      // [nk_tgt][nk_occ] row of q = k - k' (k a target point, k' occupied)
+  int nk_own, nk_part;  // k-points of the owners / of the partners (the sampled k' when the
+                        // owners are targets, all target k-points for MODE_OCC)
+  int n_own, n_part, n_occ;
   int ntiles;           // ceil(n_own / slots)
   float scale;          // -alpha / (N_k * N): per-pair scale is scale * f
   int nsplit;           // the k' loop is split into nsplit work items per owner tile
@@ -314,14 +317,15 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
   const uint32_t trow0 = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * G::COLS_PER_WARP);
   const uint32_t ttab = trow0 + (uint32_t)G::TAB;
 
-  // work item: (split, k, tile); split s covers k' in [s nk / nsplit, (s+1) nk / nsplit)
-  const int per_split = args.nk * args.ntiles;
+  // work item: (split, k, tile); split s covers partner k-points
+  // [s nk_part / nsplit, (s+1) nk_part / nsplit)
+  const int per_split = args.nk_own * args.ntiles;
   const int split = item / per_split;
   const int rem = item - split * per_split;
   const int k = rem / args.ntiles;
   const int band = (rem - k * args.ntiles) * G::T + slot;
-  const int kp_begin = (int)(((long long)split * args.nk) / args.nsplit);
-  const int kp_end = (int)(((long long)(split + 1) * args.nk) / args.nsplit);
+  const int kp_begin = (int)(((long long)split * args.nk_part) / args.nsplit);
+  const int kp_end = (int)(((long long)(split + 1) * args.nk_part) / args.nsplit);
   const bool active = valid && band < args.n_own;
   const int bandc = active ? band : 0;
   const float2* own = args.own + ((size_t)k * args.n_own + bandc) * G::N;
@@ -336,7 +340,7 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
 
   for (int kp = kp_begin; kp < kp_end; ++kp) {
     // q = k_i - k_j: APPLY-like modes own i (at k) and pair with j at kp; OCC owns j (at k)
-    const int qrow = (MODE == MODE_OCC) ? args.qidx[kp * args.nk + k] : args.qidx[k * args.nk + kp];
+    const int qrow = (MODE == MODE_OCC) ? args.qidx[kp * args.nk_own + k] : args.qidx[k * args.nk_part + kp];
     if (warp_on) cache_kernel_row<n>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
     for (int j = 0; j < args.n_part; ++j) {
       const float2* part = args.part + ((size_t)kp * args.n_part + j) * G::N;
@@ -396,7 +400,7 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     if (valid && t == 0 && active) {
       double sum = 0.0;
       for (int e = 0; e < G::TS; ++e) sum += red[slot * G::TS + e];
-      if (MODE == MODE_ENERGY) sum *= args.occ[k * args.n_occ + band];
+      if (MODE == MODE_ENERGY) sum *= args.occ_own[k * args.n_occ + band];
       args.partial[split * args.split_stride + (size_t)k * args.n_own + band] = sum;
     }
   }

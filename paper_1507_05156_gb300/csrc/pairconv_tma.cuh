@@ -509,15 +509,15 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
   const uint32_t trow0 = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * S::COLS_PER_WARP);
   const uint32_t town = trow0 + (uint32_t)Lay::OWN;
 
-  const int per_split = args.nk * args.ntiles;
+  const int per_split = args.nk_own * args.ntiles;
   const int split = blockIdx.x / per_split;
   const int rem = blockIdx.x - split * per_split;
   const int k = rem / args.ntiles;
   const int band = (rem - k * args.ntiles) * G::T + slot;
   const bool active = valid && band < args.n_own;
   const int bandc = active ? band : 0;
-  const int kp_begin = (int)(((long long)split * args.nk) / args.nsplit);
-  const int kp_end = (int)(((long long)(split + 1) * args.nk) / args.nsplit);
+  const int kp_begin = (int)(((long long)split * args.nk_part) / args.nsplit);
+  const int kp_end = (int)(((long long)(split + 1) * args.nk_part) / args.nsplit);
   const int npairs = (kp_end - kp_begin) * args.n_part;
   const float2* own = args.own + ((size_t)k * args.n_own + bandc) * G::N;
 
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
     const int kp = kp_begin + q / args.n_part;
     const float f = item_occ(occ_sh, args, kp_begin, q);
     if (kp != cur_kp) {
-      const int qrow = args.qidx[k * args.nk + kp];
+      const int qrow = args.qidx[k * args.nk_part + kp];
       Lay::cache_row(t, trow0, args.vtab + (size_t)qrow * G::N, args.scale);
       cur_kp = kp;
     }
@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
     if (valid && t == 0 && active) {
       double sum = 0.0;
       for (int e = 0; e < Lay::TS; ++e) sum += red[slot * Lay::TS + e];
-      if (MODE == MODE_ENERGY) sum *= args.occ[k * args.n_occ + band];
+      if (MODE == MODE_ENERGY) sum *= args.occ_own[k * args.n_occ + band];
       args.partial[split * args.split_stride + (size_t)k * args.n_own + band] = sum;
     }
   }

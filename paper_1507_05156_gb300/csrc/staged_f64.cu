@@ -25,7 +25,7 @@ __global__ void staged_kernel_scale(const StagedArgs a) {
     const size_t bidx = idx / a.N;
     const int j = (int)(bidx % a.n_occ);
     const int kp = a.kp0 + (int)((bidx / a.n_occ) % a.nkp);
-    const double s = a.vtab[(size_t)a.qidx[a.k * a.nk + kp] * a.N + r] * a.scale * a.occ[kp * a.n_occ + j];
+    const double s = a.vtab[(size_t)a.qidx[a.k * a.nk_occ + kp] * a.N + r] * a.scale * a.occ[kp * a.n_occ + j];
     double2 w = a.work[idx];
     w.x *= s;
     w.y *= s;
@@ -84,7 +84,7 @@ __global__ void staged_occ_scale(const StagedOccArgs a) {
     const int kl = (int)((b / a.n_tgt) % a.nkc);
     const int j = (int)(b / ((size_t)a.n_tgt * a.nkc));
     const int k = a.k0 + kl;
-    const double s = a.vtab[(size_t)a.qidx[k * a.nk + a.kp] * a.N + r] * a.scale * a.occ[a.kp * a.n_occ + j];
+    const double s = a.vtab[(size_t)a.qidx[k * a.nk_occ + a.kp] * a.N + r] * a.scale * a.occ[a.kp * a.n_occ + j];
     double2 w = a.w1[idx];
     a.w1[idx] = make_double2(w.x * s, w.y * s);
     w = a.w2[idx];

@@ -19,16 +19,16 @@
 namespace hse {
 
 struct StagedArgs {
-  const double2* u_occ;  // [nk][n_occ][N]
+  const double2* u_occ;  // [nk_occ][n_occ][N] occupied orbitals at the sampled k'
   const double2* u_tgt;  // [nk][n_tgt][N]  (or ybar)
-  const double* occ;     // [nk][n_occ]
+  const double* occ;     // [nk_occ][n_occ]
   const double* vtab;    // [nq][N] FP64 kernel rows
-  const int* qidx;       // [nk][nk]
+  const int* qidx;       // [nk][nk_occ]
   double2* work;         // [nbatch][N]
-  int nk, n_occ, n_tgt, N;
+  int nk_occ, n_occ, n_tgt, N;
   int k;                 // target k-point of this batch
   int kp0, nkp;          // k' range of this batch
-  double scale;          // -alpha / (N_k N)
+  double scale;          // -alpha / (N_q N), N_q = nk_occ
 };
 
 // One thread per pencil of length L along an axis with element stride `inner`.
@@ -54,21 +54,21 @@ __global__ void staged_fft_axis(double2* __restrict__ work, size_t nbatch, int N
 
 // VJP w.r.t. the occupied orbitals (owner j at k-point kp, partners (k, i) for k in a chunk):
 //   W1[b] = conj(u_j) u_i,  W2[b] = conj(u_j) ybar_i,  b = (j, kl, i), i fastest;
-//   both transformed, scaled by v(|G+q|) (-alpha f_j / (N_k N)), q = k - kp, transformed back;
+//   both transformed, scaled by v(|G+q|) (-alpha f_j / (N_q N)), q = k - kp, transformed back;
 //   g_occ[kp][j] (+)= sum_{kl, i} conj(W1) ybar_i + u_i conj(W2).
 struct StagedOccArgs {
-  const double2* u_occ;  // [nk][n_occ][N]
+  const double2* u_occ;  // [nk_occ][n_occ][N] occupied orbitals at the sampled k'
   const double2* u_tgt;  // [nk][n_tgt][N]
   const double2* ybar;   // [nk][n_tgt][N]
-  const double* occ;
+  const double* occ;     // [nk_occ][n_occ]
   const double* vtab;
-  const int* qidx;
+  const int* qidx;       // [nk][nk_occ]
   double2* w1;           // [nbatch][N]
   double2* w2;           // [nbatch][N]
-  int nk, n_occ, n_tgt, N;
-  int kp;                // owner k-point
-  int k0, nkc;           // partner k range
-  double scale;          // -alpha / (N_k N)
+  int nk_occ, n_occ, n_tgt, N;
+  int kp;                // owner k-point (index into the sampled k')
+  int k0, nkc;           // partner (target) k range
+  double scale;          // -alpha / (N_q N)
 };
 
 // Non-template stage kernels live in staged_f64.cu; these launch them on `stream`.

@@ -54,6 +54,8 @@ class HseProblem(ctypes.Structure):
         ("alpha", ctypes.c_double),
         ("spin_degeneracy", ctypes.c_double),
         ("dtype", ctypes.c_int),
+        ("nk_occ", ctypes.c_int),
+        ("kocc", ctypes.POINTER(ctypes.c_int)),
     ]
 
 
@@ -117,7 +119,8 @@ def _code(dtype: torch.dtype) -> int:
     raise ValueError(f"unsupported dtype {dtype}")
 
 
-def _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype) -> Tuple[HseProblem, np.ndarray]:
+def _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype, kocc=None):
+    """HseProblem and the host arrays it points to (keep them alive with it)."""
     kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
     p = HseProblem()
     p.grid[:] = [int(g) for g in grid]
@@ -130,22 +133,34 @@ def _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, d
     p.alpha = float(alpha)
     p.spin_degeneracy = float(spin_degeneracy)
     p.dtype = _code(dtype)
-    return p, kp
+    if kocc is None:
+        p.nk_occ = 0
+        ko = None
+    else:
+        ko = np.ascontiguousarray(np.asarray(kocc, dtype=np.int32).reshape(-1))
+        p.nk_occ = int(ko.shape[0])
+        p.kocc = ko.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    return p, (kp, ko)
 
 
 class Plan:
-    """An hse_plan: q table, FP64 kernel rows and reduction scratch on one device."""
+    """An hse_plan: q table, FP64 kernel rows and reduction scratch on one device.
+
+    ``kocc`` (optional) down-samples the Fock sum: the indices of the k-points whose occupied
+    orbitals enter it, with weight 1/len(kocc) (Sec. II C, after Eq. "Fock-DS"); the orbital
+    arrays keep every k-point."""
 
     def __init__(self, grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy=2.0,
-                 dtype=torch.complex64, device=None):
+                 dtype=torch.complex64, device=None, kocc=None):
         lib = load_library()
         self.grid = tuple(int(g) for g in grid)
         self.nk = int(np.asarray(kpts).reshape(-1, 3).shape[0])
+        self.kocc = None if kocc is None else tuple(int(k) for k in kocc)
         self.n_occ, self.n_tgt = int(n_occ), int(n_tgt)
         self.omega, self.alpha, self.spin_degeneracy = float(omega), float(alpha), float(spin_degeneracy)
         self.dtype = dtype
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
-        prob, self._kp = _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype)
+        prob, self._kp = _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype, self.kocc)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(lib.hse_plan_create(ctypes.byref(h), ctypes.byref(prob)), "hse_plan_create")
@@ -166,15 +181,15 @@ _plan_cache: Dict[tuple, Plan] = {}
 
 
 def get_plan(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy=2.0,
-             dtype=torch.complex64, device=None) -> Plan:
+             dtype=torch.complex64, device=None, kocc=None) -> Plan:
     """Plans are cached by every parameter that enters them."""
     dev = torch.cuda.current_device() if device is None else torch.device(device).index
     key = (tuple(int(g) for g in grid), np.asarray(lattice, np.float64).tobytes(),
            np.asarray(kpts, np.float64).tobytes(), int(n_occ), int(n_tgt), float(omega), float(alpha),
-           float(spin_degeneracy), dtype, dev)
+           float(spin_degeneracy), dtype, dev, None if kocc is None else tuple(int(k) for k in kocc))
     plan = _plan_cache.get(key)
     if plan is None:
-        plan = Plan(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype, device=dev)
+        plan = Plan(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype, device=dev, kocc=kocc)
         _plan_cache[key] = plan
     return plan
 

@@ -26,18 +26,20 @@ from . import hse
 
 
 class Geometry:
-    """Cell, k-points and HSE parameters shared by every call of one problem."""
+    """Cell, k-points and HSE parameters shared by every call of one problem.  ``kocc``
+    optionally down-samples the Fock sum to those k-point indices (weight 1/len(kocc))."""
 
-    def __init__(self, grid, lattice, kpts, alpha=0.25, spin_degeneracy=2.0):
+    def __init__(self, grid, lattice, kpts, alpha=0.25, spin_degeneracy=2.0, kocc=None):
         self.grid = tuple(int(g) for g in grid)
         self.lattice = np.asarray(lattice, dtype=np.float64)
         self.kpts = np.asarray(kpts, dtype=np.float64).reshape(-1, 3)
         self.alpha = float(alpha)
         self.spin_degeneracy = float(spin_degeneracy)
+        self.kocc = None if kocc is None else tuple(int(k) for k in kocc)
 
     def plan(self, n_occ, n_tgt, omega, dtype):
         return hse.get_plan(self.grid, self.lattice, self.kpts, n_occ, n_tgt, float(omega), self.alpha,
-                            self.spin_degeneracy, dtype=dtype)
+                            self.spin_degeneracy, dtype=dtype, kocc=self.kocc)
 
 
 class FockApply(torch.autograd.Function):

@@ -64,11 +64,23 @@ def _prob(**kw):
     (dict(n_tgt=0), -1),
     (dict(lattice=np.zeros((3, 3))), -1),          # singular cell
     (dict(kpts=np.array([[0.0, np.inf, 0.0]])), -1),
+    (dict(kpts=np.zeros((2, 3)), kocc=[2]), -1),           # sampled k-point out of range
+    (dict(kpts=np.zeros((2, 3)), kocc=[-1]), -1),
+    (dict(kpts=np.zeros((2, 3)), kocc=[1, 1]), -1),        # repeated
+    (dict(kpts=np.zeros((2, 3)), kocc=[0, 1, 0]), -1),     # more than nk
 ])
 def test_plan_create_rejects_bad_problems_on_host(lib, kw, code):
     p, keep = _prob(**kw)
     h = ctypes.c_void_p(123)
     assert lib.hse_plan_create(ctypes.byref(h), ctypes.byref(p)) == code
+    assert not h.value
+
+
+def test_batched_plans_refuse_down_sampling(lib):
+    p, keep = _prob(kpts=np.zeros((2, 3)), kocc=[1])
+    cells = (hse.HseProblem * 1)(p)
+    h = ctypes.c_void_p(123)
+    assert lib.hse_plan_create_batched(ctypes.byref(h), cells, 1) == -1
     assert not h.value
 
 
