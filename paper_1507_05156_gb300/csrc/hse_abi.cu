@@ -277,9 +277,10 @@ struct hse_plan_s {
   std::vector<BatchCell> h_cells;       // launch arguments, pointers refreshed per call
   std::vector<float2*> cell_split;      // per cell [kMaxBatchSplit][nk][n_tgt][N]
   BatchCell* d_cells = nullptr;
-  BatchItem* d_items = nullptr;
-  int* d_counter = nullptr;
+  BatchItem* d_items = nullptr;         // staged-partner items, then pencil-load items
+  int* d_counter = nullptr;             // [2]: one per list
   int nitems = 0;
+  int nitems_staged = 0;
   int batch_split = 0;                  // autotuned k' split (0: not tuned yet)
   int sms = 0;
   cudaGraphExec_t graph = nullptr;
@@ -743,14 +744,15 @@ int staged_apply(hse_plan plan, const double2* u_occ, const double* occ, const d
   return HSE_OK;
 }
 
-// Work list of a batched plan for a k' split factor: items (cell, split, k, tile) sorted by
+// Work lists of a batched plan for a k' split factor: items (cell, split, k, tile) of the
+// sides with a staged-partner pipeline, then those of the pencil-load sides, each sorted by
 // cost (partners x grid points x log2 grid points), largest first; sets each cell's split.
 void build_batch(hse_plan plan, int split, void* const* vx_out) {
   struct Entry {
     double cost;
     BatchItem it;
   };
-  std::vector<Entry> list;
+  std::vector<Entry> list[2];
   for (size_t c = 0; c < plan->cells.size(); ++c) {
     const hse_problem& q = plan->cells[c]->p;
     BatchCell& bc = plan->h_cells[c];
@@ -760,24 +762,31 @@ void build_batch(hse_plan plan, int split, void* const* vx_out) {
     const int T = slots_for(q.grid[0]);
     const int ntiles = (q.n_tgt + T - 1) / T;
     const double n = q.grid[0];
+    int sp_unused = 0, br_unused = 0;
+    const int which = batched_stage_geometry(q.grid[0], &sp_unused, &br_unused) ? 0 : 1;
     for (int sp = 0; sp < ns; ++sp) {
       const int kp0 = (int)(((long long)sp * q.nk) / ns), kp1 = (int)(((long long)(sp + 1) * q.nk) / ns);
       const double cost = (double)(kp1 - kp0) * q.n_occ * n * n * n * std::log2(n);
-      for (int r = 0; r < q.nk * ntiles; ++r) list.push_back({cost, {(int)c, sp * q.nk * ntiles + r}});
+      for (int r = 0; r < q.nk * ntiles; ++r) list[which].push_back({cost, {(int)c, sp * q.nk * ntiles + r}});
     }
   }
-  std::stable_sort(list.begin(), list.end(), [](const Entry& x, const Entry& y) { return x.cost > y.cost; });
-  std::vector<BatchItem> items(list.size());
-  for (size_t i = 0; i < list.size(); ++i) items[i] = list[i].it;
+  std::vector<BatchItem> items;
+  for (int w = 0; w < 2; ++w) {
+    std::stable_sort(list[w].begin(), list[w].end(), [](const Entry& x, const Entry& y) { return x.cost > y.cost; });
+    for (const Entry& e : list[w]) items.push_back(e.it);
+  }
+  plan->nitems_staged = (int)list[0].size();
   plan->nitems = (int)items.size();
   cudaMemcpy(plan->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
 }
 
-// counter reset + persistent kernel + reduction of split cells (graph-capturable)
+// counter reset + the two persistent kernels + reduction of split cells (graph-capturable)
 cudaError_t run_batch(hse_plan plan, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(plan->d_counter, 0, sizeof(int), st);
-  BatchArgs b{plan->d_cells, plan->d_items, plan->nitems, plan->d_counter};
-  if (e == cudaSuccess) e = launch_pairconv_batched(b, plan->sms, st);
+  cudaError_t e = cudaMemsetAsync(plan->d_counter, 0, 2 * sizeof(int), st);
+  const BatchArgs staged{plan->d_cells, plan->d_items, plan->nitems_staged, plan->d_counter, plan->status};
+  const BatchArgs pencil{plan->d_cells, plan->d_items + plan->nitems_staged, plan->nitems - plan->nitems_staged,
+                         plan->d_counter + 1, plan->status};
+  if (e == cudaSuccess) e = launch_pairconv_batched(staged, pencil, plan->sms, st);
   if (e == cudaSuccess && plan->batch_split != 1) {
     reduce_splits_batched<<<plan->sms * 4, 256, 0, st>>>(plan->d_cells, (int)plan->cells.size());
     count_launch();
@@ -1052,7 +1061,7 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
   }
   if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_cells, (size_t)ncells * sizeof(BatchCell));
   if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_items, max_items * sizeof(BatchItem));
-  if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_counter, sizeof(int));
+  if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_counter, 2 * sizeof(int));
   if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->status, sizeof(int));
   if (rc == HSE_OK && e == cudaSuccess) e = cudaMemset(plan->status, 0, sizeof(int));
   if (rc == HSE_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking);
@@ -1104,6 +1113,14 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
     bc.pa = a;
     bc.final_out = (float2*)vx_out[c];
     bc.n = sub->p.grid[0];
+    int sp = 0, br = 0;
+    if (batched_stage_geometry(bc.n, &sp, &br)) {
+      const cudaError_t te = make_partner_tmap(&bc.tmap, u_occ[c], bc.n,
+                                               (long long)sub->p.nk * sub->p.n_occ * bc.n * bc.n, sp, br);
+      if (te != cudaSuccess) return cuda_fail(te);
+    } else {
+      std::memset(&bc.tmap, 0, sizeof(bc.tmap));
+    }
   }
   cudaError_t e = cudaSuccess;
   if (plan->batch_split == 0) {
@@ -1133,7 +1150,7 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
     if (e != cudaSuccess) return cuda_fail(e);
     plan->batch_split = best;
     build_batch(plan, best, vx_out);
-    // capture counter reset + persistent kernel + split reduction as one graph
+    // capture counter reset + persistent kernels + split reduction as one graph
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {

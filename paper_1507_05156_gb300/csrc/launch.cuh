@@ -29,6 +29,7 @@ int pairconv_c64_occupancy(int n, int mode, int blocks_per_sm);
 
 // Batched launch over cells of unequal grid sides (batched.cu).
 struct BatchCell {
+  CUtensorMap tmap;     // the cell's partner array for the staged pipeline (sides with one)
   PairArgs pa;          // the cell's launch arguments (pa.out: final output or split buffer)
   float2* final_out;    // the cell's V_x u output
   int n;                // grid side
@@ -42,9 +43,15 @@ struct BatchArgs {
   const BatchItem* items;
   int nitems;
   int* counter;         // zeroed before each launch
+  int* status;          // device status word
 };
 bool batched_side_supported(int n);
-cudaError_t launch_pairconv_batched(const BatchArgs& b, int sms, cudaStream_t stream);
+// Stage geometry of the side's staged pipeline in the batched launch (pitch and box rows of
+// its tensor map); false for sides that run the pencil-load item there.
+bool batched_stage_geometry(int n, int* sp, int* box_rows);
+// The two persistent kernels of a batch: the staged-partner items and the pencil-load items
+// (either list may be empty), in stream order.
+cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& pencil, int sms, cudaStream_t stream);
 
 // One staged FP64 1-D transform pass along an axis of length L with element stride inner.
 cudaError_t launch_staged_fft(int L, int dir, double2* work, size_t nbatch, int N, int inner, cudaStream_t stream);

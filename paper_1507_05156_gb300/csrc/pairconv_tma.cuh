@@ -459,59 +459,45 @@ __device__ __forceinline__ int next_partner(const float* occ_sh, const PairArgs&
   return q;
 }
 
-// tmap: the partner array as rows of z-pencils, box {2 SP floats, BR rows}.  L: the pencil
-// layout (LayoutSeq, LayoutOne or LayoutSplit).
+// Pipeline state of the staged kernel that lives in shared memory beside the grids and
+// persists across the work items of a persistent launch.
+struct StagedShared {
+  uint64_t mbar[2];   // stage buffer b's copy has landed
+  int abort;          // a bounded wait expired: issue and wait no more
+  float occ[kOccCache];
+};
+
+// One work item (split, k, owner tile) of the staged-partner pipeline: the item's partners
+// stream through the two stage buffers, the owner orbital and the accumulators stay in TMEM.
+// tmap: the partner array as rows of z-pencils, box {2 SP floats, BR rows} (in kernel
+// parameter space or global memory).  phase0 / phase1: the parities the stage barriers are
+// expected to complete next (carried from item to item).  on: this thread's warp takes part
+// (a persistent block may be larger than the layout's); every thread of the block must call
+// this, because it synchronises the block.  sbase must be 128-byte aligned.  Returns false
+// after a timed-out wait (the caller stops).
 template <int n, int MODE, template <int> class L>
-__global__ void __launch_bounds__(L<n>::THREADS, 1)
-    pairconv_tma_kernel(const PairArgs args, const __grid_constant__ CUtensorMap tmap) {
+__device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensorMap* tmap, int item, char* sbase,
+                                            uint32_t tbase, StagedShared& sh, uint32_t& phase0, uint32_t& phase1,
+                                            bool on) {
   using G = Geo<n>;
   using Lay = L<n>;
   using S = GeoS<n, Lay>;
   static_assert(MODE == MODE_APPLY || MODE == MODE_ENERGY || MODE == MODE_DOT, "owner = target modes only");
-  extern __shared__ __align__(128) float4 smem4[];
-  __shared__ uint32_t tmem_base_sh;
-  __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ int abort_sh;
-  __shared__ float occ_sh[kOccCache];
-
   const int tid = threadIdx.x;
-  // TMA destinations must be 128-byte aligned: align the dynamic shared memory base (128 bytes
-  // of slack are requested), and refuse to run, recording the failure, should it still not be.
-  char* sbase = reinterpret_cast<char*>(smem4);
-  sbase += (128u - (smem_addr_u32(sbase) & 127u)) & 127u;
-  if ((smem_addr_u32(sbase) & 127u) != 0) {
-    if (tid == 0 && args.status) atomicExch(args.status, kStatusDevice);
-    return;
-  }
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  const bool valid = tid < G::T * Lay::TS;
+  const bool valid = on && tid < G::T * Lay::TS;
   const int slot = valid ? tid / Lay::TS : 0;
   const int t = valid ? tid - slot * Lay::TS : 0;
   float2* grids = reinterpret_cast<float2*>(sbase);
   float2* g = grids + slot * Lay::GRID_CPX;
   float2* stage = reinterpret_cast<float2*>(sbase + S::GRIDS_BYTES);
-
-  if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
-    abort_sh = 0;
-    mbar_fence_init();
-  }
-  if (warp == 0) {
-    tmem_alloc(&tmem_base_sh, S::TMEM_COLS);
-    tmem_relinquish();
-  }
-  tmem_fence_before_sync();
-  __syncthreads();
-  tmem_fence_after_sync();
-  const uint32_t tbase = tmem_base_sh;
   const uint32_t trow0 = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * S::COLS_PER_WARP);
   const uint32_t town = trow0 + (uint32_t)Lay::OWN;
 
   const int per_split = args.nk_own * args.ntiles;
-  const int split = blockIdx.x / per_split;
-  const int rem = blockIdx.x - split * per_split;
+  const int split = item / per_split;
+  const int rem = item - split * per_split;
   const int k = rem / args.ntiles;
   const int band = (rem - k * args.ntiles) * G::T + slot;
   const bool active = valid && band < args.n_own;
@@ -527,9 +513,9 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
       const int kp = kp_begin + q / args.n_part, j = q - (q / args.n_part) * args.n_part;
       const int row0 = (kp * args.n_part + j) * G::NN;
       float2* dst = stage + buf * S::STAGE_CPX;
-      mbar_arrive_expect_tx(&mbar[buf], (uint32_t)S::STAGE_TX);
+      mbar_arrive_expect_tx(&sh.mbar[buf], (uint32_t)S::STAGE_TX);
 #pragma unroll
-      for (int b = 0; b < S::NB; ++b) tensor_copy_2d_g2s(dst + b * S::BR * S::SP, &tmap, 0, row0 + b * S::BR, &mbar[buf]);
+      for (int b = 0; b < S::NB; ++b) tensor_copy_2d_g2s(dst + b * S::BR * S::SP, tmap, 0, row0 + b * S::BR, &sh.mbar[buf]);
     }
     __syncwarp();
   };
@@ -537,14 +523,17 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
   // the item's partner occupations, once (work items are sized so that they fit)
   for (int i = tid; i < npairs && i < kOccCache; i += blockDim.x) {
     const int kp = kp_begin + i / args.n_part, j = i - (i / args.n_part) * args.n_part;
-    occ_sh[i] = (float)args.occ[kp * args.n_occ + j];
+    sh.occ[i] = (float)args.occ[kp * args.n_occ + j];
   }
   __syncthreads();
-  int q = next_partner(occ_sh, args, kp_begin, 0, npairs);
-  if (warp == 0 && q < npairs && args.inject != 1) fill(q, 0);
+  int q = next_partner(sh.occ, args, kp_begin, 0, npairs);
+  if (warp == 0 && q < npairs && args.inject != 1 && !sh.abort) {
+    fence_proxy_async_smem();  // earlier generic accesses to this shared memory come first
+    fill(q, 0);
+  }
 
   // owner orbital into TMEM, accumulators to zero
-  const bool reg = Lay::regular(t);  // warp-uniform
+  const bool reg = on && Lay::regular(t);  // warp-uniform
 #pragma unroll 1
   for (int ps = 0; ps < (reg ? Lay::PPT : 0); ++ps) {
     cpx<float> w[n];
@@ -560,52 +549,52 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
     for (int e = 0; e < G::ROW; ++e) r[e] = 0.f;
     TmemRow<G::ROW>::store(trow0 + (uint32_t)(ps * G::ROW), r);
   }
-  Lay::extra_init(t, own, trow0);
+  if (on) Lay::extra_init(t, own, trow0);
 
-  uint32_t phase0 = 0, phase1 = 0;
   int buf = 0;
   int cur_kp = -1;
   while (q < npairs) {
     const int kp = kp_begin + q / args.n_part;
-    const float f = item_occ(occ_sh, args, kp_begin, q);
+    const float f = item_occ(sh.occ, args, kp_begin, q);
     if (kp != cur_kp) {
       const int qrow = args.qidx[k * args.nk_part + kp];
-      Lay::cache_row(t, trow0, args.vtab + (size_t)qrow * G::N, args.scale);
+      if (on) Lay::cache_row(t, trow0, args.vtab + (size_t)qrow * G::N, args.scale);
       cur_kp = kp;
     }
     // partner u_j has landed in stage[buf]
     const uint32_t ph = buf ? phase1 : phase0;
-    if (!abort_sh) {
-      if (!mbar_wait_bounded(&mbar[buf], ph)) {
-        abort_sh = 1;
+    if (!sh.abort) {
+      if (!mbar_wait_bounded(&sh.mbar[buf], ph)) {
+        sh.abort = 1;
         if (args.status) atomicExch(args.status, kStatusTimeout);
       }
     }
     if (buf) phase1 ^= 1u; else phase0 ^= 1u;
     const float2* stg = stage + buf * S::STAGE_CPX;
-    Lay::z_forward(g, t, valid, stg, trow0);
+    if (on) Lay::z_forward(g, t, valid, stg, trow0);
     __syncthreads();
     // every thread is past its last read of stage[buf ^ 1]: refill it with the next partner
-    const int qn = next_partner(occ_sh, args, kp_begin, q + 1, npairs);
-    if (warp == 0 && qn < npairs && !abort_sh) {
+    const int qn = next_partner(sh.occ, args, kp_begin, q + 1, npairs);
+    if (warp == 0 && qn < npairs && !sh.abort) {
       fence_proxy_async_smem();
       fill(qn, buf ^ 1);
     }
-    Lay::template y<-1>(g, t, valid);
+    if (on) Lay::template y<-1>(g, t, valid);
     __syncthreads();
-    Lay::x(g, t, valid, trow0, f);
+    if (on) Lay::x(g, t, valid, trow0, f);
     __syncthreads();
-    Lay::template y<+1>(g, t, valid);
+    if (on) Lay::template y<+1>(g, t, valid);
     __syncthreads();
-    Lay::z_inverse(g, t, stg, trow0);
+    if (on) Lay::z_inverse(g, t, stg, trow0);
     q = qn;
     buf ^= 1;
   }
   __syncthreads();
-  if (abort_sh && tid == 0) {
+  const bool ok = !sh.abort;
+  if (!ok && tid == 0) {
     // a copy may still be in flight after a timeout: give it one more bounded chance to land
-    mbar_wait_bounded(&mbar[0], phase0);
-    mbar_wait_bounded(&mbar[1], phase1);
+    mbar_wait_bounded(&sh.mbar[0], phase0);
+    mbar_wait_bounded(&sh.mbar[1], phase1);
   }
 
   if constexpr (MODE == MODE_APPLY) {
@@ -620,7 +609,7 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
         for (int e = 0; e < n / 2; ++e) o[e] = make_float4(acc[4 * e], acc[4 * e + 1], acc[4 * e + 2], acc[4 * e + 3]);
       }
     }
-    Lay::extra_store(t, obase, trow0, active);
+    if (on) Lay::extra_store(t, obase, trow0, active);
   } else {
     const float2* lhs = (MODE == MODE_ENERGY) ? own : args.part2 + ((size_t)k * args.n_own + bandc) * G::N;
     double d = 0.0;
@@ -633,7 +622,7 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
 #pragma unroll
       for (int e = 0; e < n; ++e) d += (double)w[e].x * (double)acc[2 * e] + (double)w[e].y * (double)acc[2 * e + 1];
     }
-    d += Lay::extra_dot(t, lhs, trow0);
+    if (on) d += Lay::extra_dot(t, lhs, trow0);
     __syncthreads();
     double* red = reinterpret_cast<double*>(sbase);
     red[tid] = valid ? d : 0.0;
@@ -645,11 +634,52 @@ __global__ void __launch_bounds__(L<n>::THREADS, 1)
       args.partial[split * args.split_stride + (size_t)k * args.n_own + band] = sum;
     }
   }
+  __syncthreads();  // the grids, the reduction scratch and the occupation cache are reused next
+  return ok;
+}
 
+// Aligns the dynamic shared memory base to 128 bytes for TMA (128 bytes of slack are
+// requested); null (and the status word set) should it still not be aligned.
+__device__ __forceinline__ char* staged_smem_base(float4* smem4, int* status) {
+  char* sbase = reinterpret_cast<char*>(smem4);
+  sbase += (128u - (smem_addr_u32(sbase) & 127u)) & 127u;
+  if ((smem_addr_u32(sbase) & 127u) != 0) {
+    if (threadIdx.x == 0 && status) atomicExch(status, kStatusDevice);
+    return nullptr;
+  }
+  return sbase;
+}
+
+// One work item per CTA.  L: the pencil layout (LayoutSeq, LayoutOne or LayoutSplit).
+template <int n, int MODE, template <int> class L>
+__global__ void __launch_bounds__(L<n>::THREADS, 1)
+    pairconv_tma_kernel(const PairArgs args, const __grid_constant__ CUtensorMap tmap) {
+  using S = GeoS<n, L<n>>;
+  extern __shared__ __align__(128) float4 smem4[];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ StagedShared sh;
+  char* sbase = staged_smem_base(smem4, args.status);
+  if (!sbase) return;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(&sh.mbar[0], 1);
+    mbar_init(&sh.mbar[1], 1);
+    sh.abort = 0;
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base_sh, S::TMEM_COLS);
+    tmem_relinquish();
+  }
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
-  if (warp == 0) tmem_dealloc(tbase, S::TMEM_COLS);
+  uint32_t phase0 = 0, phase1 = 0;
+  staged_item<n, MODE, L>(args, &tmap, blockIdx.x, sbase, tmem_base_sh, sh, phase0, phase1, true);
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(tmem_base_sh, S::TMEM_COLS);
 }
 
 }  // namespace hse
