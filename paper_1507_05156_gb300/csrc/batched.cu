@@ -6,7 +6,8 @@
 // split in two lists by the pipeline their side runs, each with its own persistent kernel:
 //   * staged-partner items (sides 8, 12, 18, 20; pairconv_tma.cuh): the partner orbitals
 //     stream in by TMA from the cell's tensor map into two stage buffers, the owner orbital
-//     and the accumulators stay in Tensor Memory.  512 threads (20^3 with lane-split pencils);
+//     and the accumulators stay in Tensor Memory.  512 threads (8^3 with eight owner slots of
+//     one pencil per thread);
 //   * pencil-load items (sides 16, 24; pairconv_c64.cuh): orbitals are read as pencils
 //     through L1.  That kernel keeps only its own shared-memory footprint so that L1 keeps
 //     the rest of the SM's storage: with the staged kernel's 208 KB of shared memory
@@ -28,12 +29,12 @@ using SeqS = GeoS<n, LayoutSeq<n>>;
 template <int n>
 using OneS = GeoS<n, LayoutOne<n>>;
 
-static_assert(LayoutSplit<20>::THREADS == kStagedThreads && LayoutOne<8>::THREADS <= kStagedThreads &&
+static_assert(LayoutOne<20>::THREADS <= kStagedThreads && LayoutOne<8>::THREADS <= kStagedThreads &&
                   LayoutSeq<12>::THREADS <= kStagedThreads && LayoutOne<18>::THREADS <= kStagedThreads,
               "staged batched block too small for a side's layout");
 static_assert(Geo<16>::THREADS <= kPencilThreads && Geo<24>::THREADS <= kPencilThreads,
               "pencil-load batched block too small");
-static_assert(OneS<8>::FITS && SeqS<12>::FITS && OneS<18>::FITS && GeoS<20, LayoutSplit<20>>::FITS,
+static_assert(OneS<8>::FITS && SeqS<12>::FITS && OneS<18>::FITS && OneS<20>::FITS,
               "staged layouts of the batched kernel must fit");
 
 // One staged item as a call of its own: each side's pipeline gets the whole register budget
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) pairconv_batched_staged_ker
       case 8: ok = staged_call<8, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutOne<8>::WARPS); break;
       case 12: ok = staged_call<12, MODE, LayoutSeq>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutSeq<12>::WARPS); break;
       case 18: ok = staged_call<18, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutOne<18>::WARPS); break;
-      case 20: ok = staged_call<20, MODE, LayoutSplit>(c, wi.item, sbase, tbase, sh, ph0, ph1, true); break;
+      case 20: ok = staged_call<20, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutOne<20>::WARPS); break;
       default: break;  // the host puts only the sides above in this list
     }
     if (!ok) break;  // a bounded wait expired (uniform: read after a block barrier)
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kPencilThreads, 1) pairconv_batched_pencil_ker
 
 constexpr size_t max_c(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kStagedSmem = max_c(max_c(OneS<8>::SMEM_REQUEST, SeqS<12>::SMEM_REQUEST),
-                                     max_c(OneS<18>::SMEM_REQUEST, GeoS<20, LayoutSplit<20>>::SMEM_REQUEST));
+                                     max_c(OneS<18>::SMEM_REQUEST, OneS<20>::SMEM_REQUEST));
 // >= 118784: a second CTA (which would need TMEM too) never fits
 constexpr size_t kPencilSmem = max_c(max_c(Geo<16>::SMEM_BYTES, Geo<24>::SMEM_BYTES), (size_t)118784);
 

@@ -186,14 +186,57 @@ __device__ __forceinline__ void stage_y(float2* g, int t, bool valid) {
   }
 }
 
+// X-stage pencil of thread t when each thread owns one X pencil: the first R of the n^2
+// pencils (y, z), p = y n + z, grouped 16 to a half-warp with distinct 8-byte banks
+// (y P + z mod 16) as long as every bank class still has a member, the rest of those R after
+// them; pencils R and up keep their place.  With the pitch P = n the identity already has
+// this property; with P != n (20^3: P = 21) consecutive pencils wrap from one y row to the
+// next inside a half-warp and two of them share a bank.
+template <int n>
+struct XPermTable {
+  unsigned short v[n * n];
+};
+template <int n, int R>
+constexpr XPermTable<n> make_xperm() {
+  constexpr int NN = n * n, P = Geo<n>::P;
+  XPermTable<n> t{};
+  unsigned short bucket[16][NN / 16 + 16] = {};
+  int cnt[16] = {};
+  for (int p = 0; p < R; ++p) {
+    const int r = ((p / n) * P + p % n) % 16;
+    bucket[r][cnt[r]++] = (unsigned short)p;
+  }
+  int ming = NN;
+  for (int r = 0; r < 16; ++r) ming = cnt[r] < ming ? cnt[r] : ming;
+  int k = 0;
+  for (int g = 0; g < ming; ++g)
+    for (int r = 0; r < 16; ++r) t.v[k++] = bucket[r][g];
+  for (int r = 0; r < 16; ++r)
+    for (int g = ming; g < cnt[r]; ++g) t.v[k++] = bucket[r][g];
+  for (int p = R; p < NN; ++p) t.v[k++] = (unsigned short)p;
+  return t;
+}
+template <int n, int R>
+__device__ const XPermTable<n> kXPerm = make_xperm<n, R>();
+
+template <int n, bool XP, int R = n * n>
+__device__ __forceinline__ int x_pencil(int p) {
+  if constexpr (XP && Geo<n>::P != n) {
+    return kXPerm<n, R>.v[p];
+  } else {
+    return p;
+  }
+}
+
 // Stage X: FFT, multiply by the kernel row (cached in TMEM, already times -alpha/(N_k N))
 // times the occupation f, inverse FFT, for the PPT pencils.  Warp-wide (TMEM loads).
-template <int n, int PPT = 2>
+// XP (one pencil per thread): the bank-spread X-pencil order of x_pencil over the first XR.
+template <int n, int PPT = 2, bool XP = false, int XR = n * n>
 __device__ __forceinline__ void stage_x(float2* g, int t, bool valid, uint32_t ttab, float f) {
   using G = Geo<n>;
 #pragma unroll 1
   for (int ps = 0; ps < PPT; ++ps) {
-    const Pencil<n> pc(t + ps * (G::NN / PPT));
+    const Pencil<n> pc(x_pencil<n, XP, XR>(t + ps * (G::NN / PPT)));
     float tv[n];
     TmemRow<n>::load(ttab + (uint32_t)(ps * n), tv);
     cpx<float> v[n];
@@ -211,12 +254,12 @@ __device__ __forceinline__ void stage_x(float2* g, int t, bool valid, uint32_t t
 }
 
 // Kernel row v(|G+q|) * scale of this thread's PPT X-pencils into the TMEM cache.
-template <int n, int PPT = 2>
+template <int n, int PPT = 2, bool XP = false, int XR = n * n>
 __device__ __forceinline__ void cache_kernel_row(int t, uint32_t ttab, const float* __restrict__ vrow, float scale) {
   using G = Geo<n>;
 #pragma unroll 1
   for (int ps = 0; ps < PPT; ++ps) {
-    const int p = t + ps * (G::NN / PPT);
+    const int p = x_pencil<n, XP, XR>(t + ps * (G::NN / PPT));
     float tv[n];
 #pragma unroll
     for (int e = 0; e < n; ++e) tv[e] = __ldg(vrow + e * G::NN + p) * scale;

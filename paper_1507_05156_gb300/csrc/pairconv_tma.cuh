@@ -117,7 +117,8 @@ __device__ __forceinline__ void stage_z_inverse_staged(const float2* g, int t, c
 //                over the four warp schedulers of the SM; one pencil per thread leaves the
 //                busiest scheduler fewer pencil passes when n^2 / 128 has a small fractional
 //                part (18^3: 3 instead of 4) and gives each scheduler more warps to hide
-//                shared-memory latency.
+//                shared-memory latency.  Its X stage takes the pencils in the bank-spread
+//                order of x_pencil (no bank conflicts where the pitch P differs from n).
 //   LayoutSplit: one pencil per thread for the first R = 128 floor(n^2 / 128) pencils (whole
 //                warps, the same count on every scheduler), plus four warps, one per scheduler,
 //                that transform the L = n^2 - R pencils left over with their DFT split over
@@ -128,7 +129,9 @@ __device__ __forceinline__ void stage_z_inverse_staged(const float2* g, int t, c
 // TMEM columns of a warp: [acc (PPT pencils) | kernel rows (PPT) | owner u_i (PPT) | extra].
 // ---------------------------------------------------------------------------------------
 
-template <int n, int PPT_>
+// XP: with one pencil per thread, the X-stage pencils go to threads in the bank-spread order
+// of x_pencil.
+template <int n, int PPT_, bool XP = (PPT_ == 1)>
 struct LayoutLin {
   using G = Geo<n>;
   static constexpr int PPT = PPT_;
@@ -152,10 +155,10 @@ struct LayoutLin {
     stage_y<n, DIR, PPT>(g, t, valid);
   }
   static __device__ __forceinline__ void x(float2* g, int t, bool valid, uint32_t trow0, float f) {
-    stage_x<n, PPT>(g, t, valid, trow0 + (uint32_t)TAB, f);
+    stage_x<n, PPT, XP>(g, t, valid, trow0 + (uint32_t)TAB, f);
   }
   static __device__ __forceinline__ void cache_row(int t, uint32_t trow0, const float* vrow, float scale) {
-    cache_kernel_row<n, PPT>(t, trow0 + (uint32_t)TAB, vrow, scale);
+    cache_kernel_row<n, PPT, XP>(t, trow0 + (uint32_t)TAB, vrow, scale);
   }
   // pencils beyond the regular ones (LayoutSplit): none here
   static __device__ __forceinline__ bool regular(int) { return true; }
@@ -226,7 +229,9 @@ struct LayoutSplit {
   static constexpr int OWN = TAB + n;
   static constexpr int EXTRA = OWN + G::ROW;
   static constexpr int COLS_PER_WARP = EXTRA + SG::COLS;
-  using Reg = LayoutLin<n, 1>;  // the regular pencils 0 .. R-1 (pencil = thread)
+  // the regular pencils 0 .. R-1 (pencil = thread in every stage: with the split pencils
+  // beside them, the bank-spread X order measured slower, 35.3 against 34.7 ms at 20^3)
+  using Reg = LayoutLin<n, 1, false>;
   static __device__ __forceinline__ bool regular(int t) { return t < SG::R; }
 
   // role of this lane in the hosting warp: s = scheduler, A: (pencil, b), B: (pencil, k1)
@@ -239,9 +244,10 @@ struct LayoutSplit {
       const int first = SG::R + (warp - SG::HOST0) * SG::PER;
       a_on = host && lane < SG::PER * SG::N2;
       b_on = host && lane < SG::PER * SG::N1;
-      pa = first + lane / SG::N2;
+      // lanes without a role keep an in-range pencil (its index also selects table entries)
+      pa = a_on ? first + lane / SG::N2 : SG::R;
       b = lane % SG::N2;
-      pb = first + lane / SG::N1;
+      pb = b_on ? first + lane / SG::N1 : SG::R;
       k1 = lane % SG::N1;
       k1e1 = (k1 * SG::E1) % n;
     }
@@ -392,7 +398,8 @@ struct LayoutSplit {
       float kv[SG::KW];
 #pragma unroll
       for (int k2 = 0; k2 < SG::KW; ++k2)
-        kv[k2] = (r.b_on && k2 < SG::N2) ? __ldg(vrow + SG::crt(r.k1e1, k2) * G::NN + r.pb) * scale : 0.f;
+        kv[k2] = (r.b_on && k2 < SG::N2) ? __ldg(vrow + SG::crt(r.k1e1, k2) * G::NN + r.pb) * scale
+                                         : 0.f;
       TmemRow<SG::KW>::store(trow0 + (uint32_t)(EXTRA + SG::C_KER), kv);
     }
     if (regular(t)) Reg::cache_row(t, trow0, vrow, scale);
