@@ -10,6 +10,15 @@ Only ``tests/`` may use it.  Follows arXiv:1507.05156:
   Hamiltonian at t + dt/2 approximated by the one at t (the choice the paper reports as
   sufficient for HSE).  The synthetic Hamiltonian used here is h = T[A(t)] + V_x[psi(t)]:
   the pseudopotential, Hartree and semilocal terms of the paper need data that is not here.
+* Sec. II A, Eqs. "current_dns" / "current_elec": the spatially averaged electric current
+  J(t) = -(1/Omega) int_Omega j dr, j = sum_i Re[psi_i* (-i grad + A) psi_i] (atomic units,
+  e = m = hbar = 1, e/c absorbed), without the pseudopotential's nonlocal part J_NL.  Each
+  orbital counts with g_s f_{i,k} / N_k.  With psi = e^{ik.r} u, u = sum_G c_G e^{iG.r}
+  (c = the 1/N forward transform), int_Omega psi* (-i grad + A) psi = Omega sum_G |c_G|^2
+  (G + k + A), so J = -sum_{k,i} (g_s f_{i,k} / N_k) sum_G |c_G|^2 (G + k + A).
+* Sec. IV (laser pulse): A(t) = -(E0 / w) cos(w t) sin^2(pi t / T_d) along a direction for
+  0 < t < T_d (zero otherwise), E(t) = -dA/dt, and the energy given to the electrons per unit
+  volume W(t) = int^t J(t') . E(t') dt' (Eq. for W in Sec. V).
 """
 from __future__ import annotations
 
@@ -62,3 +71,58 @@ def taylor_norm_factor(x: float, order: int = 4) -> float:
     """|sum_{n<=order} (-i x)^n / n!|^2 for real x (the truncated series on an eigenvector)."""
     s = sum((-1j * x) ** n / math.factorial(n) for n in range(order + 1))
     return float(abs(s) ** 2)
+
+
+def current(u, occ, kpts, lattice, grid, A, spin_degeneracy: float = 2.0) -> np.ndarray:
+    """J = -sum_{k,i} (g_s f_{i,k} / N_k) sum_G |c_G|^2 (G + k + A), c = forward transform of
+    u_{i,k} (Eqs. current_dns / current_elec without J_NL), a 3-vector."""
+    grid = tuple(int(g) for g in grid)
+    u = np.asarray(u, dtype=np.complex128).reshape(np.shape(u)[:2] + grid)
+    occ = np.asarray(occ, dtype=np.float64)
+    G = ho.g_vectors(grid, lattice)
+    nk = u.shape[0]
+    J = np.zeros(3)
+    for k in range(nk):
+        gk = G + np.asarray(kpts[k]) + np.asarray(A, dtype=np.float64)       # [grid][3]
+        c = ho.forward_transform(u[k])                                        # [nb][grid]
+        w = np.abs(c) ** 2
+        J -= spin_degeneracy / nk * np.einsum("b,bxyz,xyzc->c", occ[k], w, gk)
+    return J
+
+
+def pulse_vector_potential(t: float, E0: float, w: float, Td: float, direction) -> np.ndarray:
+    """A(t) = -(E0 / w) cos(w t) sin^2(pi t / T_d) d for 0 <= t <= T_d, else 0 (Sec. IV)."""
+    d = np.asarray(direction, dtype=np.float64)
+    if t <= 0.0 or t >= Td:
+        return np.zeros(3)
+    return -(E0 / w) * math.cos(w * t) * math.sin(math.pi * t / Td) ** 2 * d
+
+
+def pulse_field(t: float, E0: float, w: float, Td: float, direction) -> np.ndarray:
+    """E(t) = -dA/dt of pulse_vector_potential, differentiated by hand."""
+    d = np.asarray(direction, dtype=np.float64)
+    if t <= 0.0 or t >= Td:
+        return np.zeros(3)
+    s, c = math.sin(math.pi * t / Td), math.cos(math.pi * t / Td)
+    dA = (E0 / w) * (w * math.sin(w * t) * s * s - math.cos(w * t) * 2.0 * s * c * math.pi / Td)
+    return -dA * d
+
+
+def propagate_pulse(psi0, occ, kpts, lattice, grid, omega, alpha, dt, nsteps, E0, w, Td, direction,
+                    spin_degeneracy: float = 2.0):
+    """nsteps Taylor steps under the pulse; step s (t_s = s dt -> t_s + dt) uses h frozen at
+    psi(t_s) with A(t_s).  Returns (psi, J [nsteps+1][3], W [nsteps+1]) with J_s = J(t_s)
+    from psi(t_s) and A(t_s), and W by the trapezoidal rule on J . E."""
+    psi = np.array(psi0, dtype=np.complex128, copy=True)
+    Js, Ws = [], [0.0]
+    for s in range(nsteps + 1):
+        t = s * dt
+        A = pulse_vector_potential(t, E0, w, Td, direction)
+        Js.append(current(psi, occ, kpts, lattice, grid, A, spin_degeneracy))
+        if s > 0:
+            e0 = pulse_field(t - dt, E0, w, Td, direction)
+            e1 = pulse_field(t, E0, w, Td, direction)
+            Ws.append(Ws[-1] + 0.5 * dt * (Js[-2] @ e0 + Js[-1] @ e1))
+        if s < nsteps:
+            psi = taylor_step(psi, occ, kpts, lattice, grid, A, omega, alpha, dt)
+    return psi, np.array(Js), np.array(Ws)

@@ -78,3 +78,90 @@ def test_propagate_uses_vector_potential_of_time():
     s1 = td.taylor_step(psi, occ, kpts, lattice, grid, np.zeros(3), 0.2, 0.0, 0.02)
     s2 = td.taylor_step(s1, occ, kpts, lattice, grid, -E * 0.02, 0.2, 0.0, 0.02)
     np.testing.assert_allclose(two, s2, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Current (Eqs. current_dns / current_elec) and the laser-pulse driver (Sec. IV / V)
+# ---------------------------------------------------------------------------
+
+def test_current_of_plane_waves_closed_form():
+    """One plane wave Omega^-1/2 e^{iG_k r} per k-point: J = -sum_k g_s f_k / (N_k Omega) (G_k + k + A)."""
+    grid = (5, 4, 6)
+    A_ = TRICLINIC
+    Om = abs(np.linalg.det(A_))
+    b = 2 * np.pi * np.linalg.inv(A_).T
+    r = _positions(grid, A_)
+    kpts = np.array([[0.05, -0.11, 0.02], [-0.2, 0.07, 0.13]])
+    ms = [(1, -1, 2), (-2, 1, 0)]
+    u = np.zeros((2, 1) + grid, complex)
+    Gs = []
+    for k, m in enumerate(ms):
+        G = m[0] * b[0] + m[1] * b[1] + m[2] * b[2]
+        Gs.append(G)
+        u[k, 0] = np.exp(1j * (r @ G)) / np.sqrt(Om)
+    occ = np.array([[0.7], [0.4]])
+    A = np.array([0.03, -0.01, 0.02])
+    J = td.current(u, occ, kpts, A_, grid, A, spin_degeneracy=2.0)
+    expect = -sum(2.0 * occ[k, 0] / (2 * Om) * (Gs[k] + kpts[k] + A) for k in range(2))
+    np.testing.assert_allclose(J, expect, rtol=0, atol=1e-14 * np.abs(expect).max())
+
+
+def test_current_diamagnetic_shift_and_zero_for_real_orbitals():
+    """J(A') - J(A) = -(g_s / (N_k Omega)) sum f (A' - A) for normalised orbitals; real orbitals at
+    k = 0 on an odd grid (every G has its -G) carry no current at A = 0."""
+    grid = (5, 3, 5)
+    kpts = np.array([[0.0, 0.0, 0.0], [0.1, 0.05, -0.08]])
+    rng = np.random.default_rng(9)
+    u = inputs.orthonormal_orbitals(rng, grid, TRICLINIC, kpts, 3, ecut=30.0)
+    occ = np.array([[1.0, 0.6, 0.2], [0.9, 0.5, 0.1]])
+    Om = abs(np.linalg.det(TRICLINIC))
+    A0, A1 = np.array([0.01, 0.0, -0.02]), np.array([-0.04, 0.03, 0.01])
+    d = td.current(u, occ, kpts, TRICLINIC, grid, A1) - td.current(u, occ, kpts, TRICLINIC, grid, A0)
+    np.testing.assert_allclose(d, -2.0 / (2 * Om) * occ.sum() * (A1 - A0), rtol=1e-12, atol=0)
+    ur = np.real(u[:1]).astype(complex)
+    ur /= np.sqrt(np.sum(np.abs(ur) ** 2, axis=(2, 3, 4), keepdims=True) * Om / np.prod(grid))
+    J = td.current(ur, np.ones((1, 3)), kpts[:1], TRICLINIC, grid, np.zeros(3))
+    assert np.abs(J).max() < 1e-15
+
+
+def test_pulse_field_is_minus_dA_dt_and_vanishes_outside():
+    E0, w, Td, d = 0.01, 0.057, 400.0, (0.0, 0.0, 1.0)
+    for t in (13.0, 101.7, 250.2, 399.0):
+        h = 1e-4
+        num = -(td.pulse_vector_potential(t + h, E0, w, Td, d) - td.pulse_vector_potential(t - h, E0, w, Td, d)) / (2 * h)
+        np.testing.assert_allclose(td.pulse_field(t, E0, w, Td, d), num, rtol=1e-7, atol=1e-12)
+    for t in (-1.0, 0.0, Td, Td + 5):
+        assert np.all(td.pulse_vector_potential(t, E0, w, Td, d) == 0)
+        assert np.all(td.pulse_field(t, E0, w, Td, d) == 0)
+
+
+def test_pulse_on_free_plane_wave_work_closed_form():
+    """alpha = 0, one plane wave: it stays an eigenvector of h(t_s) with eps_s = |G + k + A_s|^2 / 2,
+    so each step multiplies its norm by the truncated-series factor F(eps_s dt) and
+    J_s = -c (G + k + A_s) prod_{j<s} F(eps_j dt), c = g_s f / (N_k Omega).  The work
+    W(t) = int J . E = c [(G + k) . A + |A|^2 / 2]_0^t (E = -dA/dt) is followed by the trapezoidal
+    W to O(dt^2) and returns to 0 after the pulse."""
+    grid = (4, 4, 4)
+    A_ = inputs.cubic_lattice(6.0)
+    Om = 6.0 ** 3
+    b = 2 * np.pi / 6.0
+    G = np.array([b, 0.0, -b])
+    u = np.exp(1j * (_positions(grid, A_) @ G))[None, None] / np.sqrt(Om)
+    k = np.array([[0.02, 0.0, 0.01]])
+    E0, w, Td, d = 0.02, 0.4, 40.0, (1.0, 0.0, 0.0)
+    dt, nsteps = 0.05, 900
+    psi, J, W = td.propagate_pulse(u, np.ones((1, 1)), k, A_, grid, 0.2, 0.0, dt, nsteps, E0, w, Td, d)
+    c = 2.0 / Om
+    # trapezoidal-rule error bound dt^2 / 12 * T_d * max |(J . E)''|, with
+    # |(J . E)''| <= c E0 (|G + k| + E0 / w) (w + 2 pi / T_d)^2
+    tol = dt ** 2 / 12 * Td * c * E0 * (np.abs(G + k[0]).max() + E0 / w) * (w + 2 * np.pi / Td) ** 2
+    norm = 1.0
+    for s in range(nsteps + 1):
+        A = td.pulse_vector_potential(s * dt, E0, w, Td, d)
+        gk = G + k[0] + A
+        if s % 150 == 0:
+            np.testing.assert_allclose(J[s], -c * gk * norm, rtol=1e-12, atol=1e-15)
+            Wex = c * ((G + k[0]) @ A + 0.5 * A @ A)
+            assert abs(W[s] - Wex) <= tol
+        norm *= td.taylor_norm_factor(0.5 * (gk @ gk) * dt)
+    assert abs(W[-1]) <= tol
