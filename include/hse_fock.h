@@ -179,6 +179,34 @@ const char *hse_strerror(int code);
 int hse_exchange_energy_noalloc(const hse_problem *p, const void *u_occ, const double *occ,
                                 double *e_x, hse_stream_t stream);
 
+/* One fourth-order Taylor step of the time-dependent Kohn-Sham equation (Sec. II C, "time
+ * evolution": the propagator exp[h dt / i] expanded to fourth order, with the Hamiltonian at
+ * t + dt/2 taken at t, the choice the paper reports as sufficient for HSE):
+ *   psi_out = sum_{n=0}^{4} (-i dt h)^n / n! psi,   h = T[A] + V_x[psi]
+ * with T the velocity-gauge kinetic term of hse_kinetic_apply and V_x built from psi itself
+ * (the plan's occupied set) with occupations occ; the Hamiltonian is frozen over the step.
+ *   psi, psi_out device [nk][n_occ][N] (the plan's dtype; the plan must have n_tgt == n_occ);
+ *                must not overlap
+ *   occ          device [nk][n_occ]
+ *   A            HOST [3] vector potential at the start of the step (bohr^-1)
+ * The first call allocates three orbital-sized scratch arrays in the plan (device-wide
+ * synchronisation); later calls are asynchronous on `stream`.  Not for batched plans. */
+int hse_taylor_step(hse_plan plan, const void *psi, const double *occ, const double *A, double dt,
+                    void *psi_out, hse_stream_t stream);
+
+/* Spatially averaged electric current of the orbitals (Sec. II A, Eqs. "current_dns" and
+ * "current_elec", without J_NL, the nonlocal pseudopotential part; atomic units, e/c
+ * absorbed into A):
+ *   J = -(1/Omega) int_Omega sum_i w_i Re[psi_i* (-i grad + A) psi_i]
+ *     = -sum_{k,i} (g_s f_{i,k} / N_k) sum_G |c_{i,k}(G)|^2 (G + k + A),
+ * c = (1/N) sum_r u(r) e^{-iG.r}, computed with FP64 transforms and reduced in FP64.
+ *   psi  device [nk][n_occ][N] (the plan's dtype), occ device [nk][n_occ]
+ *   A    HOST [3];  J  device double[3], overwritten
+ * g_s is the plan's spin_degeneracy.  The first call allocates an FP64 copy of the orbitals
+ * in the plan; later calls are asynchronous on `stream`.  Not for batched plans. */
+int hse_current(hse_plan plan, const void *psi, const double *occ, const double *A, double *J,
+                hse_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -271,6 +271,10 @@ struct hse_plan_s {
   void* u_sub = nullptr;        // device [nkq][n_occ][N] gathered occupied orbitals
   double* occ_sub = nullptr;    // device [nkq][n_occ]
   void* g_sub = nullptr;        // device [nkq][n_occ][N] VJP w.r.t. the sampled orbitals
+  // time propagation (allocated on first use)
+  void* tay[3] = {nullptr, nullptr, nullptr};  // Taylor step: term, T term, V_x term [nk][n_occ][N]
+  double2* cur_work = nullptr;  // current: FP64 transforms [nk][n_occ][N]
+  double* cur_partial = nullptr;  // current: [nk][n_occ][3]
   // batched plans (hse_plan_create_batched)
   bool batched = false;
   std::vector<hse_plan> cells;          // one sub-plan (kernel tables) per cell
@@ -402,6 +406,9 @@ int hse_plan_destroy(hse_plan plan) {
   cudaFree(plan->u_sub);
   cudaFree(plan->occ_sub);
   cudaFree(plan->g_sub);
+  for (void* b : plan->tay) cudaFree(b);
+  cudaFree(plan->cur_work);
+  cudaFree(plan->cur_partial);
   cudaSetDevice(prev);
   delete plan;
   return HSE_OK;
@@ -1025,6 +1032,65 @@ int hse_kinetic_apply(hse_plan plan, const void* u, int nbands, const double* A,
     return cuda_fail(launch_kinetic_c64(p.grid[0], (const float2*)u, (float2*)out, a, st));
   }
   return cuda_fail(launch_kinetic_f64((const double2*)u, (double2*)out, a, st));
+}
+
+int hse_taylor_step(hse_plan plan, const void* psi, const double* occ, const double* A, double dt, void* psi_out,
+                    hse_stream_t stream) {
+  if (!plan || plan->batched || !psi || !occ || !A || !psi_out || !std::isfinite(dt)) return HSE_ERR_INVALID_ARG;
+  const hse_problem& p = plan->p;
+  if (p.n_tgt != p.n_occ) return HSE_ERR_INVALID_ARG;  // the step propagates the occupied set
+  for (int c = 0; c < 3; ++c)
+    if (!std::isfinite(A[c])) return HSE_ERR_INVALID_ARG;
+  if (!aligned16(psi) || !aligned16(psi_out)) return HSE_ERR_INVALID_ARG;
+  const size_t count = (size_t)p.nk * p.n_occ * plan->N;
+  const size_t bytes = count * elem_bytes(p.dtype);
+  if (overlaps(psi_out, bytes, psi, bytes) || overlaps(psi_out, bytes, occ, (size_t)p.nk * p.n_occ * sizeof(double)))
+    return HSE_ERR_ALIAS;
+  for (void*& b : plan->tay)
+    if (!b) {
+      const cudaError_t e = cudaMalloc(&b, bytes);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+  cudaStream_t st = S(stream);
+  cudaError_t e = cudaMemcpyAsync(psi_out, psi, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const void* term = psi;
+  for (int n = 1; n <= 4; ++n) {
+    int rc = hse_kinetic_apply(plan, term, p.n_occ, A, plan->tay[1], stream);
+    if (rc) return rc;
+    rc = hse_fock_apply(plan, psi, occ, term, plan->tay[2], stream);
+    if (rc) return rc;
+    e = launch_taylor_accumulate(p.dtype == HSE_C128, plan->tay[1], plan->tay[2], plan->tay[0], psi_out, count,
+                                 dt / n, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    term = plan->tay[0];
+  }
+  return HSE_OK;
+}
+
+int hse_current(hse_plan plan, const void* psi, const double* occ, const double* A, double* J, hse_stream_t stream) {
+  if (!plan || plan->batched || !psi || !occ || !A || !J) return HSE_ERR_INVALID_ARG;
+  for (int c = 0; c < 3; ++c)
+    if (!std::isfinite(A[c])) return HSE_ERR_INVALID_ARG;
+  if (!aligned16(psi)) return HSE_ERR_INVALID_ARG;
+  const hse_problem& p = plan->p;
+  const size_t norb = (size_t)p.nk * p.n_occ;
+  if (!plan->cur_work) {
+    cudaError_t e = cudaMalloc(&plan->cur_work, norb * plan->N * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&plan->cur_partial, norb * 3 * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  CurArgs a{};
+  a.n1 = p.grid[0];
+  a.n2 = p.grid[1];
+  a.n3 = p.grid[2];
+  a.nk = p.nk;
+  a.nbands = p.n_occ;
+  std::memcpy(a.b, plan->b, sizeof(a.b));
+  for (int c = 0; c < 3; ++c) a.A[c] = A[c];
+  a.kpts = plan->dkpts;
+  return cuda_fail(launch_current(p.dtype == HSE_C128, psi, occ, a, plan->cur_work, plan->cur_partial,
+                                  p.spin_degeneracy, J, S(stream)));
 }
 
 int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells) {

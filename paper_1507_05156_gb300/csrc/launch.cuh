@@ -20,6 +20,20 @@ struct KinArgs {
 };
 cudaError_t launch_kinetic_f64(const double2* u, double2* out, const KinArgs& a, cudaStream_t stream);
 
+// Taylor-step accumulation and the electric current (tdks.cu).
+struct CurArgs {
+  int n1, n2, n3, nk, nbands;
+  double b[9];          // reciprocal rows b1, b2, b3
+  double A[3];          // vector potential (bohr^-1)
+  const double* kpts;   // device [nk][3]
+};
+cudaError_t launch_taylor_accumulate(bool c128, const void* kin, const void* vx, void* term, void* out, size_t count,
+                                     double s, cudaStream_t stream);
+// J (device double[3]) from the orbitals psi [nk][nbands][N] and occupations [nk][nbands];
+// work: [nk][nbands][N] double2 scratch, partial: [nk][nbands][3] double scratch.
+cudaError_t launch_current(bool c128, const void* psi, const double* occ, const CurArgs& a, double2* work,
+                           double* partial, double spin_degeneracy, double* J, cudaStream_t stream);
+
 // Fused complex64 pair-convolution launch for a cubic grid of side n (one TU per size
 // group keeps the build parallel).  Returns a cudaError_t.
 cudaError_t launch_pairconv_c64(int n, int mode, const PairArgs& args, int blocks_per_sm, cudaStream_t stream);

@@ -10,6 +10,10 @@
   sum_{n<=4} (-i dt h)^n / n! psi(t), with h = T[A(t)] + V_x[psi(t)] frozen over the step.
   ``propagate`` recomputes each step in the backward pass (activation checkpointing), so
   only one set of orbitals per step is kept.
+* ``propagate_pulse`` drives the orbitals with the sin^2 pulse of Sec. IV,
+  A(t) = -(E0 / w) cos(w t) sin^2(pi t / T_d), through the library's fused Taylor step
+  (hse_taylor_step, no autograd) and records the current J(t) (hse_current, Sec. II A without
+  the nonlocal part) and the energy absorbed per unit volume W(t) = int J . E dt (Sec. V).
 
 Every operator application runs in the CUDA library; PyTorch only holds the tensors, forms
 the Taylor sum and drives autograd.
@@ -112,3 +116,40 @@ def propagate(psi0, occ, omega, geom: Geometry, dt: float, nsteps: int, efield: 
         else:
             psi = taylor_step(psi, occ, omega, A, dt, geom)
     return psi
+
+
+def pulse_vector_potential(t: float, E0: float, w: float, Td: float, direction) -> np.ndarray:
+    """A(t) = -(E0 / w) cos(w t) sin^2(pi t / T_d) along ``direction`` inside (0, T_d), else 0."""
+    if not 0.0 < t < Td:
+        return np.zeros(3)
+    return -(E0 / w) * np.cos(w * t) * np.sin(np.pi * t / Td) ** 2 * np.asarray(direction, dtype=np.float64)
+
+
+def pulse_field(t: float, E0: float, w: float, Td: float, direction) -> np.ndarray:
+    """E(t) = -dA/dt of pulse_vector_potential."""
+    if not 0.0 < t < Td:
+        return np.zeros(3)
+    ph, env = w * t, np.pi * t / Td
+    dA_dt = (E0 / w) * (w * np.sin(ph) * np.sin(env) ** 2 - np.cos(ph) * (np.pi / Td) * np.sin(2.0 * env))
+    return -dA_dt * np.asarray(direction, dtype=np.float64)
+
+
+def propagate_pulse(psi0: torch.Tensor, occ: torch.Tensor, omega: float, geom: Geometry, dt: float, nsteps: int,
+                    E0: float, w: float, Td: float, direction):
+    """nsteps fused Taylor steps under the pulse.  Step s (t_s = s dt) uses h frozen at psi(t_s)
+    with A(t_s); J_s = J(t_s) from psi(t_s) and A(t_s); W by the trapezoidal rule on J . E.
+    Returns (psi(t_nsteps), J [nsteps+1][3] float64 on the device, W [nsteps+1] numpy)."""
+    plan = geom.plan(psi0.shape[1], psi0.shape[1], omega, psi0.dtype)
+    bufs = [psi0.contiguous().clone(), torch.empty_like(psi0)]
+    J = torch.empty((nsteps + 1, 3), dtype=torch.float64, device=psi0.device)
+    for s in range(nsteps + 1):
+        A = pulse_vector_potential(s * dt, E0, w, Td, direction)
+        hse.hse_current(plan, bufs[0], occ, A, out=J[s])
+        if s < nsteps:
+            hse.hse_taylor_step(plan, bufs[0], occ, A, dt, out=bufs[1])
+            bufs.reverse()
+    Jh = J.cpu().numpy()
+    E = np.stack([pulse_field(s * dt, E0, w, Td, direction) for s in range(nsteps + 1)])
+    p = np.einsum("sc,sc->s", Jh, E)
+    W = np.concatenate([[0.0], np.cumsum(0.5 * dt * (p[1:] + p[:-1]))])
+    return bufs[0], J, W

@@ -134,3 +134,62 @@ def test_differentiation_workload_gradients_vs_finite_differences():
     assert rel(psi_T32.detach().cpu().numpy(), psi_T64.cpu().numpy()) <= 1e-5
     assert rel(p32.grad.cpu().numpy(), g_psi.cpu().numpy()) <= 1e-4
     assert abs(float(om32.grad) - g_om) <= 1e-4 * abs(g_om)
+
+
+# ---------------------------------------------------------------------------
+# Fused Taylor step, electric current and the laser-pulse driver vs the FP64 oracle
+# ---------------------------------------------------------------------------
+
+def _tdks_cell(seed, grid, lattice, nk, nb, dtype):
+    rng = np.random.default_rng(seed)
+    b = 2 * np.pi * np.linalg.inv(lattice).T
+    kpts = (rng.random((nk, 3)) - 0.5) @ b
+    u = inputs.orthonormal_orbitals(rng, grid, lattice, kpts, nb, ecut=60.0)
+    if dtype == torch.complex64:
+        u = u.astype(np.complex64).astype(np.complex128)
+    occ = rng.random((nk, nb)) * 0.5 + 0.5
+    return kpts, u, occ
+
+
+STEP_CASES = [(torch.complex64, (12, 12, 12), inputs.cubic_lattice(10.26), 1e-5),
+              (torch.complex128, (6, 5, 4), TRICLINIC, 1e-10)]
+
+
+@pytest.mark.parametrize("dtype,grid,lattice,tol", STEP_CASES)
+def test_fused_taylor_step_matches_oracle(dtype, grid, lattice, tol):
+    kpts, u, occ = _tdks_cell(31, grid, lattice, 2, 3, dtype)
+    A = np.array([0.011, -0.02, 0.005])
+    dt, omega, alpha = 0.05, 0.2, 0.25
+    plan = hse.get_plan(grid, lattice, kpts, 3, 3, omega, alpha, dtype=dtype)
+    got = hse.hse_taylor_step(plan, dev(u, dtype), dev(occ, torch.float64), A, dt).cpu().numpy()
+    ref = otd.taylor_step(u, occ, kpts, lattice, grid, A, omega, alpha, dt)
+    # compare the increments psi(t + dt) - psi(t): the step itself, not the carried state
+    assert rel(got - u, ref - u) <= tol
+    assert rel(got, ref) <= tol
+
+
+@pytest.mark.parametrize("dtype,grid,lattice,tol", [(torch.complex64, (12, 12, 12), inputs.cubic_lattice(10.26), 1e-12),
+                                                    (torch.complex128, (6, 5, 4), TRICLINIC, 1e-12)])
+def test_current_matches_oracle(dtype, grid, lattice, tol):
+    kpts, u, occ = _tdks_cell(32, grid, lattice, 3, 2, dtype)
+    A = np.array([-0.03, 0.012, 0.02])
+    plan = hse.get_plan(grid, lattice, kpts, 2, 2, 0.2, 0.25, dtype=dtype)
+    J = hse.hse_current(plan, dev(u, dtype), dev(occ, torch.float64), A).cpu().numpy()
+    ref = otd.current(u, occ, kpts, lattice, grid, A, 2.0)
+    assert np.abs(J - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-9), (torch.complex64, 2e-5)])
+def test_pulse_driver_matches_oracle(dtype, tol):
+    grid, lattice = (8, 8, 8), inputs.cubic_lattice(10.26)
+    kpts, u, occ = _tdks_cell(33, grid, lattice, 2, 2, dtype)
+    E0, w, Td, d = 0.02, 0.3, 2.0, (0.0, 0.6, 0.8)
+    dt, nsteps, omega = 0.1, 12, 0.2
+    geom = tdks.Geometry(grid, lattice, kpts, alpha=0.25)
+    psi, J, W = tdks.propagate_pulse(dev(u, dtype), dev(occ, torch.float64), omega, geom, dt, nsteps, E0, w, Td, d)
+    r_psi, r_J, r_W = otd.propagate_pulse(u, occ, kpts, lattice, grid, omega, 0.25, dt, nsteps, E0, w, Td, d)
+    assert rel(psi.cpu().numpy(), r_psi) <= tol
+    J = J.cpu().numpy()
+    assert np.abs(J - r_J).max() <= tol * np.abs(r_J).max()
+    assert np.abs(W - r_W).max() <= tol * np.abs(r_W).max() + 1e-15
+    assert np.abs(r_W).max() > 0  # the pulse did work
