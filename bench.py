@@ -163,6 +163,22 @@ def config_dict(cell):
             "l2": "flushed between timed steps by a 256 MB write (inputs 65.5 MB < L2)"}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of every rank's value (the slowest replica's time); x itself on one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` independent replicas (weak scaling): every rank
+    processes units_per_rank in the time of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def run_cuda(args, rank, world, dist):
     import torch
     from paper_1507_05156_gb300 import hse, inputs
@@ -205,13 +221,9 @@ def run_cuda(args, rank, world, dist):
     launches = hse.kernel_launches() - l0
     hse.hse_status(plan)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     pairs = cell.pairs
-    value = world * pairs * args.steps / (total_ms / 1e3)
+    value = replica_throughput(pairs * args.steps, world, total_ms / 1e3)
 
     # ---- end to end through the public API: pinned host in, host out ------------------
     out_host = torch.empty(out.shape, dtype=d).pin_memory()
@@ -227,11 +239,8 @@ def run_cuda(args, rank, world, dist):
         out_host.copy_(r, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * pairs / (float(te.item()) / 1e3)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
+    e2e_value = replica_throughput(pairs, world, e2e_ms / 1e3)
     h2d = u_host.numel() * u_host.element_size() + occ_host.numel() * occ_host.element_size()
     d2h = out_host.numel() * out_host.element_size()
 
