@@ -8,7 +8,8 @@
 //     stream in by TMA from the cell's tensor map into two stage buffers, the owner orbital
 //     and the accumulators stay in Tensor Memory.  512 threads (8^3 with eight owner slots of
 //     one pencil per thread);
-//   * pencil-load items (sides 16, 24; pairconv_c64.cuh): orbitals are read as pencils
+//   * pencil-load items (sides 16, 24; pairconv_c64.cuh; 24^3 in its ragged 12-warp form, 384
+//     threads): orbitals are read as pencils
 //     through L1.  That kernel keeps only its own shared-memory footprint so that L1 keeps
 //     the rest of the SM's storage: with the staged kernel's 208 KB of shared memory
 //     reserved, its 24^3 items ran 37% slower.
@@ -22,7 +23,7 @@ namespace hse {
 namespace {
 
 constexpr int kStagedThreads = 512;
-constexpr int kPencilThreads = 288;
+constexpr int kPencilThreads = kRaggedThreads;  // the ragged 24^3 form (12 warps)
 
 template <int n>
 using SeqS = GeoS<n, LayoutSeq<n>>;
@@ -32,7 +33,7 @@ using OneS = GeoS<n, LayoutOne<n>>;
 static_assert(LayoutOne<20>::THREADS <= kStagedThreads && LayoutOne<8>::THREADS <= kStagedThreads &&
                   LayoutSeq<12>::THREADS <= kStagedThreads && LayoutOne<18>::THREADS <= kStagedThreads,
               "staged batched block too small for a side's layout");
-static_assert(Geo<16>::THREADS <= kPencilThreads && Geo<24>::THREADS <= kPencilThreads,
+static_assert(Geo<16>::THREADS <= kPencilThreads && GeoP<24, 2, kRaggedThreads>::THREADS <= kPencilThreads,
               "pencil-load batched block too small");
 static_assert(OneS<8>::FITS && SeqS<12>::FITS && OneS<18>::FITS && OneS<20>::FITS,
               "staged layouts of the batched kernel must fit");
@@ -120,7 +121,10 @@ __global__ void __launch_bounds__(kPencilThreads, 1) pairconv_batched_pencil_ker
     const BatchCell& c = b.cells[wi.cell];
     switch (c.n) {
       case 16: pairconv_item<16, MODE>(c.pa, wi.item, smem4, tbase, warp < Geo<16>::WARPS); break;
-      case 24: pairconv_item<24, MODE>(c.pa, wi.item, smem4, tbase, warp < Geo<24>::WARPS); break;
+      case 24:
+        pairconv_item<24, MODE, 2, kRaggedThreads>(c.pa, wi.item, smem4, tbase,
+                                                   warp < GeoP<24, 2, kRaggedThreads>::WARPS);
+        break;
       default: break;  // the host puts only the sides above in this list
     }
     __syncthreads();  // the shared grid and TMEM rows are reused by the next item

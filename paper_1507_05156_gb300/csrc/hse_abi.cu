@@ -257,7 +257,7 @@ struct hse_plan_s {
   double2* work = nullptr;   // [batch][N]
   size_t work_pairs = 0;
   double2* vx64 = nullptr;   // [nk][max(n_occ, n_tgt)][N]
-  int blocks_per_sm = 0;     // fused-kernel variant: 0 default, -1/-2/-3 staged-partner layouts, 1/2 pencil loads
+  int blocks_per_sm = 0;     // fused-kernel variant: 0 default, -1/-2/-3 staged-partner layouts, 1/2/3 pencil loads
   int inject = 0;            // test hook (HSE_INJECT_SKIP_FILL=1 at plan creation)
   int nsplit[3] = {1, 1, 1};  // k'-loop splits of the fused kernel per OwnerRole
   float2* split_buf = nullptr;  // [nsplit][nk_own][n_own][N] partial outputs when nsplit > 1
@@ -441,7 +441,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   if (const char* env = std::getenv("HSE_INJECT_SKIP_FILL")) plan->inject = std::atoi(env) == 1 ? 1 : 0;
   if (const char* env = std::getenv("HSE_BLOCKS_PER_SM")) {
     const int v = std::atoi(env);
-    plan->blocks_per_sm = v < -3 ? 0 : (v >= 2 ? 2 : v);
+    plan->blocks_per_sm = (v < -3 || v > 3) ? 0 : v;
   }
   const int n1 = p->grid[0], n2 = p->grid[1], n3 = p->grid[2];
   plan->N = n1 * n2 * n3;

@@ -73,14 +73,14 @@ bool staged_fft_supported(int L);
 
 // Template body used by the per-size translation units.  `blocks_per_sm` selects the
 // occupancy variant (1: registers uncapped; 2: two CTAs per SM where they fit).
-template <int n, int MODE, int MINB>
+template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT>
 cudaError_t pairconv_set_attr() {
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_done[dev]) {
-    cudaError_t err = cudaFuncSetAttribute(pairconv_c64_kernel<n, MODE, MINB>,
+    cudaError_t err = cudaFuncSetAttribute(pairconv_c64_kernel<n, MODE, MINB, PPT, TSX>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)pairconv_smem_bytes<n>());
     if (err != cudaSuccess) return err;
@@ -89,25 +89,41 @@ cudaError_t pairconv_set_attr() {
   return cudaSuccess;
 }
 
-template <int n, int MODE, int MINB>
+template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT>
 cudaError_t launch_pairconv_variant(const PairArgs& args, cudaStream_t stream) {
-  cudaError_t err = pairconv_set_attr<n, MODE, MINB>();
+  cudaError_t err = pairconv_set_attr<n, MODE, MINB, PPT, TSX>();
   if (err != cudaSuccess) return err;
   const dim3 grid((unsigned)((size_t)args.nsplit * args.nk_own * args.ntiles));
-  pairconv_c64_kernel<n, MODE, MINB><<<grid, Geo<n>::THREADS, pairconv_smem_bytes<n>(), stream>>>(args);
+  pairconv_c64_kernel<n, MODE, MINB, PPT, TSX>
+      <<<grid, GeoP<n, PPT, TSX>::THREADS, pairconv_smem_bytes<n>(), stream>>>(args);
   count_launch();
   return cudaGetLastError();
 }
 
 // Resident CTAs per SM of a variant (0 on error).
-template <int n, int MODE, int MINB>
+template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT>
 int pairconv_occupancy_variant() {
-  if (pairconv_set_attr<n, MODE, MINB>() != cudaSuccess) return 0;
+  if (pairconv_set_attr<n, MODE, MINB, PPT, TSX>() != cudaSuccess) return 0;
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pairconv_c64_kernel<n, MODE, MINB>, Geo<n>::THREADS,
-                                                    pairconv_smem_bytes<n>()) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pairconv_c64_kernel<n, MODE, MINB, PPT, TSX>,
+                                                    GeoP<n, PPT, TSX>::THREADS, pairconv_smem_bytes<n>()) != cudaSuccess)
     return 0;
   return blocks;
+}
+
+// Ragged pencil-load variant: 12 warps per owner slot (at most 3 on a warp scheduler, so up to
+// 170 registers a thread); thread t takes pencil t and, for t < n^2 - 384, pencil t + 384.  For
+// 24^3 (576 pencils) the busiest scheduler runs 5 pencil passes per stage instead of the 6 of
+// two pencils per thread on 9 warps (3/2/2/2).
+constexpr int kRaggedThreads = 384;
+template <int n>
+constexpr bool pencil_ragged_fits() {
+  if constexpr (Geo<n>::T == 1 && Geo<n>::NN > kRaggedThreads && Geo<n>::NN <= 2 * kRaggedThreads &&
+                (Geo<n>::NN - kRaggedThreads) % 32 == 0) {
+    return GeoP<n, 2, kRaggedThreads>::TMEM_COLS <= 512;
+  } else {
+    return false;
+  }
 }
 
 // Staged-partner kernel (pairconv_tma.cuh): one CTA per SM.
@@ -149,8 +165,9 @@ constexpr bool tma_fits() {
 // Kernel variant: 0 the default (the staged-partner kernel with its default layout where it
 // exists for (n, mode), else the pencil-load kernel at the occupancy the size allows);
 // -1 / -2 / -3 the staged-partner kernel with LayoutSeq / LayoutOne / LayoutSplit; 1 or 2 the
-// pencil-load kernel with that occupancy.  A staged layout that does not fit falls back to
-// the default.
+// pencil-load kernel with that occupancy; 3 the ragged pencil-load kernel (pencil_ragged_fits;
+// the default of the pencil-load kernel where it exists: 24^3 99.6 -> 95.6 ms on the 4x4x4 k,
+// 16-band cell).  A variant that does not exist for the size falls back to the default.
 template <int n, int MODE>
 constexpr int staged_layout(int variant) {
   if (variant > 0) return 0;
@@ -178,7 +195,10 @@ cudaError_t launch_pairconv_mode(const PairArgs& args, int variant, cudaStream_t
       break;
     default: break;
   }
-  const int blocks_per_sm = variant <= 0 ? 2 : variant;
+  if constexpr (pencil_ragged_fits<n>()) {
+    if (variant == 3 || variant <= 0) return launch_pairconv_variant<n, MODE, 1, 2, kRaggedThreads>(args, stream);
+  }
+  const int blocks_per_sm = (variant <= 0 || variant == 3) ? 2 : variant;
   if (blocks_per_sm >= 2 && Geo<n>::MAXB >= 2) return launch_pairconv_variant<n, MODE, Geo<n>::MAXB>(args, stream);
   return launch_pairconv_variant<n, MODE, 1>(args, stream);
 }
@@ -186,7 +206,10 @@ cudaError_t launch_pairconv_mode(const PairArgs& args, int variant, cudaStream_t
 template <int n, int MODE>
 int pairconv_occupancy_mode(int variant) {
   if (staged_layout<n, MODE>(variant) != 0) return 1;
-  const int blocks_per_sm = variant <= 0 ? 2 : variant;
+  if constexpr (pencil_ragged_fits<n>()) {
+    if (variant == 3 || variant <= 0) return pairconv_occupancy_variant<n, MODE, 1, 2, kRaggedThreads>();
+  }
+  const int blocks_per_sm = (variant <= 0 || variant == 3) ? 2 : variant;
   if (blocks_per_sm >= 2 && Geo<n>::MAXB >= 2) return pairconv_occupancy_variant<n, MODE, Geo<n>::MAXB>();
   return pairconv_occupancy_variant<n, MODE, 1>();
 }

@@ -79,6 +79,23 @@ struct Geo {
   static_assert(ZVEC == 1 || (P % 2 == 0 && Q % 2 == 0), "128-bit Z accesses need even pitches");
 };
 
+// Thread and TMEM geometry of the pencil-load pipeline with TS threads per owner slot, each
+// taking pencils t, t + TS, ... (at most PPT of them) in every stage; PPT = 2 with TS = n^2/2
+// is Geo's own.  TS need not divide n^2 (24^3: 384 threads, the first 192 take a second
+// pencil), but n^2 - (PPT - 1) TS must be a multiple of 32 so that the last pass covers whole
+// warps.
+template <int n, int PPT, int TS_ = Geo<n>::NN / PPT>
+struct GeoP {
+  using G = Geo<n>;
+  static constexpr int TS = TS_;                                  // threads per owner slot
+  static_assert((PPT - 1) * TS < G::NN && PPT * TS >= G::NN, "PPT passes of TS threads cover the pencils");
+  static constexpr int THREADS = ((G::T * TS + 31) / 32) * 32;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int TAB = PPT * G::ROW;                        // column of the kernel-row cache
+  static constexpr int COLS_PER_WARP = PPT * G::ROW + PPT * n;    // accumulators + kernel rows
+  static constexpr int TMEM_COLS = pow2_at_least(((WARPS + 3) / 4) * COLS_PER_WARP);
+};
+
 // What a launch computes.
 enum PairMode : int {
   MODE_APPLY = 0,   // owner = target i, partner = occupied j: out = V_x u_i
@@ -173,12 +190,13 @@ struct Pencil {
 };
 
 // Stage Y (DIR) for the PPT pencils of the thread (pencil t + ps NN/PPT): load, FFT, store.
-template <int n, int DIR, int PPT = 2>
+template <int n, int DIR, int PPT = 2, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void stage_y(float2* g, int t, bool valid) {
   using G = Geo<n>;
 #pragma unroll 1
   for (int ps = 0; ps < PPT; ++ps) {
-    const Pencil<n> pc(t + ps * (G::NN / PPT));
+    if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;  // whole warps past the last pencil
+    const Pencil<n> pc(t + ps * TS);
     cpx<float> v[n];
     load_s<n, 1>(v, g, pc.ys, G::P);
     fft<n, DIR, float>(v);
@@ -231,12 +249,13 @@ __device__ __forceinline__ int x_pencil(int p) {
 // Stage X: FFT, multiply by the kernel row (cached in TMEM, already times -alpha/(N_k N))
 // times the occupation f, inverse FFT, for the PPT pencils.  Warp-wide (TMEM loads).
 // XP (one pencil per thread): the bank-spread X-pencil order of x_pencil over the first XR.
-template <int n, int PPT = 2, bool XP = false, int XR = n * n>
+template <int n, int PPT = 2, bool XP = false, int XR = n * n, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void stage_x(float2* g, int t, bool valid, uint32_t ttab, float f) {
   using G = Geo<n>;
 #pragma unroll 1
   for (int ps = 0; ps < PPT; ++ps) {
-    const Pencil<n> pc(x_pencil<n, XP, XR>(t + ps * (G::NN / PPT)));
+    if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
+    const Pencil<n> pc(x_pencil<n, XP, XR>(t + ps * TS));
     float tv[n];
     TmemRow<n>::load(ttab + (uint32_t)(ps * n), tv);
     cpx<float> v[n];
@@ -254,12 +273,13 @@ __device__ __forceinline__ void stage_x(float2* g, int t, bool valid, uint32_t t
 }
 
 // Kernel row v(|G+q|) * scale of this thread's PPT X-pencils into the TMEM cache.
-template <int n, int PPT = 2, bool XP = false, int XR = n * n>
+template <int n, int PPT = 2, bool XP = false, int XR = n * n, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void cache_kernel_row(int t, uint32_t ttab, const float* __restrict__ vrow, float scale) {
   using G = Geo<n>;
 #pragma unroll 1
   for (int ps = 0; ps < PPT; ++ps) {
-    const int p = x_pencil<n, XP, XR>(t + ps * (G::NN / PPT));
+    if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
+    const int p = x_pencil<n, XP, XR>(t + ps * TS);
     float tv[n];
 #pragma unroll
     for (int e = 0; e < n; ++e) tv[e] = __ldg(vrow + e * G::NN + p) * scale;
@@ -267,14 +287,15 @@ __device__ __forceinline__ void cache_kernel_row(int t, uint32_t ttab, const flo
   }
 }
 
-// Z forward for both pencils: v = conj(a) * b, FFT along z, store.
-template <int n>
+// Z forward for the thread's pencils: v = conj(a) * b, FFT along z, store.
+template <int n, int PPT = 2, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void stage_z_forward(float2* g, int t, bool valid, const float2* __restrict__ a,
                                                 const float2* __restrict__ b) {
   using G = Geo<n>;
 #pragma unroll 1
-  for (int ps = 0; ps < 2; ++ps) {
-    const Pencil<n> pc(t + ps * G::TS);
+  for (int ps = 0; ps < PPT; ++ps) {
+    if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
+    const Pencil<n> pc(t + ps * TS);
     cpx<float> v[n], w[n];
     load_pencil_global<n>(w, a + pc.zg);
     load_pencil_global<n>(v, b + pc.zg);
@@ -291,15 +312,16 @@ enum Epi : int {
   EPI_WCONJ = 2,    // acc += w * conj(phi)
 };
 
-// Z inverse for both pencils, then the epilogue into each pencil's TMEM row.  Executed by
-// every thread of the warp (TMEM accesses are warp-wide).
-template <int n, int EPI>
+// Z inverse for the thread's pencils, then the epilogue into each pencil's TMEM row.
+// Executed by every thread of the warp (TMEM accesses are warp-wide).
+template <int n, int EPI, int PPT = 2, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void stage_z_inverse(const float2* g, int t, const float2* __restrict__ wbase,
                                                 uint32_t trow0) {
   using G = Geo<n>;
 #pragma unroll 1
-  for (int ps = 0; ps < 2; ++ps) {
-    const Pencil<n> pc(t + ps * G::TS);
+  for (int ps = 0; ps < PPT; ++ps) {
+    if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
+    const Pencil<n> pc(t + ps * TS);
     cpx<float> v[n];
     load_s<n, G::ZVEC>(v, g, pc.zs, 1);
     fft<n, +1, float>(v);
@@ -328,14 +350,14 @@ __device__ __forceinline__ void stage_z_inverse(const float2* g, int t, const fl
 }
 
 // One pair chain between the Z stages; all threads of the CTA call it together.
-template <int n>
+template <int n, int PPT = 2, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32_t ttab, float f, bool warp_on = true) {
   __syncthreads();
-  if (warp_on) stage_y<n, -1>(g, t, valid);
+  if (warp_on) stage_y<n, -1, PPT, TS>(g, t, valid);
   __syncthreads();
-  if (warp_on) stage_x<n>(g, t, valid, ttab, f);
+  if (warp_on) stage_x<n, PPT, false, n * n, TS>(g, t, valid, ttab, f);
   __syncthreads();
-  if (warp_on) stage_y<n, +1>(g, t, valid);
+  if (warp_on) stage_y<n, +1, PPT, TS>(g, t, valid);
   __syncthreads();
 }
 
@@ -343,22 +365,24 @@ __device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32
 // the item needs (the batched kernel runs every grid side in one block shape): warps with
 // warp_on == false skip all work and TMEM traffic but pass every barrier.  tbase: the CTA's
 // TMEM allocation, at least Geo<n>::TMEM_COLS columns for this block's warp count.
-template <int n, int MODE>
+template <int n, int MODE, int PPT = 2, int TSX = Geo<n>::NN / PPT>
 __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, float4* smem4, uint32_t tbase,
                                               bool warp_on) {
   using G = Geo<n>;
+  using GP = GeoP<n, PPT, TSX>;
+  constexpr int TS = GP::TS;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
-  const bool valid = tid < G::T * G::TS;
-  const int slot = valid ? tid / G::TS : 0;
-  const int t = valid ? tid - slot * G::TS : 0;
+  const bool valid = tid < G::T * TS;
+  const int slot = valid ? tid / TS : 0;
+  const int t = valid ? tid - slot * TS : 0;
   float2* g = reinterpret_cast<float2*>(smem4) + slot * G::GRID_CPX;
 
   // tensor memory for the accumulators: warp w uses lanes 32 (w % 4) .. +31, columns from
   // (w / 4) * COLS_PER_WARP; the thread's pencil pass ps is the row at + ps * ROW.
-  const uint32_t trow0 = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * G::COLS_PER_WARP);
-  const uint32_t ttab = trow0 + (uint32_t)G::TAB;
+  const uint32_t trow0 = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * GP::COLS_PER_WARP);
+  const uint32_t ttab = trow0 + (uint32_t)GP::TAB;
 
   // work item: (split, k, tile); split s covers partner k-points
   // [s nk_part / nsplit, (s+1) nk_part / nsplit)
@@ -377,33 +401,33 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     float z[G::ROW];
 #pragma unroll
     for (int e = 0; e < G::ROW; ++e) z[e] = 0.f;
-    TmemRow<G::ROW>::store(trow0, z);
-    TmemRow<G::ROW>::store(trow0 + G::ROW, z);
+#pragma unroll
+    for (int ps = 0; ps < PPT; ++ps) TmemRow<G::ROW>::store(trow0 + (uint32_t)(ps * G::ROW), z);
   }
 
   for (int kp = kp_begin; kp < kp_end; ++kp) {
     // q = k_i - k_j: APPLY-like modes own i (at k) and pair with j at kp; OCC owns j (at k)
     const int qrow = (MODE == MODE_OCC) ? args.qidx[kp * args.nk_own + k] : args.qidx[k * args.nk_part + kp];
-    if (warp_on) cache_kernel_row<n>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
+    if (warp_on) cache_kernel_row<n, PPT, false, n * n, TS>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
     for (int j = 0; j < args.n_part; ++j) {
       const float2* part = args.part + ((size_t)kp * args.n_part + j) * G::N;
       if constexpr (MODE != MODE_OCC) {
         const float f = (float)args.occ[kp * args.n_occ + j];
         if (f == 0.f) continue;  // uniform over the CTA
-        if (warp_on) stage_z_forward<n>(g, t, valid, part, own);          // conj(u_j) u_i
-        pair_middle<n>(g, t, valid, ttab, f, warp_on);
-        if (warp_on) stage_z_inverse<n, EPI_MUL>(g, t, part, trow0);      // acc += u_j phi
+        if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, part, own);          // conj(u_j) u_i
+        pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
+        if (warp_on) stage_z_inverse<n, EPI_MUL, PPT, TS>(g, t, part, trow0);      // acc += u_j phi
       } else {
         const float f = (float)args.occ[k * args.n_occ + bandc];
         const float2* ybar = args.part2 + ((size_t)kp * args.n_part + j) * G::N;
         // chain 1: rho = conj(u_j) u_i -> phi;  acc += conj(phi) ybar_i
-        if (warp_on) stage_z_forward<n>(g, t, valid, own, part);
-        pair_middle<n>(g, t, valid, ttab, f, warp_on);
-        if (warp_on) stage_z_inverse<n, EPI_CONJPHI>(g, t, ybar, trow0);
+        if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, own, part);
+        pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
+        if (warp_on) stage_z_inverse<n, EPI_CONJPHI, PPT, TS>(g, t, ybar, trow0);
         // chain 2: sigma = conj(u_j) ybar_i -> psibar;  acc += u_i conj(psibar)
-        if (warp_on) stage_z_forward<n>(g, t, valid, own, ybar);
-        pair_middle<n>(g, t, valid, ttab, f, warp_on);
-        if (warp_on) stage_z_inverse<n, EPI_WCONJ>(g, t, part, trow0);
+        if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, own, ybar);
+        pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
+        if (warp_on) stage_z_inverse<n, EPI_WCONJ, PPT, TS>(g, t, part, trow0);
       }
     }
   }
@@ -412,8 +436,9 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     if (!warp_on) return;
     float2* obase = args.out + split * args.split_stride + ((size_t)k * args.n_own + bandc) * G::N;
 #pragma unroll 1
-    for (int ps = 0; ps < 2; ++ps) {
-      const Pencil<n> pc(t + ps * G::TS);
+    for (int ps = 0; ps < PPT; ++ps) {
+      if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
+      const Pencil<n> pc(t + ps * TS);
       float acc[G::ROW];
       TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
       if (active) {
@@ -427,8 +452,9 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     const float2* lhs = (MODE == MODE_ENERGY) ? own : args.part2 + ((size_t)k * args.n_own + bandc) * G::N;
     double d = 0.0;
 #pragma unroll 1
-    for (int ps = 0; ps < 2 && warp_on; ++ps) {
-      const Pencil<n> pc(t + ps * G::TS);
+    for (int ps = 0; ps < PPT && warp_on; ++ps) {
+      if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
+      const Pencil<n> pc(t + ps * TS);
       float acc[G::ROW];
       TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
       cpx<float> w[n];
@@ -442,16 +468,16 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     __syncthreads();
     if (valid && t == 0 && active) {
       double sum = 0.0;
-      for (int e = 0; e < G::TS; ++e) sum += red[slot * G::TS + e];
+      for (int e = 0; e < TS; ++e) sum += red[slot * TS + e];
       if (MODE == MODE_ENERGY) sum *= args.occ_own[k * args.n_occ + band];
       args.partial[split * args.split_stride + (size_t)k * args.n_own + band] = sum;
     }
   }
 }
 
-template <int n, int MODE, int MINB>
-__global__ void __launch_bounds__(Geo<n>::THREADS, MINB) pairconv_c64_kernel(const PairArgs args) {
-  using G = Geo<n>;
+template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT>
+__global__ void __launch_bounds__(GeoP<n, PPT, TSX>::THREADS, MINB) pairconv_c64_kernel(const PairArgs args) {
+  using G = GeoP<n, PPT, TSX>;
   extern __shared__ __align__(16) float4 smem4[];
   __shared__ uint32_t tmem_base_sh;
   const int warp = threadIdx.x >> 5;
@@ -463,7 +489,7 @@ __global__ void __launch_bounds__(Geo<n>::THREADS, MINB) pairconv_c64_kernel(con
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tbase = tmem_base_sh;
-  pairconv_item<n, MODE>(args, blockIdx.x, smem4, tbase, true);
+  pairconv_item<n, MODE, PPT, TSX>(args, blockIdx.x, smem4, tbase, true);
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();

@@ -1,7 +1,10 @@
-"""Each pencil layout of the staged-partner kernel against the FP64 oracle.
+"""Each pencil layout of the fused kernels against the FP64 oracle.
 
-The layout is chosen per plan through HSE_BLOCKS_PER_SM (-1 two pencils per thread, -2 one
-pencil per thread, -3 one pencil per thread plus the lane-split pencils of 20^3).  For every
+The layout is chosen per plan through HSE_BLOCKS_PER_SM: for the staged-partner kernel -1 two
+pencils per thread, -2 one pencil per thread, -3 one pencil per thread plus the lane-split
+pencils of 20^3; for the pencil-load kernel (24^3) 0 its default (two pencils per thread on 9
+warps, variant 1) and 3 the ragged form (12 warps, a second pencil for the first 192 threads;
+the default).  For every
 layout the test runs V_x u (owner = target apply), the exchange energy (energy epilogue) and
 the full vector-Jacobian product, whose d/d omega term runs the owner = target dot epilogue
 (Sec. II C; Eq. "Fock" and its derivative with respect to omega).
@@ -15,7 +18,7 @@ from paper_1507_05156_gb300 import hse, inputs
 
 pytestmark = pytest.mark.gpu
 
-LAYOUT_CASES = [(12, -1), (12, -2), (18, -1), (18, -2), (20, -1), (20, -2), (20, -3)]
+LAYOUT_CASES = [(12, -1), (12, -2), (18, -1), (18, -2), (20, -1), (20, -2), (20, -3), (24, 1), (24, 3)]
 
 
 def _dev(x, dtype):
