@@ -4,12 +4,12 @@
 // Each CTA takes work items from a global counter (largest first, as the host sorts them)
 // until its list is exhausted; an item is (cell, k'-split, k, owner tile).  The items are
 // split in two lists by the pipeline their side runs, each with its own persistent kernel:
-//   * staged-partner items (sides 8, 12, 18, 20; pairconv_tma.cuh): the partner orbitals
+//   * staged-partner items (sides 8, 12, 16, 18, 20; pairconv_tma.cuh): the partner orbitals
 //     stream in by TMA from the cell's tensor map into two stage buffers, the owner orbital
 //     and the accumulators stay in Tensor Memory.  512 threads (8^3 with eight owner slots of
 //     one pencil per thread);
-//   * pencil-load items (sides 16, 24; pairconv_c64.cuh; 24^3 in its ragged 12-warp form, 384
-//     threads): orbitals are read as pencils
+//   * pencil-load items (side 24; pairconv_c64.cuh; in its ragged 12-warp form, 384 threads):
+//     orbitals are read as pencils
 //     through L1.  That kernel keeps only its own shared-memory footprint so that L1 keeps
 //     the rest of the SM's storage: with the staged kernel's 208 KB of shared memory
 //     reserved, its 24^3 items ran 37% slower.
@@ -31,11 +31,12 @@ template <int n>
 using OneS = GeoS<n, LayoutOne<n>>;
 
 static_assert(LayoutOne<20>::THREADS <= kStagedThreads && LayoutOne<8>::THREADS <= kStagedThreads &&
+                  LayoutOne<16>::THREADS <= kStagedThreads &&
                   LayoutSeq<12>::THREADS <= kStagedThreads && LayoutOne<18>::THREADS <= kStagedThreads,
               "staged batched block too small for a side's layout");
-static_assert(Geo<16>::THREADS <= kPencilThreads && GeoP<24, 2, kRaggedThreads>::THREADS <= kPencilThreads,
+static_assert(GeoP<24, 2, kRaggedThreads>::THREADS <= kPencilThreads,
               "pencil-load batched block too small");
-static_assert(OneS<8>::FITS && SeqS<12>::FITS && OneS<18>::FITS && OneS<20>::FITS,
+static_assert(OneS<8>::FITS && SeqS<12>::FITS && OneS<16>::FITS && OneS<18>::FITS && OneS<20>::FITS,
               "staged layouts of the batched kernel must fit");
 
 // One staged item as a call of its own: each side's pipeline gets the whole register budget
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) pairconv_batched_staged_ker
     switch (c.n) {
       case 8: ok = staged_call<8, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutOne<8>::WARPS); break;
       case 12: ok = staged_call<12, MODE, LayoutSeq>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutSeq<12>::WARPS); break;
+      case 16: ok = staged_call<16, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutOne<16>::WARPS); break;
       case 18: ok = staged_call<18, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutOne<18>::WARPS); break;
       case 20: ok = staged_call<20, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutOne<20>::WARPS); break;
       default: break;  // the host puts only the sides above in this list
@@ -120,7 +122,6 @@ __global__ void __launch_bounds__(kPencilThreads, 1) pairconv_batched_pencil_ker
     const BatchItem wi = b.items[it];
     const BatchCell& c = b.cells[wi.cell];
     switch (c.n) {
-      case 16: pairconv_item<16, MODE>(c.pa, wi.item, smem4, tbase, warp < Geo<16>::WARPS); break;
       case 24:
         pairconv_item<24, MODE, 2, kRaggedThreads>(c.pa, wi.item, smem4, tbase,
                                                    warp < GeoP<24, 2, kRaggedThreads>::WARPS);
@@ -136,10 +137,10 @@ __global__ void __launch_bounds__(kPencilThreads, 1) pairconv_batched_pencil_ker
 }
 
 constexpr size_t max_c(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t kStagedSmem = max_c(max_c(OneS<8>::SMEM_REQUEST, SeqS<12>::SMEM_REQUEST),
+constexpr size_t kStagedSmem = max_c(max_c(max_c(OneS<8>::SMEM_REQUEST, SeqS<12>::SMEM_REQUEST), OneS<16>::SMEM_REQUEST),
                                      max_c(OneS<18>::SMEM_REQUEST, OneS<20>::SMEM_REQUEST));
 // >= 118784: a second CTA (which would need TMEM too) never fits
-constexpr size_t kPencilSmem = max_c(max_c(Geo<16>::SMEM_BYTES, Geo<24>::SMEM_BYTES), (size_t)118784);
+constexpr size_t kPencilSmem = max_c(Geo<24>::SMEM_BYTES, (size_t)118784);
 
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes, bool* done) {
@@ -162,6 +163,7 @@ bool batched_stage_geometry(int n, int* sp, int* box_rows) {
   switch (n) {
     case 8: *sp = StageGeo<8>::SP; *box_rows = StageGeo<8>::BR; return true;
     case 12: *sp = StageGeo<12>::SP; *box_rows = StageGeo<12>::BR; return true;
+    case 16: *sp = StageGeo<16>::SP; *box_rows = StageGeo<16>::BR; return true;
     case 18: *sp = StageGeo<18>::SP; *box_rows = StageGeo<18>::BR; return true;
     case 20: *sp = StageGeo<20>::SP; *box_rows = StageGeo<20>::BR; return true;
     default: return false;

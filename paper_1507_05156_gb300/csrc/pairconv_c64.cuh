@@ -40,7 +40,7 @@ __host__ __device__ constexpr KCfg kcfg(int n) {
          : n == 8  ? KCfg{9, 72, 1, 1, 8}
          : n == 10 ? KCfg{10, 106, 1, 2, 4}
          : n == 12 ? KCfg{12, 156, 1, 2, 4}
-         : n == 16 ? KCfg{16, 257, 0, 1, 2}
+         : n == 16 ? KCfg{17, 272, 1, 1, 2}
          : n == 18 ? KCfg{18, 338, 1, 2, 1}
          : n == 20 ? KCfg{21, 420, 1, 1, 1}
          : n == 24 ? KCfg{25, 600, 1, 1, 1}
