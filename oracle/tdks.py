@@ -16,6 +16,11 @@ Only ``tests/`` may use it.  Follows arXiv:1507.05156:
   orbital counts with g_s f_{i,k} / N_k.  With psi = e^{ik.r} u, u = sum_G c_G e^{iG.r}
   (c = the 1/N forward transform), int_Omega psi* (-i grad + A) psi = Omega sum_G |c_G|^2
   (G + k + A), so J = -sum_{k,i} (g_s f_{i,k} / N_k) sum_G |c_G|^2 (G + k + A).
+* Sec. II A (Eq. "tdks-h") and Sec. V (Eq. "Eex01"): the Hartree potential v_H of the density
+  rho(r) = sum_{k,i} (g_s f_{i,k} / N_k) |u_{i,k}(r)|^2, from Poisson's equation in atomic
+  units, -lap v_H = 4 pi (rho - rho_avg): v_H(G) = 4 pi rho~(G) / |G|^2, v_H(G = 0) = 0 (the
+  neutralising background), and the Hartree energy per cell 1/2 int_Omega v_H rho.  A local
+  potential v_loc(r) (v_H here) enters h as a multiplication.
 * Sec. IV (laser pulse): A(t) = -(E0 / w) cos(w t) sin^2(pi t / T_d) along a direction for
   0 < t < T_d (zero otherwise), E(t) = -dA/dt, and the energy given to the electrons per unit
   volume W(t) = int^t J(t') . E(t') dt' (Eq. for W in Sec. V).
@@ -42,20 +47,53 @@ def kinetic_apply(u, kpts, lattice, grid, A) -> np.ndarray:
     return out
 
 
-def hamiltonian_apply(psi_frozen, occ, phi, kpts, lattice, grid, A, omega, alpha) -> np.ndarray:
-    """h phi = T[A] phi + V_x[psi_frozen] phi."""
-    return kinetic_apply(phi, kpts, lattice, grid, A) + ho.fock_apply(
+def hamiltonian_apply(psi_frozen, occ, phi, kpts, lattice, grid, A, omega, alpha, vloc=None) -> np.ndarray:
+    """h phi = T[A] phi + v_loc phi + V_x[psi_frozen] phi (v_loc: a real grid, or None)."""
+    out = kinetic_apply(phi, kpts, lattice, grid, A) + ho.fock_apply(
         psi_frozen, occ, phi, kpts, lattice, grid, omega, alpha)
+    if vloc is not None:
+        grid = tuple(int(g) for g in grid)
+        out = out + np.asarray(vloc, dtype=np.float64).reshape(grid) * np.asarray(phi).reshape(out.shape)
+    return out
 
 
-def taylor_step(psi, occ, kpts, lattice, grid, A, omega, alpha, dt, order: int = 4) -> np.ndarray:
+def taylor_step(psi, occ, kpts, lattice, grid, A, omega, alpha, dt, order: int = 4, vloc=None) -> np.ndarray:
     """sum_{n=0}^{order} (-i dt h)^n / n! psi with h frozen at psi (Sec. II C)."""
     out = np.array(psi, dtype=np.complex128, copy=True)
     term = out.copy()
     for n in range(1, order + 1):
-        term = (-1j * dt / n) * hamiltonian_apply(psi, occ, term, kpts, lattice, grid, A, omega, alpha)
+        term = (-1j * dt / n) * hamiltonian_apply(psi, occ, term, kpts, lattice, grid, A, omega, alpha, vloc)
         out = out + term
     return out
+
+
+def density(u, occ, grid, spin_degeneracy: float = 2.0) -> np.ndarray:
+    """rho(r) = sum_{k,i} (g_s f_{i,k} / N_k) |u_{i,k}(r)|^2 (electrons per bohr^3)."""
+    grid = tuple(int(g) for g in grid)
+    u = np.asarray(u, dtype=np.complex128).reshape(np.shape(u)[:2] + grid)
+    occ = np.asarray(occ, dtype=np.float64)
+    return spin_degeneracy / u.shape[0] * np.einsum("kb,kbxyz->xyz", occ, np.abs(u) ** 2)
+
+
+def hartree_potential(u, occ, lattice, grid, spin_degeneracy: float = 2.0) -> np.ndarray:
+    """v_H(r) = sum_{G != 0} 4 pi rho~(G) / |G|^2 e^{iG.r}, real [N1][N2][N3]."""
+    grid = tuple(int(g) for g in grid)
+    rho_t = ho.forward_transform(density(u, occ, grid, spin_degeneracy))
+    G = ho.g_vectors(grid, lattice)
+    g2 = np.sum(G * G, axis=-1)
+    fac = np.zeros_like(g2)
+    nz = g2 > 0
+    fac[nz] = 4.0 * np.pi / g2[nz]
+    return np.real(ho.inverse_transform(rho_t * fac))
+
+
+def hartree_energy(u, occ, lattice, grid, spin_degeneracy: float = 2.0) -> float:
+    """E_H = 1/2 int_Omega v_H rho dr per cell (Eq. Eex01), by the grid sum with dV = Omega / N."""
+    grid = tuple(int(g) for g in grid)
+    rho = density(u, occ, grid, spin_degeneracy)
+    vh = hartree_potential(u, occ, lattice, grid, spin_degeneracy)
+    dV = ho.cell_volume(lattice) / np.prod(grid)
+    return float(0.5 * dV * np.sum(vh * rho))
 
 
 def propagate(psi0, occ, kpts, lattice, grid, omega, alpha, dt, nsteps, efield) -> np.ndarray:

@@ -165,3 +165,70 @@ def test_pulse_on_free_plane_wave_work_closed_form():
             assert abs(W[s] - Wex) <= tol
         norm *= td.taylor_norm_factor(0.5 * (gk @ gk) * dt)
     assert abs(W[-1]) <= tol
+
+
+# ---------------------------------------------------------------------------
+# Hartree potential (Sec. II A Eq. tdks-h, Sec. V Eq. Eex01)
+# ---------------------------------------------------------------------------
+
+def test_hartree_of_two_plane_waves_closed_form():
+    """u = (e^{iG1 r} + e^{iG2 r}) / sqrt(2 Omega): rho = c (1 + cos(dG . r)), c = g_s f / (N_k Omega), so
+    v_H = 4 pi c cos(dG . r) / |dG|^2 exactly (dG inside the box), and E_H = 1/2 Omega c^2 4 pi / |dG|^2 / 2."""
+    grid = (6, 5, 8)
+    A_ = TRICLINIC
+    Om = abs(np.linalg.det(A_))
+    b = 2 * np.pi * np.linalg.inv(A_).T
+    r = _positions(grid, A_)
+    G1 = 1 * b[0] - 1 * b[1] + 2 * b[2]
+    G2 = 0 * b[0] + 1 * b[1] + 1 * b[2]
+    u = ((np.exp(1j * (r @ G1)) + np.exp(1j * (r @ G2))) / np.sqrt(2 * Om))[None, None]
+    f = 0.8
+    c = 2.0 * f / Om
+    dG = G1 - G2
+    vh = td.hartree_potential(u, np.array([[f]]), A_, grid)
+    expect = 4 * np.pi * c * np.cos(r @ dG) / (dG @ dG)
+    np.testing.assert_allclose(vh, expect, rtol=0, atol=1e-13 * np.abs(expect).max())
+    eh = td.hartree_energy(u, np.array([[f]]), A_, grid)
+    assert abs(eh - 0.5 * Om * c * c * 4 * np.pi / (dG @ dG) / 2) <= 1e-13 * eh
+
+
+def test_hartree_of_uniform_density_vanishes_and_energy_is_nonnegative():
+    grid = (4, 5, 3)
+    kpts = np.array([[0.0, 0.0, 0.0], [0.1, -0.05, 0.2]])
+    A_ = TRICLINIC
+    Om = abs(np.linalg.det(A_))
+    b = 2 * np.pi * np.linalg.inv(A_).T
+    r = _positions(grid, A_)
+    G = 1 * b[0] + 1 * b[2]
+    u = np.exp(1j * (r @ G))[None, None].repeat(2, axis=0) / np.sqrt(Om)
+    assert np.abs(td.hartree_potential(u, np.ones((2, 1)), A_, grid)).max() < 1e-14
+    rng = np.random.default_rng(5)
+    w = inputs.orthonormal_orbitals(rng, grid, A_, kpts, 3, ecut=40.0)
+    occ = np.array([[1.0, 0.5, 0.2], [0.9, 0.4, 0.0]])
+    assert td.hartree_energy(w, occ, A_, grid) > 0
+    # charge: the density integrates to g_s sum f / N_k electrons per cell
+    rho = td.density(w, occ, grid)
+    assert abs(rho.sum() * Om / np.prod(grid) - 2.0 * occ.sum() / 2) < 1e-12
+
+
+def test_taylor_step_with_local_potential_matches_matrix_exponential():
+    """With a random real local potential added, h stays Hermitian and the Taylor step keeps its
+    fifth-order local error against expm(-i h dt) (halving dt divides it by ~32)."""
+    grid = (4, 4, 4)
+    lattice = inputs.cubic_lattice(5.0)
+    kpts = np.array([[0.05, 0.0, -0.03]])
+    rng = np.random.default_rng(7)
+    psi = inputs.orthonormal_orbitals(rng, grid, lattice, kpts, 2, ecut=50.0)
+    occ = np.ones((1, 2))
+    A = np.array([0.02, 0.0, 0.0])
+    vloc = rng.standard_normal(grid) * 0.3
+    N = 64
+    basis = np.eye(N, dtype=complex).reshape(N, *grid)[None]
+    H = td.hamiltonian_apply(psi, occ, basis, kpts, lattice, grid, A, 0.3, 0.25, vloc)[0].reshape(N, N).T
+    assert np.allclose(H, H.conj().T, atol=1e-12)
+    errs = []
+    for dt in (0.1, 0.05):
+        ref = (scipy.linalg.expm(-1j * dt * H) @ psi[0].reshape(2, N).T).T.reshape(psi.shape)
+        got = td.taylor_step(psi, occ, kpts, lattice, grid, A, 0.3, 0.25, dt, vloc=vloc)
+        errs.append(np.linalg.norm(got - ref))
+    assert errs[1] < errs[0] / 20
