@@ -182,17 +182,32 @@ int hse_exchange_energy_noalloc(const hse_problem *p, const void *u_occ, const d
 /* One fourth-order Taylor step of the time-dependent Kohn-Sham equation (Sec. II C, "time
  * evolution": the propagator exp[h dt / i] expanded to fourth order, with the Hamiltonian at
  * t + dt/2 taken at t, the choice the paper reports as sufficient for HSE):
- *   psi_out = sum_{n=0}^{4} (-i dt h)^n / n! psi,   h = T[A] + V_x[psi]
- * with T the velocity-gauge kinetic term of hse_kinetic_apply and V_x built from psi itself
+ *   psi_out = sum_{n=0}^{4} (-i dt h)^n / n! psi,   h = T[A] + v_loc + V_x[psi]
+ * with T the velocity-gauge kinetic term of hse_kinetic_apply, v_loc a real local potential
+ * (e.g. the Hartree potential of hse_hartree_potential for psi) and V_x built from psi itself
  * (the plan's occupied set) with occupations occ; the Hamiltonian is frozen over the step.
  *   psi, psi_out device [nk][n_occ][N] (the plan's dtype; the plan must have n_tgt == n_occ);
  *                must not overlap
  *   occ          device [nk][n_occ]
  *   A            HOST [3] vector potential at the start of the step (bohr^-1)
+ *   vloc         device double [N] local potential on the grid, or NULL for none
  * The first call allocates three orbital-sized scratch arrays in the plan (device-wide
  * synchronisation); later calls are asynchronous on `stream`.  Not for batched plans. */
 int hse_taylor_step(hse_plan plan, const void *psi, const double *occ, const double *A, double dt,
-                    void *psi_out, hse_stream_t stream);
+                    const double *vloc, void *psi_out, hse_stream_t stream);
+
+/* Hartree potential of the orbitals' density (Sec. II A, Eq. "tdks-h"; Poisson's equation in
+ * atomic units with a neutralising background):
+ *   rho(r) = sum_{k,i} (g_s f_{i,k} / N_k) |u_{i,k}(r)|^2,
+ *   v_H(r) = sum_{G != 0} 4 pi rho~(G) / |G|^2 e^{iG.r},  rho~ = (1/N) sum_r rho e^{-iG.r},
+ * in FP64 (density, transforms and scaling).  The Hartree energy of Eq. "Eex01" is
+ * 1/2 dV sum_r v_H rho.
+ *   psi  device [nk][n_occ][N] (the plan's dtype), occ device [nk][n_occ]
+ *   vh   device double [N], overwritten
+ * g_s is the plan's spin_degeneracy.  The first call allocates an N-point FP64 work array in
+ * the plan; later calls are asynchronous on `stream`.  Not for batched plans. */
+int hse_hartree_potential(hse_plan plan, const void *psi, const double *occ, double *vh,
+                          hse_stream_t stream);
 
 /* Spatially averaged electric current of the orbitals (Sec. II A, Eqs. "current_dns" and
  * "current_elec", without J_NL, the nonlocal pseudopotential part; atomic units, e/c

@@ -147,9 +147,9 @@ def pulse_field(t: float, E0: float, w: float, Td: float, direction) -> np.ndarr
 
 
 def propagate_pulse(psi0, occ, kpts, lattice, grid, omega, alpha, dt, nsteps, E0, w, Td, direction,
-                    spin_degeneracy: float = 2.0):
+                    spin_degeneracy: float = 2.0, hartree: bool = False):
     """nsteps Taylor steps under the pulse; step s (t_s = s dt -> t_s + dt) uses h frozen at
-    psi(t_s) with A(t_s).  Returns (psi, J [nsteps+1][3], W [nsteps+1]) with J_s = J(t_s)
+    psi(t_s) with A(t_s) (and, with ``hartree``, v_H of psi(t_s) as a local potential).  Returns (psi, J [nsteps+1][3], W [nsteps+1]) with J_s = J(t_s)
     from psi(t_s) and A(t_s), and W by the trapezoidal rule on J . E."""
     psi = np.array(psi0, dtype=np.complex128, copy=True)
     Js, Ws = [], [0.0]
@@ -162,5 +162,6 @@ def propagate_pulse(psi0, occ, kpts, lattice, grid, omega, alpha, dt, nsteps, E0
             e1 = pulse_field(t, E0, w, Td, direction)
             Ws.append(Ws[-1] + 0.5 * dt * (Js[-2] @ e0 + Js[-1] @ e1))
         if s < nsteps:
-            psi = taylor_step(psi, occ, kpts, lattice, grid, A, omega, alpha, dt)
+            vloc = hartree_potential(psi, occ, lattice, grid, spin_degeneracy) if hartree else None
+            psi = taylor_step(psi, occ, kpts, lattice, grid, A, omega, alpha, dt, vloc=vloc)
     return psi, np.array(Js), np.array(Ws)

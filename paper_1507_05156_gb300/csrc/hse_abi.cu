@@ -275,6 +275,7 @@ struct hse_plan_s {
   void* tay[3] = {nullptr, nullptr, nullptr};  // Taylor step: term, T term, V_x term [nk][n_occ][N]
   double2* cur_work = nullptr;  // current: FP64 transforms [nk][n_occ][N]
   double* cur_partial = nullptr;  // current: [nk][n_occ][3]
+  double2* hart_work = nullptr;   // Hartree potential: [N] FP64 transform
   // batched plans (hse_plan_create_batched)
   bool batched = false;
   std::vector<hse_plan> cells;          // one sub-plan (kernel tables) per cell
@@ -409,6 +410,7 @@ int hse_plan_destroy(hse_plan plan) {
   for (void* b : plan->tay) cudaFree(b);
   cudaFree(plan->cur_work);
   cudaFree(plan->cur_partial);
+  cudaFree(plan->hart_work);
   cudaSetDevice(prev);
   delete plan;
   return HSE_OK;
@@ -1034,8 +1036,8 @@ int hse_kinetic_apply(hse_plan plan, const void* u, int nbands, const double* A,
   return cuda_fail(launch_kinetic_f64((const double2*)u, (double2*)out, a, st));
 }
 
-int hse_taylor_step(hse_plan plan, const void* psi, const double* occ, const double* A, double dt, void* psi_out,
-                    hse_stream_t stream) {
+int hse_taylor_step(hse_plan plan, const void* psi, const double* occ, const double* A, double dt, const double* vloc,
+                    void* psi_out, hse_stream_t stream) {
   if (!plan || plan->batched || !psi || !occ || !A || !psi_out || !std::isfinite(dt)) return HSE_ERR_INVALID_ARG;
   const hse_problem& p = plan->p;
   if (p.n_tgt != p.n_occ) return HSE_ERR_INVALID_ARG;  // the step propagates the occupied set
@@ -1044,7 +1046,8 @@ int hse_taylor_step(hse_plan plan, const void* psi, const double* occ, const dou
   if (!aligned16(psi) || !aligned16(psi_out)) return HSE_ERR_INVALID_ARG;
   const size_t count = (size_t)p.nk * p.n_occ * plan->N;
   const size_t bytes = count * elem_bytes(p.dtype);
-  if (overlaps(psi_out, bytes, psi, bytes) || overlaps(psi_out, bytes, occ, (size_t)p.nk * p.n_occ * sizeof(double)))
+  if (overlaps(psi_out, bytes, psi, bytes) || overlaps(psi_out, bytes, occ, (size_t)p.nk * p.n_occ * sizeof(double)) ||
+      overlaps(psi_out, bytes, vloc, (size_t)plan->N * sizeof(double)))
     return HSE_ERR_ALIAS;
   for (void*& b : plan->tay)
     if (!b) {
@@ -1060,8 +1063,8 @@ int hse_taylor_step(hse_plan plan, const void* psi, const double* occ, const dou
     if (rc) return rc;
     rc = hse_fock_apply(plan, psi, occ, term, plan->tay[2], stream);
     if (rc) return rc;
-    e = launch_taylor_accumulate(p.dtype == HSE_C128, plan->tay[1], plan->tay[2], plan->tay[0], psi_out, count,
-                                 dt / n, st);
+    e = launch_taylor_accumulate(p.dtype == HSE_C128, plan->tay[1], plan->tay[2], term, vloc, (size_t)plan->N,
+                                 plan->tay[0], psi_out, count, dt / n, st);
     if (e != cudaSuccess) return cuda_fail(e);
     term = plan->tay[0];
   }
@@ -1091,6 +1094,25 @@ int hse_current(hse_plan plan, const void* psi, const double* occ, const double*
   a.kpts = plan->dkpts;
   return cuda_fail(launch_current(p.dtype == HSE_C128, psi, occ, a, plan->cur_work, plan->cur_partial,
                                   p.spin_degeneracy, J, S(stream)));
+}
+
+int hse_hartree_potential(hse_plan plan, const void* psi, const double* occ, double* vh, hse_stream_t stream) {
+  if (!plan || plan->batched || !psi || !occ || !vh) return HSE_ERR_INVALID_ARG;
+  if (!aligned16(psi)) return HSE_ERR_INVALID_ARG;
+  const hse_problem& p = plan->p;
+  if (!plan->hart_work) {
+    const cudaError_t e = cudaMalloc(&plan->hart_work, (size_t)plan->N * sizeof(double2));
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  CurArgs a{};
+  a.n1 = p.grid[0];
+  a.n2 = p.grid[1];
+  a.n3 = p.grid[2];
+  a.nk = p.nk;
+  a.nbands = p.n_occ;
+  std::memcpy(a.b, plan->b, sizeof(a.b));
+  a.kpts = plan->dkpts;
+  return cuda_fail(launch_hartree(p.dtype == HSE_C128, psi, occ, a, p.spin_degeneracy, plan->hart_work, vh, S(stream)));
 }
 
 int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells) {

@@ -27,8 +27,11 @@ struct CurArgs {
   double A[3];          // vector potential (bohr^-1)
   const double* kpts;   // device [nk][3]
 };
-cudaError_t launch_taylor_accumulate(bool c128, const void* kin, const void* vx, void* term, void* out, size_t count,
-                                     double s, cudaStream_t stream);
+cudaError_t launch_taylor_accumulate(bool c128, const void* kin, const void* vx, const void* prev, const double* vloc,
+                                     size_t N, void* term, void* out, size_t count, double s, cudaStream_t stream);
+// v_H (device double [N]) of the orbitals' density; work: [N] double2 scratch.
+cudaError_t launch_hartree(bool c128, const void* psi, const double* occ, const CurArgs& a, double spin_degeneracy,
+                           double2* work, double* vh, cudaStream_t stream);
 // J (device double[3]) from the orbitals psi [nk][nbands][N] and occupations [nk][nbands];
 // work: [nk][nbands][N] double2 scratch, partial: [nk][nbands][3] double scratch.
 cudaError_t launch_current(bool c128, const void* psi, const double* occ, const CurArgs& a, double2* work,

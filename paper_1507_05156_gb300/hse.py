@@ -33,7 +33,7 @@ ERRORS = {
 EXPORTS = ("hse_plan_create", "hse_plan_create_batched", "hse_plan_destroy", "hse_fock_apply",
            "hse_exchange_energy", "hse_fock_apply_vjp", "hse_fock_apply_batched", "hse_status",
            "hse_grid_supported", "hse_kernel_launches", "hse_strerror", "hse_exchange_energy_noalloc",
-           "hse_kinetic_apply", "hse_taylor_step", "hse_current")
+           "hse_kinetic_apply", "hse_taylor_step", "hse_current", "hse_hartree_potential")
 
 
 class HseError(RuntimeError):
@@ -88,10 +88,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hse_exchange_energy_noalloc.restype = i
         lib.hse_kinetic_apply.argtypes = [vp, vp, i, ctypes.POINTER(ctypes.c_double), vp, vp]
         lib.hse_kinetic_apply.restype = i
-        lib.hse_taylor_step.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.c_double, vp, vp]
+        lib.hse_taylor_step.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.c_double, vp, vp, vp]
         lib.hse_taylor_step.restype = i
         lib.hse_current.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp]
         lib.hse_current.restype = i
+        lib.hse_hartree_potential.argtypes = [vp, vp, vp, vp, vp]
+        lib.hse_hartree_potential.restype = i
         lib.hse_strerror.argtypes = [i]
         lib.hse_strerror.restype = ctypes.c_char_p
         for name in ("hse_plan_create", "hse_plan_create_batched", "hse_plan_destroy", "hse_fock_apply",
@@ -339,17 +341,33 @@ def _vec3(A):
 
 
 def hse_taylor_step(plan: Plan, psi: torch.Tensor, occ: torch.Tensor, A, dt: float,
-                    out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-    """One fourth-order Taylor step psi -> sum_n (-i dt h)^n / n! psi, h = T[A] + V_x[psi]
-    frozen over the step (the plan's occupied set is psi; n_tgt == n_occ)."""
+                    vloc: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+                    stream=None) -> torch.Tensor:
+    """One fourth-order Taylor step psi -> sum_n (-i dt h)^n / n! psi, h = T[A] + v_loc + V_x[psi]
+    frozen over the step (the plan's occupied set is psi; n_tgt == n_occ); vloc: float64 grid."""
+    lib = load_library()
+    _dev(psi, plan, plan.shape(plan.n_occ), plan.dtype, "psi")
+    _dev(occ, plan, (plan.nk, plan.n_occ), torch.float64, "occ")
+    _dev(vloc, plan, plan.grid, torch.float64, "vloc")
+    if out is None:
+        out = torch.empty_like(psi)
+    _dev(out, plan, plan.shape(plan.n_occ), plan.dtype, "out")
+    _check(lib.hse_taylor_step(plan.handle, _ptr(psi), _ptr(occ), _vec3(A), float(dt), _ptr(vloc), _ptr(out),
+                               _stream(stream)), "hse_taylor_step")
+    return out
+
+
+def hse_hartree_potential(plan: Plan, psi: torch.Tensor, occ: torch.Tensor, out: Optional[torch.Tensor] = None,
+                          stream=None) -> torch.Tensor:
+    """Hartree potential (float64 grid on the device) of the density of psi [nk][n_occ][grid]."""
     lib = load_library()
     _dev(psi, plan, plan.shape(plan.n_occ), plan.dtype, "psi")
     _dev(occ, plan, (plan.nk, plan.n_occ), torch.float64, "occ")
     if out is None:
-        out = torch.empty_like(psi)
-    _dev(out, plan, plan.shape(plan.n_occ), plan.dtype, "out")
-    _check(lib.hse_taylor_step(plan.handle, _ptr(psi), _ptr(occ), _vec3(A), float(dt), _ptr(out), _stream(stream)),
-           "hse_taylor_step")
+        out = torch.empty(plan.grid, dtype=torch.float64, device=plan.device)
+    _dev(out, plan, plan.grid, torch.float64, "out")
+    _check(lib.hse_hartree_potential(plan.handle, _ptr(psi), _ptr(occ), _ptr(out), _stream(stream)),
+           "hse_hartree_potential")
     return out
 
 

@@ -135,9 +135,10 @@ def pulse_field(t: float, E0: float, w: float, Td: float, direction) -> np.ndarr
 
 
 def propagate_pulse(psi0: torch.Tensor, occ: torch.Tensor, omega: float, geom: Geometry, dt: float, nsteps: int,
-                    E0: float, w: float, Td: float, direction):
+                    E0: float, w: float, Td: float, direction, hartree: bool = False):
     """nsteps fused Taylor steps under the pulse.  Step s (t_s = s dt) uses h frozen at psi(t_s)
-    with A(t_s); J_s = J(t_s) from psi(t_s) and A(t_s); W by the trapezoidal rule on J . E.
+    with A(t_s) (and, with ``hartree``, the Hartree potential of psi(t_s)); J_s = J(t_s) from
+    psi(t_s) and A(t_s); W by the trapezoidal rule on J . E.
     Returns (psi(t_nsteps), J [nsteps+1][3] float64 on the device, W [nsteps+1] numpy)."""
     plan = geom.plan(psi0.shape[1], psi0.shape[1], omega, psi0.dtype)
     bufs = [psi0.contiguous().clone(), torch.empty_like(psi0)]
@@ -146,7 +147,8 @@ def propagate_pulse(psi0: torch.Tensor, occ: torch.Tensor, omega: float, geom: G
         A = pulse_vector_potential(s * dt, E0, w, Td, direction)
         hse.hse_current(plan, bufs[0], occ, A, out=J[s])
         if s < nsteps:
-            hse.hse_taylor_step(plan, bufs[0], occ, A, dt, out=bufs[1])
+            vh = hse.hse_hartree_potential(plan, bufs[0], occ) if hartree else None
+            hse.hse_taylor_step(plan, bufs[0], occ, A, dt, vloc=vh, out=bufs[1])
             bufs.reverse()
     Jh = J.cpu().numpy()
     E = np.stack([pulse_field(s * dt, E0, w, Td, direction) for s in range(nsteps + 1)])

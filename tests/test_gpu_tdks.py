@@ -179,15 +179,42 @@ def test_current_matches_oracle(dtype, grid, lattice, tol):
     assert np.abs(J - ref).max() <= tol * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-9), (torch.complex64, 2e-5)])
-def test_pulse_driver_matches_oracle(dtype, tol):
+@pytest.mark.parametrize("dtype,grid,lattice", [(torch.complex64, (12, 12, 12), inputs.cubic_lattice(10.26)),
+                                                (torch.complex128, (6, 5, 4), TRICLINIC)])
+def test_hartree_potential_matches_oracle(dtype, grid, lattice):
+    kpts, u, occ = _tdks_cell(34, grid, lattice, 3, 2, dtype)
+    plan = hse.get_plan(grid, lattice, kpts, 2, 2, 0.2, 0.25, dtype=dtype)
+    vh = hse.hse_hartree_potential(plan, dev(u, dtype), dev(occ, torch.float64)).cpu().numpy()
+    ref = otd.hartree_potential(u, occ, lattice, grid, 2.0)
+    assert np.abs(vh - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dtype,grid,lattice,tol", STEP_CASES)
+def test_fused_taylor_step_with_hartree_matches_oracle(dtype, grid, lattice, tol):
+    kpts, u, occ = _tdks_cell(35, grid, lattice, 2, 3, dtype)
+    A = np.array([0.0, 0.01, -0.02])
+    dt, omega, alpha = 0.05, 0.2, 0.25
+    plan = hse.get_plan(grid, lattice, kpts, 3, 3, omega, alpha, dtype=dtype)
+    psi = dev(u, dtype)
+    vh = hse.hse_hartree_potential(plan, psi, dev(occ, torch.float64))
+    got = hse.hse_taylor_step(plan, psi, dev(occ, torch.float64), A, dt, vloc=vh).cpu().numpy()
+    ref = otd.taylor_step(u, occ, kpts, lattice, grid, A, omega, alpha, dt,
+                          vloc=otd.hartree_potential(u, occ, lattice, grid, 2.0))
+    assert rel(got - u, ref - u) <= tol
+
+
+@pytest.mark.parametrize("dtype,tol,hartree", [(torch.complex128, 1e-9, False), (torch.complex64, 2e-5, False),
+                                               (torch.complex128, 1e-9, True)])
+def test_pulse_driver_matches_oracle(dtype, tol, hartree):
     grid, lattice = (8, 8, 8), inputs.cubic_lattice(10.26)
     kpts, u, occ = _tdks_cell(33, grid, lattice, 2, 2, dtype)
     E0, w, Td, d = 0.02, 0.3, 2.0, (0.0, 0.6, 0.8)
     dt, nsteps, omega = 0.1, 12, 0.2
     geom = tdks.Geometry(grid, lattice, kpts, alpha=0.25)
-    psi, J, W = tdks.propagate_pulse(dev(u, dtype), dev(occ, torch.float64), omega, geom, dt, nsteps, E0, w, Td, d)
-    r_psi, r_J, r_W = otd.propagate_pulse(u, occ, kpts, lattice, grid, omega, 0.25, dt, nsteps, E0, w, Td, d)
+    psi, J, W = tdks.propagate_pulse(dev(u, dtype), dev(occ, torch.float64), omega, geom, dt, nsteps, E0, w, Td, d,
+                                     hartree=hartree)
+    r_psi, r_J, r_W = otd.propagate_pulse(u, occ, kpts, lattice, grid, omega, 0.25, dt, nsteps, E0, w, Td, d,
+                                          hartree=hartree)
     assert rel(psi.cpu().numpy(), r_psi) <= tol
     J = J.cpu().numpy()
     assert np.abs(J - r_J).max() <= tol * np.abs(r_J).max()
