@@ -302,6 +302,25 @@ def run_cuda(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(spec: str):
+    """Two applies of one seeded cell (grid side n, n_k^3 Monkhorst-Pack k-points, nb bands,
+    complex64): the launch an ncu capture of a secondary kernel selects with -s 1 -c 1.  Prints
+    no bench line."""
+    import torch
+    from paper_1507_05156_gb300 import hse, inputs
+    n, km, nb = (int(x) for x in spec.split(","))
+    cell = inputs.make_cell(inputs.SEED_BASE + 100 + n, (n, n, n), (km, km, km), nb, name=f"c64_{n}cube_k{km}_b{nb}")
+    u = torch.from_numpy(cell.u_occ.astype(np.complex64)).cuda()
+    occ = torch.from_numpy(cell.occ).cuda()
+    plan = hse.get_plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha)
+    out = torch.empty_like(u)
+    for _ in range(2):
+        hse.hse_fock_apply(plan, u, occ, u, out=out)
+    torch.cuda.synchronize()
+    hse.hse_status(plan)
+    print(f"profile case {cell.name}: {cell.pairs} pair convolutions per apply", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -311,7 +330,12 @@ def main():
     ap.add_argument("--cpu-targets", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--profile-case", default=None, metavar="N,KM,NB",
+                    help="only run two applies of one cell (for ncu captures of secondary kernels)")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
