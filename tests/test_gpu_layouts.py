@@ -2,9 +2,10 @@
 
 The layout is chosen per plan through HSE_BLOCKS_PER_SM: for the staged-partner kernel -1 two
 pencils per thread, -2 one pencil per thread, -3 one pencil per thread plus the lane-split
-pencils of 20^3; for the pencil-load kernel (24^3) 0 its default (two pencils per thread on 9
-warps, variant 1) and 3 the ragged form (12 warps, a second pencil for the first 192 threads;
-the default).  For every
+pencils of 20^3; for the pencil-load kernel 1 one CTA per SM with uncapped registers (two
+pencils per thread on 9 warps at 24^3), 2 two CTAs per SM where they fit (16^3), and 3 the
+ragged 24^3 form (12 warps, a second pencil for the first 192 threads; the default there).
+For every
 layout the test runs V_x u (owner = target apply), the exchange energy (energy epilogue) and
 the full vector-Jacobian product, whose d/d omega term runs the owner = target dot epilogue
 (Sec. II C; Eq. "Fock" and its derivative with respect to omega).
