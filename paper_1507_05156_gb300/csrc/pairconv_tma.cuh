@@ -160,6 +160,15 @@ struct LayoutLin {
   static __device__ __forceinline__ void cache_row(int t, uint32_t trow0, const float* vrow, float scale) {
     cache_kernel_row<n, PPT, XP>(t, trow0 + (uint32_t)TAB, vrow, scale);
   }
+  // Warp-local planes.  Pencil p of the Z and Y stages lies in the x-plane p / n; when n
+  // divides 32, the 32 consecutive pencils of a warp's pass are 32 / n whole planes in both
+  // stages (and a warp never straddles two owner slots), so the Y stage after a Z stage and the
+  // Z stage after a Y stage read only what the same warp wrote: __syncwarp replaces the block
+  // barrier there, and only the X stage, which reads every plane, keeps block barriers.  (Groups
+  // of several warps under named barriers measured slower: 20^3 34.6 -> 35.9 ms, 18^3 1.23 ->
+  // 1.25 ms; warp-local 16^3 14.40 -> 14.23 ms, 8^3 1.87 -> 1.84 ms.)
+  static constexpr bool GROUPED = 32 % n == 0 && (G::T == 1 || TS % 32 == 0);
+  static __device__ __forceinline__ void group_sync(int) { __syncwarp(); }
   // pencils beyond the regular ones (LayoutSplit): none here
   static __device__ __forceinline__ bool regular(int) { return true; }
   static __device__ __forceinline__ void extra_init(int, const float2*, uint32_t) {}
@@ -233,6 +242,9 @@ struct LayoutSplit {
   // beside them, the bank-spread X order measured slower, 35.3 against 34.7 ms at 20^3)
   using Reg = LayoutLin<n, 1, false>;
   static __device__ __forceinline__ bool regular(int t) { return t < SG::R; }
+  // block barriers only
+  static constexpr bool GROUPED = false;
+  static __device__ __forceinline__ void group_sync(int) {}
 
   // role of this lane in the hosting warp: s = scheduler, A: (pencil, b), B: (pencil, k1)
   struct Roles {
@@ -578,20 +590,33 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
     }
     if (buf) phase1 ^= 1u; else phase0 ^= 1u;
     const float2* stg = stage + buf * S::STAGE_CPX;
-    if (on) Lay::z_forward(g, t, valid, stg, trow0);
-    __syncthreads();
-    // every thread is past its last read of stage[buf ^ 1]: refill it with the next partner
     const int qn = next_partner(sh.occ, args, kp_begin, q + 1, npairs);
-    if (warp == 0 && qn < npairs && !sh.abort) {
-      fence_proxy_async_smem();
-      fill(qn, buf ^ 1);
+    // refill stage[buf ^ 1] with the next partner once every thread is past its last read of it
+    // (the previous pair's Z inverse)
+    auto refill = [&]() {
+      if (warp == 0 && qn < npairs && !sh.abort) {
+        fence_proxy_async_smem();
+        fill(qn, buf ^ 1);
+      }
+    };
+    if (on) Lay::z_forward(g, t, valid, stg, trow0);
+    if constexpr (Lay::GROUPED) {
+      if (on) Lay::group_sync(tid);
+    } else {
+      __syncthreads();
+      refill();
     }
     if (on) Lay::template y<-1>(g, t, valid);
     __syncthreads();
+    if constexpr (Lay::GROUPED) refill();
     if (on) Lay::x(g, t, valid, trow0, f);
     __syncthreads();
     if (on) Lay::template y<+1>(g, t, valid);
-    __syncthreads();
+    if constexpr (Lay::GROUPED) {
+      if (on) Lay::group_sync(tid);
+    } else {
+      __syncthreads();
+    }
     if (on) Lay::z_inverse(g, t, stg, trow0);
     q = qn;
     buf ^= 1;

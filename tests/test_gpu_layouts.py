@@ -19,7 +19,7 @@ from paper_1507_05156_gb300 import hse, inputs
 
 pytestmark = pytest.mark.gpu
 
-LAYOUT_CASES = [(12, -1), (12, -2), (16, -1), (16, -2), (16, 2), (18, -1), (18, -2), (20, -1), (20, -2), (20, -3), (24, 1), (24, 3)]
+LAYOUT_CASES = [(12, -1), (12, -2), (16, -1), (16, -2), (16, 2), (18, -1), (18, -2), (20, -1), (20, -2), (20, -3), (8, -1), (8, -2), (24, 1), (24, 3)]
 
 
 def _dev(x, dtype):
