@@ -38,6 +38,17 @@ int occupancy_pairconv_c64_small(int n, int mode, int bps);
 int occupancy_pairconv_c64_mid(int n, int mode, int bps);
 int occupancy_pairconv_c64_20(int mode, int bps);
 int occupancy_pairconv_c64_24(int mode, int bps);
+bool pencil_load_pairconv_c64_small(int n, int mode, int bps);
+bool pencil_load_pairconv_c64_mid(int n, int mode, int bps);
+bool pencil_load_pairconv_c64_20(int mode, int bps);
+bool pencil_load_pairconv_c64_24(int mode, int bps);
+
+bool pairconv_c64_pencil_load(int n, int mode, int bps) {
+  if (n <= 12) return pencil_load_pairconv_c64_small(n, mode, bps);
+  if (n <= 18) return pencil_load_pairconv_c64_mid(n, mode, bps);
+  if (n == 20) return pencil_load_pairconv_c64_20(mode, bps);
+  return pencil_load_pairconv_c64_24(mode, bps);
+}
 
 int pairconv_c64_occupancy(int n, int mode, int bps) {
   if (n <= 12) return occupancy_pairconv_c64_small(n, mode, bps);
@@ -66,6 +77,22 @@ __global__ void reduce_splits_batched(const BatchCell* __restrict__ cells, int n
       }
       out[i] = a;
     }
+  }
+}
+
+// Copy of norb orbitals in the pencil-blocked layout of the pencil-load kernel: the 16-byte
+// chunk e (elements 2e, 2e + 1) of z-pencil p = 32 b + l goes to float4 (b n/2 + e) 32 + l of
+// the orbital's nbk / 2 float4s; one thread per source chunk (coalesced reads).  The padding
+// of a last partial block is left as it is (never read).
+__global__ void to_pencil_blocks(float4* __restrict__ dst, const float4* __restrict__ src, int n, size_t nbk4,
+                                 size_t norb) {
+  const int h = n / 2;
+  const size_t n4 = (size_t)n * n * h;  // float4 per orbital
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < norb * n4; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t o = i / n4;
+    const size_t r = i - o * n4;
+    const int p = (int)(r / h), e = (int)(r - (size_t)p * h);
+    dst[o * nbk4 + ((size_t)(p >> 5) * h + e) * 32 + (p & 31)] = __ldg(src + i);
   }
 }
 
@@ -257,11 +284,16 @@ struct hse_plan_s {
   double2* work = nullptr;   // [batch][N]
   size_t work_pairs = 0;
   double2* vx64 = nullptr;   // [nk][max(n_occ, n_tgt)][N]
+  bool blocked = true;       // pencil-load launches read pencil-blocked copies (HSE_PENCIL_BLOCKS=0: no)
   int blocks_per_sm = 0;     // fused-kernel variant: 0 default, -1/-2/-3 staged-partner layouts, 1/2/3 pencil loads
   int inject = 0;            // test hook (HSE_INJECT_SKIP_FILL=1 at plan creation)
   int nsplit[3] = {1, 1, 1};  // k'-loop splits of the fused kernel per OwnerRole
   float2* split_buf = nullptr;  // [nsplit][nk_own][n_own][N] partial outputs when nsplit > 1
   size_t split_buf_elems = 0;
+  // pencil-blocked copies of the orbital arrays a pencil-load launch reads (allocated on first
+  // use, grown when a larger call comes)
+  float2* blk_buf = nullptr;
+  size_t blk_elems = 0;
   // down-sampled Fock sum
   int nkq = 0;                  // k-points of the Fock sum: nk, or nk_occ when sampled
   bool sampled = false;
@@ -281,6 +313,7 @@ struct hse_plan_s {
   std::vector<hse_plan> cells;          // one sub-plan (kernel tables) per cell
   std::vector<BatchCell> h_cells;       // launch arguments, pointers refreshed per call
   std::vector<float2*> cell_split;      // per cell [kMaxBatchSplit][nk][n_tgt][N]
+  std::vector<float2*> cell_blk;        // pencil-load cells: blocked u_tgt then u_occ (else null)
   BatchCell* d_cells = nullptr;
   BatchItem* d_items = nullptr;         // staged-partner items, then pencil-load items
   int* d_counter = nullptr;             // [2]: one per list
@@ -385,6 +418,7 @@ int hse_plan_destroy(hse_plan plan) {
   cudaSetDevice(plan->device);
   for (hse_plan c : plan->cells) hse_plan_destroy(c);
   for (float2* b : plan->cell_split) cudaFree(b);
+  for (float2* b : plan->cell_blk) cudaFree(b);
   cudaFree(plan->d_cells);
   cudaFree(plan->d_items);
   cudaFree(plan->d_counter);
@@ -402,6 +436,7 @@ int hse_plan_destroy(hse_plan plan) {
   cudaFree(plan->work);
   cudaFree(plan->vx64);
   cudaFree(plan->split_buf);
+  cudaFree(plan->blk_buf);
   cudaFree(plan->d_kocc);
   cudaFree(plan->d_kinv);
   cudaFree(plan->u_sub);
@@ -441,6 +476,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   plan->p.kocc = plan->sampled ? plan->kocc.data() : nullptr;
   cudaGetDevice(&plan->device);
   if (const char* env = std::getenv("HSE_INJECT_SKIP_FILL")) plan->inject = std::atoi(env) == 1 ? 1 : 0;
+  if (const char* env = std::getenv("HSE_PENCIL_BLOCKS")) plan->blocked = std::atoi(env) != 0;
   if (const char* env = std::getenv("HSE_BLOCKS_PER_SM")) {
     const int v = std::atoi(env);
     plan->blocks_per_sm = (v < -3 || v > 3) ? 0 : v;
@@ -635,10 +671,58 @@ PairArgs base_args(hse_plan plan) {
 
 int role_of(int mode) { return mode == MODE_ENERGY ? ROLE_ENERGY : (mode == MODE_OCC ? ROLE_OCC : ROLE_TGT); }
 
+// Blocked layouts of the orbital arrays a pencil-load launch reads (own, part and, for
+// MODE_DOT / MODE_OCC, part2), in the plan's scratch; an array given twice is copied once.
+int to_blocked(hse_plan plan, int mode, PairArgs& a, cudaStream_t st) {
+  const int n = plan->p.grid[0];
+  const size_t nbk = blocked_stride(n);
+  struct Arr {
+    const float2** ptr;
+    size_t norb;
+  };
+  Arr arrs[3] = {{&a.own, (size_t)a.nk_own * a.n_own}, {&a.part, (size_t)a.nk_part * a.n_part}, {&a.part2, 0}};
+  if (mode == MODE_DOT) arrs[2].norb = (size_t)a.nk_own * a.n_own;
+  if (mode == MODE_OCC) arrs[2].norb = (size_t)a.nk_part * a.n_part;
+  size_t need = 0;
+  for (const Arr& r : arrs) need += r.norb * nbk;
+  if (need > plan->blk_elems) {
+    cudaFree(plan->blk_buf);
+    plan->blk_buf = nullptr;
+    plan->blk_elems = 0;
+    const cudaError_t e = cudaMalloc(&plan->blk_buf, need * sizeof(float2));
+    if (e != cudaSuccess) return cuda_fail(e);
+    plan->blk_elems = need;
+  }
+  const float2* src[3] = {a.own, a.part, a.part2};
+  const float2* dst[3] = {nullptr, nullptr, nullptr};
+  size_t off = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (!arrs[i].norb) continue;
+    for (int j = 0; j < i; ++j)
+      if (arrs[j].norb == arrs[i].norb && src[j] == src[i]) dst[i] = dst[j];
+    if (!dst[i]) {
+      float2* d = plan->blk_buf + off;
+      off += arrs[i].norb * nbk;
+      const size_t count4 = arrs[i].norb * plan->N / 2;
+      const unsigned blocks = (unsigned)std::min<size_t>((count4 + 255) / 256, 152 * 16);
+      to_pencil_blocks<<<blocks, 256, 0, st>>>((float4*)d, (const float4*)src[i], n, nbk / 2, arrs[i].norb);
+      count_launch();
+      dst[i] = d;
+    }
+    *arrs[i].ptr = dst[i];
+  }
+  a.blk = 1;
+  return cuda_fail(cudaGetLastError());
+}
+
 int run_pairconv(hse_plan plan, int mode, PairArgs a, int n_own, cudaStream_t st) {
   const int n = plan->p.grid[0];
   const int T = slots_for(n);
   a.n_own = n_own;
+  if (pairconv_c64_pencil_load(n, mode, plan->blocks_per_sm) && plan->blocked) {
+    const int rc = to_blocked(plan, mode, a, st);
+    if (rc) return rc;
+  }
   a.ntiles = (n_own + T - 1) / T;
   a.nsplit = plan->nsplit[role_of(mode)];
   const size_t count = (size_t)a.nk_own * n_own * plan->N;
@@ -1146,6 +1230,11 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
     float2* buf = nullptr;
     if (q.nk > 1) e = cudaMalloc(&buf, (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * q.n_tgt * sub->N * sizeof(float2));
     plan->cell_split.push_back(buf);
+    float2* blk = nullptr;
+    int sp = 0, br = 0;
+    if (e == cudaSuccess && !batched_stage_geometry(q.grid[0], &sp, &br))
+      e = cudaMalloc(&blk, (size_t)q.nk * (q.n_tgt + q.n_occ) * blocked_stride(q.grid[0]) * sizeof(float2));
+    plan->cell_blk.push_back(blk);
   }
   if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_cells, (size_t)ncells * sizeof(BatchCell));
   if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_items, max_items * sizeof(BatchItem));
@@ -1198,6 +1287,33 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
     a.nsplit = bc.pa.nsplit > 0 ? bc.pa.nsplit : 1;
     a.split_stride = (size_t)sub->p.nk * a.n_own * sub->N;
     a.out = a.nsplit > 1 ? plan->cell_split[c] : (float2*)vx_out[c];
+    if (plan->cell_blk[c]) {
+      // the pencil-load pipeline reads pencil-blocked copies (refreshed on every call, before
+      // the graph)
+      const int n = sub->p.grid[0];
+      const size_t nbk = blocked_stride(n);
+      const size_t ntgt = (size_t)sub->p.nk * sub->p.n_tgt, nocc = (size_t)sub->p.nk * sub->p.n_occ;
+      float2* bt = plan->cell_blk[c];
+      float2* bo = bt + ntgt * nbk;
+      const float2* srcs[2] = {a.own, a.part};
+      float2* dsts[2] = {bt, bo};
+      const size_t norbs[2] = {ntgt, nocc};
+      for (int i = 0; i < 2; ++i) {
+        if (i == 1 && srcs[1] == srcs[0] && nocc == ntgt) {
+          dsts[1] = bt;
+          break;
+        }
+        const size_t count4 = norbs[i] * sub->N / 2;
+        const unsigned blocks = (unsigned)std::min<size_t>((count4 + 255) / 256, 152 * 16);
+        to_pencil_blocks<<<blocks, 256, 0, st>>>((float4*)dsts[i], (const float4*)srcs[i], n, nbk / 2, norbs[i]);
+        count_launch();
+      }
+      a.own = dsts[0];
+      a.part = dsts[1];
+      a.blk = 1;
+      const cudaError_t le = cudaGetLastError();
+      if (le != cudaSuccess) return cuda_fail(le);
+    }
     bc.pa = a;
     bc.final_out = (float2*)vx_out[c];
     bc.n = sub->p.grid[0];

@@ -217,6 +217,18 @@ int pairconv_occupancy_mode(int variant) {
   return pairconv_occupancy_variant<n, MODE, 1>();
 }
 
+// Whether (n, mode, variant) runs the pencil-load kernel (which reads the pencil-blocked
+// orbital layout when PairArgs::blk is set) rather than the staged-partner one.
+template <int n>
+bool pencil_load_n(int mode, int variant) {
+  switch (mode) {
+    case MODE_APPLY: return staged_layout<n, MODE_APPLY>(variant) == 0;
+    case MODE_ENERGY: return staged_layout<n, MODE_ENERGY>(variant) == 0;
+    case MODE_DOT: return staged_layout<n, MODE_DOT>(variant) == 0;
+    default: return true;
+  }
+}
+
 template <int n>
 cudaError_t launch_pairconv_c64_n(int mode, const PairArgs& args, int blocks_per_sm, cudaStream_t stream) {
   switch (mode) {

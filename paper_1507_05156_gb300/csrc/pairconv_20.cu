@@ -7,4 +7,6 @@ cudaError_t launch_pairconv_c64_20(int mode, const PairArgs& args, int bps, cuda
 }
 
 int occupancy_pairconv_c64_20(int mode, int bps) { return pairconv_occupancy_n<20>(mode, bps); }
+
+bool pencil_load_pairconv_c64_20(int mode, int bps) { return pencil_load_n<20>(mode, bps); }
 }  // namespace hse

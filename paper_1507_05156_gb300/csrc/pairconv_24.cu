@@ -7,4 +7,6 @@ cudaError_t launch_pairconv_c64_24(int mode, const PairArgs& args, int bps, cuda
 }
 
 int occupancy_pairconv_c64_24(int mode, int bps) { return pairconv_occupancy_n<24>(mode, bps); }
+
+bool pencil_load_pairconv_c64_24(int mode, int bps) { return pencil_load_n<24>(mode, bps); }
 }  // namespace hse

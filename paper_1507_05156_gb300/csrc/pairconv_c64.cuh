@@ -48,6 +48,8 @@ __host__ __device__ constexpr KCfg kcfg(int n) {
 }
 
 __host__ __device__ constexpr int slots_for(int n) { return kcfg(n).slots; }
+// complex elements of one orbital in the pencil-blocked layout (OrbBlk below)
+__host__ __device__ constexpr size_t blocked_stride(int n) { return (size_t)((n * n + 31) / 32) * 32 * n; }
 
 __host__ __device__ constexpr int pow2_at_least(int x) {
   int p = 32;
@@ -123,6 +125,8 @@ struct PairArgs {
   size_t split_stride;  // elements between the per-split outputs (out: float2, partial: double)
   int* status;          // device status word for failed device-side waits (may be null)
   int inject;           // test hook: 1 = the staged kernel never issues its first partner copy
+  int blk;              // pencil-load kernel: own, part and part2 are in the pencil-blocked
+                        // layout (OrbBlk below) instead of [x][y][z]; out stays [x][y][z]
 };
 
 template <int n>
@@ -134,6 +138,40 @@ __device__ __forceinline__ void load_pencil_global(cpx<float> (&v)[n], const flo
     v[2 * e] = {w.x, w.y};
     v[2 * e + 1] = {w.z, w.w};
   }
+}
+
+// Pencil-blocked orbital layout, read by the pencil-load kernel.  A thread of that kernel reads
+// its own z-pencil (n complex, 8n bytes); in the natural layout the 32 lanes of a warp are 8n
+// bytes apart, so every 16-byte access of the warp touches 32 cache lines.  Blocked, the
+// z-pencils p = 32 b + l (l < 32) of block b store their elements (2e, 2e + 1) as 16-byte chunks
+// side by side: chunk (b, e, l) at float4 index (b n/2 + e) 32 + l.  A warp reading 32
+// consecutive pencils then reads 512 contiguous bytes per access.  NBK: complex per blocked
+// orbital (the last block is padded to 32 pencils).
+template <int n>
+struct OrbBlk {
+  static constexpr size_t NBK = blocked_stride(n);
+};
+
+// Z-pencil p (= x n + y) of one orbital, natural (blk = 0) or pencil-blocked (blk = 1).
+template <int n>
+__device__ __forceinline__ void load_pencil(cpx<float> (&v)[n], const float2* __restrict__ orb, int p, int blk) {
+  if (blk) {
+    const float4* b4 = reinterpret_cast<const float4*>(orb) + (size_t)(p >> 5) * (n / 2) * 32 + (p & 31);
+#pragma unroll
+    for (int e = 0; e < n / 2; ++e) {
+      const float4 w = __ldg(b4 + 32 * e);
+      v[2 * e] = {w.x, w.y};
+      v[2 * e + 1] = {w.z, w.w};
+    }
+  } else {
+    load_pencil_global<n>(v, orb + (size_t)p * n);
+  }
+}
+
+// complex elements between consecutive orbitals of an array in the given layout
+template <int n>
+__host__ __device__ __forceinline__ size_t orb_stride(int blk) {
+  return blk ? (size_t)OrbBlk<n>::NBK : (size_t)n * n * n;
 }
 
 // One pencil of the smem grid: n complex values at base + e * stride.  A stride of 1 with
@@ -288,17 +326,19 @@ __device__ __forceinline__ void cache_kernel_row(int t, uint32_t ttab, const flo
 }
 
 // Z forward for the thread's pencils: v = conj(a) * b, FFT along z, store.
+// a, b: orbitals in layout blk.
 template <int n, int PPT = 2, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void stage_z_forward(float2* g, int t, bool valid, const float2* __restrict__ a,
-                                                const float2* __restrict__ b) {
+                                                const float2* __restrict__ b, int blk) {
   using G = Geo<n>;
+  static_assert(G::ZFAST_Y == 1, "z-pencil p of the Z stage is (x, y) = (p / n, p % n)");
 #pragma unroll 1
   for (int ps = 0; ps < PPT; ++ps) {
     if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
     const Pencil<n> pc(t + ps * TS);
     cpx<float> v[n], w[n];
-    load_pencil_global<n>(w, a + pc.zg);
-    load_pencil_global<n>(v, b + pc.zg);
+    load_pencil<n>(w, a, t + ps * TS, blk);
+    load_pencil<n>(v, b, t + ps * TS, blk);
 #pragma unroll
     for (int e = 0; e < n; ++e) v[e] = {w[e].x * v[e].x + w[e].y * v[e].y, w[e].x * v[e].y - w[e].y * v[e].x};
     fft<n, -1, float>(v);
@@ -316,7 +356,7 @@ enum Epi : int {
 // Executed by every thread of the warp (TMEM accesses are warp-wide).
 template <int n, int EPI, int PPT = 2, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void stage_z_inverse(const float2* g, int t, const float2* __restrict__ wbase,
-                                                uint32_t trow0) {
+                                                uint32_t trow0, int blk) {
   using G = Geo<n>;
 #pragma unroll 1
   for (int ps = 0; ps < PPT; ++ps) {
@@ -329,7 +369,7 @@ __device__ __forceinline__ void stage_z_inverse(const float2* g, int t, const fl
     const uint32_t trow = trow0 + (uint32_t)(ps * G::ROW);
     TmemRow<G::ROW>::load(trow, acc);
     cpx<float> w[n];
-    load_pencil_global<n>(w, wbase + pc.zg);
+    load_pencil<n>(w, wbase, t + ps * TS, blk);
 #pragma unroll
     for (int e = 0; e < n; ++e) {
       float& ar = acc[2 * e];
@@ -395,7 +435,9 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
   const int kp_end = (int)(((long long)(split + 1) * args.nk_part) / args.nsplit);
   const bool active = valid && band < args.n_own;
   const int bandc = active ? band : 0;
-  const float2* own = args.own + ((size_t)k * args.n_own + bandc) * G::N;
+  const int blk = args.blk;
+  const size_t ostr = orb_stride<n>(blk);
+  const float2* own = args.own + ((size_t)k * args.n_own + bandc) * ostr;
 
   if (warp_on) {
     float z[G::ROW];
@@ -410,24 +452,24 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     const int qrow = (MODE == MODE_OCC) ? args.qidx[kp * args.nk_own + k] : args.qidx[k * args.nk_part + kp];
     if (warp_on) cache_kernel_row<n, PPT, false, n * n, TS>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
     for (int j = 0; j < args.n_part; ++j) {
-      const float2* part = args.part + ((size_t)kp * args.n_part + j) * G::N;
+      const float2* part = args.part + ((size_t)kp * args.n_part + j) * ostr;
       if constexpr (MODE != MODE_OCC) {
         const float f = (float)args.occ[kp * args.n_occ + j];
         if (f == 0.f) continue;  // uniform over the CTA
-        if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, part, own);          // conj(u_j) u_i
+        if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, part, own, blk);          // conj(u_j) u_i
         pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
-        if (warp_on) stage_z_inverse<n, EPI_MUL, PPT, TS>(g, t, part, trow0);      // acc += u_j phi
+        if (warp_on) stage_z_inverse<n, EPI_MUL, PPT, TS>(g, t, part, trow0, blk);      // acc += u_j phi
       } else {
         const float f = (float)args.occ[k * args.n_occ + bandc];
-        const float2* ybar = args.part2 + ((size_t)kp * args.n_part + j) * G::N;
+        const float2* ybar = args.part2 + ((size_t)kp * args.n_part + j) * ostr;
         // chain 1: rho = conj(u_j) u_i -> phi;  acc += conj(phi) ybar_i
-        if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, own, part);
+        if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, own, part, blk);
         pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
-        if (warp_on) stage_z_inverse<n, EPI_CONJPHI, PPT, TS>(g, t, ybar, trow0);
+        if (warp_on) stage_z_inverse<n, EPI_CONJPHI, PPT, TS>(g, t, ybar, trow0, blk);
         // chain 2: sigma = conj(u_j) ybar_i -> psibar;  acc += u_i conj(psibar)
-        if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, own, ybar);
+        if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, own, ybar, blk);
         pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
-        if (warp_on) stage_z_inverse<n, EPI_WCONJ, PPT, TS>(g, t, part, trow0);
+        if (warp_on) stage_z_inverse<n, EPI_WCONJ, PPT, TS>(g, t, part, trow0, blk);
       }
     }
   }
@@ -449,16 +491,15 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     }
   } else {
     // FP64 dot of the accumulator with u_i (ENERGY) or ybar_i (DOT), per owner.
-    const float2* lhs = (MODE == MODE_ENERGY) ? own : args.part2 + ((size_t)k * args.n_own + bandc) * G::N;
+    const float2* lhs = (MODE == MODE_ENERGY) ? own : args.part2 + ((size_t)k * args.n_own + bandc) * ostr;
     double d = 0.0;
 #pragma unroll 1
     for (int ps = 0; ps < PPT && warp_on; ++ps) {
       if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
-      const Pencil<n> pc(t + ps * TS);
       float acc[G::ROW];
       TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
       cpx<float> w[n];
-      load_pencil_global<n>(w, lhs + pc.zg);
+      load_pencil<n>(w, lhs, t + ps * TS, blk);
 #pragma unroll
       for (int e = 0; e < n; ++e) d += (double)w[e].x * (double)acc[2 * e] + (double)w[e].y * (double)acc[2 * e + 1];
     }

@@ -17,4 +17,12 @@ int occupancy_pairconv_c64_mid(int n, int mode, int bps) {
     default: return 0;
   }
 }
+
+bool pencil_load_pairconv_c64_mid(int n, int mode, int bps) {
+  switch (n) {
+    case 16: return pencil_load_n<16>(mode, bps);
+    case 18: return pencil_load_n<18>(mode, bps);
+    default: return true;
+  }
+}
 }  // namespace hse

@@ -23,4 +23,15 @@ int occupancy_pairconv_c64_small(int n, int mode, int bps) {
     default: return 0;
   }
 }
+
+bool pencil_load_pairconv_c64_small(int n, int mode, int bps) {
+  switch (n) {
+    case 4: return pencil_load_n<4>(mode, bps);
+    case 6: return pencil_load_n<6>(mode, bps);
+    case 8: return pencil_load_n<8>(mode, bps);
+    case 10: return pencil_load_n<10>(mode, bps);
+    case 12: return pencil_load_n<12>(mode, bps);
+    default: return true;
+  }
+}
 }  // namespace hse
