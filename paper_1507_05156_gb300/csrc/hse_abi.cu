@@ -58,7 +58,8 @@ int pairconv_c64_occupancy(int n, int mode, int bps) {
   return 0;
 }
 
-// For every cell with a k' split: final_out = sum of its split partials (ascending order).
+// For every cell with a k' split: final_out = sum of its split partials (ascending order,
+// compensated).
 __global__ void reduce_splits_batched(const BatchCell* __restrict__ cells, int ncells) {
   for (int c = 0; c < ncells; ++c) {
     const BatchCell& bc = cells[c];
@@ -67,15 +68,9 @@ __global__ void reduce_splits_batched(const BatchCell* __restrict__ cells, int n
     const float4* buf = reinterpret_cast<const float4*>(bc.pa.out);
     float4* out = reinterpret_cast<float4*>(bc.final_out);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count4; i += (size_t)gridDim.x * blockDim.x) {
-      float4 a = buf[i];
-      for (int sp = 1; sp < bc.pa.nsplit; ++sp) {
-        const float4 b = buf[(size_t)sp * count4 + i];
-        a.x += b.x;
-        a.y += b.y;
-        a.z += b.z;
-        a.w += b.w;
-      }
-      out[i] = a;
+      float4 a = buf[i], cs = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int sp = 1; sp < bc.pa.nsplit; ++sp) fold4(a, cs, buf[(size_t)sp * count4 + i], cs);
+      out[i] = make_float4(a.x + cs.x, a.y + cs.y, a.z + cs.z, a.w + cs.w);
     }
   }
 }
@@ -96,18 +91,13 @@ __global__ void to_pencil_blocks(float4* __restrict__ dst, const float4* __restr
   }
 }
 
-// out[i] = sum_s buf[s * count + i], splits in ascending order (deterministic)
+// out[i] = sum_s buf[s * count + i], splits in ascending order (deterministic), compensated
+// (TwoSum, as the k' groups inside a split)
 __global__ void reduce_splits(float4* __restrict__ out, const float4* __restrict__ buf, int nsplit, size_t count4) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count4; i += (size_t)gridDim.x * blockDim.x) {
-    float4 a = buf[i];
-    for (int sp = 1; sp < nsplit; ++sp) {
-      const float4 b = buf[(size_t)sp * count4 + i];
-      a.x += b.x;
-      a.y += b.y;
-      a.z += b.z;
-      a.w += b.w;
-    }
-    out[i] = a;
+    float4 a = buf[i], c = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int sp = 1; sp < nsplit; ++sp) fold4(a, c, buf[(size_t)sp * count4 + i], c);
+    out[i] = make_float4(a.x + c.x, a.y + c.y, a.z + c.z, a.w + c.w);
   }
 }
 
@@ -285,11 +275,12 @@ struct hse_plan_s {
   size_t work_pairs = 0;
   double2* vx64 = nullptr;   // [nk][max(n_occ, n_tgt)][N]
   bool blocked = true;       // pencil-load launches read pencil-blocked copies (HSE_PENCIL_BLOCKS=0: no)
-  int blocks_per_sm = 0;     // fused-kernel variant: 0 default, -1/-2/-3 staged-partner layouts, 1/2/3 pencil loads
+  int blocks_per_sm = 0;     // fused-kernel variant: 0 default, -1/-2 staged-partner layouts, 1/2/3 pencil loads
   int inject = 0;            // test hook (HSE_INJECT_SKIP_FILL=1 at plan creation)
   int nsplit[3] = {1, 1, 1};  // k'-loop splits of the fused kernel per OwnerRole
   float2* split_buf = nullptr;  // [nsplit][nk_own][n_own][N] partial outputs when nsplit > 1
   size_t split_buf_elems = 0;
+  float2* comp_buf = nullptr;   // [nsplit][nk_own][n_own][N] compensation sums (APPLY / OCC)
   // pencil-blocked copies of the orbital arrays a pencil-load launch reads (allocated on first
   // use, grown when a larger call comes)
   float2* blk_buf = nullptr;
@@ -314,6 +305,7 @@ struct hse_plan_s {
   std::vector<BatchCell> h_cells;       // launch arguments, pointers refreshed per call
   std::vector<float2*> cell_split;      // per cell [kMaxBatchSplit][nk][n_tgt][N]
   std::vector<float2*> cell_blk;        // pencil-load cells: blocked u_tgt then u_occ (else null)
+  std::vector<float2*> cell_comp;       // per cell [min(kMaxBatchSplit, nk)][nk][n_tgt][N] compensation sums
   BatchCell* d_cells = nullptr;
   BatchItem* d_items = nullptr;         // staged-partner items, then pencil-load items
   int* d_counter = nullptr;             // [2]: one per list
@@ -419,6 +411,7 @@ int hse_plan_destroy(hse_plan plan) {
   for (hse_plan c : plan->cells) hse_plan_destroy(c);
   for (float2* b : plan->cell_split) cudaFree(b);
   for (float2* b : plan->cell_blk) cudaFree(b);
+  for (float2* b : plan->cell_comp) cudaFree(b);
   cudaFree(plan->d_cells);
   cudaFree(plan->d_items);
   cudaFree(plan->d_counter);
@@ -436,6 +429,7 @@ int hse_plan_destroy(hse_plan plan) {
   cudaFree(plan->work);
   cudaFree(plan->vx64);
   cudaFree(plan->split_buf);
+  cudaFree(plan->comp_buf);
   cudaFree(plan->blk_buf);
   cudaFree(plan->d_kocc);
   cudaFree(plan->d_kinv);
@@ -479,7 +473,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   if (const char* env = std::getenv("HSE_PENCIL_BLOCKS")) plan->blocked = std::atoi(env) != 0;
   if (const char* env = std::getenv("HSE_BLOCKS_PER_SM")) {
     const int v = std::atoi(env);
-    plan->blocks_per_sm = (v < -3 || v > 3) ? 0 : v;
+    plan->blocks_per_sm = (v < -2 || v > 3) ? 0 : v;
   }
   const int n1 = p->grid[0], n2 = p->grid[1], n3 = p->grid[2];
   plan->N = n1 * n2 * n3;
@@ -546,7 +540,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
     const int k_own[3] = {nk, nk, nkq};
     const int k_part[3] = {nkq, nkq, nk};
     const int b_part[3] = {p->n_occ, p->n_occ, p->n_tgt};
-    size_t buf = 0;
+    size_t buf = 0, comp = 0;
     for (int o = 0; o < 3; ++o) {
       const int T = slots_for(n1);
       const long long items = (long long)k_own[o] * ((owners[o] + T - 1) / T);
@@ -572,11 +566,13 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
       if (need * sizeof(float2) > ((size_t)4 << 30)) best = 1;  // keep split buffers modest
       plan->nsplit[o] = best;
       if (best > 1) buf = std::max(buf, need);
+      if (o != ROLE_ENERGY) comp = std::max(comp, (size_t)best * k_own[o] * owners[o] * N);
     }
     if (buf) {
       HSE_TRY(cudaMalloc(&plan->split_buf, buf * sizeof(float2)));
       plan->split_buf_elems = buf;
     }
+    HSE_TRY(cudaMalloc(&plan->comp_buf, comp * sizeof(float2)));
   }
   {
     const size_t np = std::max((size_t)plan->nsplit[ROLE_TGT] * nk * p->n_tgt,
@@ -727,6 +723,7 @@ int run_pairconv(hse_plan plan, int mode, PairArgs a, int n_own, cudaStream_t st
   a.nsplit = plan->nsplit[role_of(mode)];
   const size_t count = (size_t)a.nk_own * n_own * plan->N;
   float2* final_out = a.out;
+  a.comp = plan->comp_buf;
   if (mode == MODE_ENERGY || mode == MODE_DOT) {
     a.split_stride = (size_t)a.nk_own * n_own;  // doubles between the splits' partials
   } else {
@@ -1230,6 +1227,10 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
     float2* buf = nullptr;
     if (q.nk > 1) e = cudaMalloc(&buf, (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * q.n_tgt * sub->N * sizeof(float2));
     plan->cell_split.push_back(buf);
+    float2* comp = nullptr;
+    if (e == cudaSuccess)
+      e = cudaMalloc(&comp, (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * q.n_tgt * sub->N * sizeof(float2));
+    plan->cell_comp.push_back(comp);
     float2* blk = nullptr;
     int sp = 0, br = 0;
     if (e == cudaSuccess && !batched_stage_geometry(q.grid[0], &sp, &br))
@@ -1287,6 +1288,7 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
     a.nsplit = bc.pa.nsplit > 0 ? bc.pa.nsplit : 1;
     a.split_stride = (size_t)sub->p.nk * a.n_own * sub->N;
     a.out = a.nsplit > 1 ? plan->cell_split[c] : (float2*)vx_out[c];
+    a.comp = plan->cell_comp[c];
     if (plan->cell_blk[c]) {
       // the pencil-load pipeline reads pencil-blocked copies (refreshed on every call, before
       // the graph)

@@ -167,21 +167,18 @@ constexpr bool tma_fits() {
 
 // Kernel variant: 0 the default (the staged-partner kernel with its default layout where it
 // exists for (n, mode), else the pencil-load kernel at the occupancy the size allows);
-// -1 / -2 / -3 the staged-partner kernel with LayoutSeq / LayoutOne / LayoutSplit; 1 or 2 the
+// -1 / -2 the staged-partner kernel with LayoutSeq / LayoutOne; 1 or 2 the
 // pencil-load kernel with that occupancy; 3 the ragged pencil-load kernel (pencil_ragged_fits;
 // the default of the pencil-load kernel where it exists: 24^3 99.6 -> 95.6 ms on the 4x4x4 k,
 // 16-band cell).  A variant that does not exist for the size falls back to the default.
 template <int n, int MODE>
 constexpr int staged_layout(int variant) {
   if (variant > 0) return 0;
-  const bool seq = tma_fits<n, MODE, LayoutSeq>(), one = tma_fits<n, MODE, LayoutOne>(),
-             split = tma_fits<n, MODE, LayoutSplit>();
+  const bool seq = tma_fits<n, MODE, LayoutSeq>(), one = tma_fits<n, MODE, LayoutOne>();
   if (variant == -1 && seq) return -1;
   if (variant == -2 && one) return -2;
-  if (variant == -3 && split) return -3;
-  // default: one pencil per thread where it fits, else two (the lane-split layout measured no
-  // faster at 20^3 than one pencil per thread with the bank-spread X order: 34.7 ms each)
-  return one ? -2 : (seq ? -1 : (split ? -3 : 0));
+  // default: one pencil per thread where it fits, else two
+  return one ? -2 : (seq ? -1 : 0);
 }
 
 template <int n, int MODE>
@@ -192,9 +189,6 @@ cudaError_t launch_pairconv_mode(const PairArgs& args, int variant, cudaStream_t
       break;
     case -2:
       if constexpr (tma_fits<n, MODE, LayoutOne>()) return launch_pairconv_tma<n, MODE, LayoutOne>(args, stream);
-      break;
-    case -3:
-      if constexpr (tma_fits<n, MODE, LayoutSplit>()) return launch_pairconv_tma<n, MODE, LayoutSplit>(args, stream);
       break;
     default: break;
   }

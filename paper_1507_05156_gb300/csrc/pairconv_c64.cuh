@@ -127,7 +127,66 @@ struct PairArgs {
   int inject;           // test hook: 1 = the staged kernel never issues its first partner copy
   int blk;              // pencil-load kernel: own, part and part2 are in the pencil-blocked
                         // layout (OrbBlk below) instead of [x][y][z]; out stays [x][y][z]
+  float2* comp;         // APPLY / OCC: compensation sums, the shape of out (split_stride apart)
 };
+
+// ---------------------------------------------------------------------------------------
+// Compensated accumulation over k' (Sec. II C, Eq. "Fock": V_x u sums the pair terms over
+// every k' and every occupied band).  The TMEM accumulator of a pencil holds the sum over the
+// bands of one k' (a group, in FP32).  When the group ends it is added to the pencil's running
+// sum s with Knuth's TwoSum, whose exact rounding error is added to a second running sum c;
+// the pencil's result is s + c.  s lives in the output (or the work item's split partial), c in
+// PairArgs::comp at the same offset; only the thread that owns the pencil touches them.  The
+// dot epilogues (energy, d/d omega) instead add each group's FP32 pencil dot to an FP64 sum.
+// ---------------------------------------------------------------------------------------
+
+// a + b = s + err exactly, s = fl(a + b) (TwoSum; no fast-math reassociation in this build)
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float s = a + b;
+  const float bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+  return s;
+}
+
+__device__ __forceinline__ void fold4(float4& sv, float4& cv, const float4 s0, const float4 c0) {
+  float er;
+  sv.x = two_sum(s0.x, sv.x, er);
+  cv.x = c0.x + er;
+  sv.y = two_sum(s0.y, sv.y, er);
+  cv.y = c0.y + er;
+  sv.z = two_sum(s0.z, sv.z, er);
+  cv.z = c0.z + er;
+  sv.w = two_sum(s0.w, sv.w, er);
+  cv.w = c0.w + er;
+}
+
+// Folds one group row g (a z-pencil, 2n floats) into the running sums at s4 / c4 (n/2 float4
+// each, global).  first: s = g, c = 0 (nothing is read).  last: the final s + c is written to
+// s4 and c4 is left alone.
+template <int n>
+__device__ __forceinline__ void fold_group(const float* g, float4* s4, float4* c4, bool first, bool last) {
+#pragma unroll
+  for (int e = 0; e < n / 2; ++e) {
+    float4 sv = make_float4(g[4 * e], g[4 * e + 1], g[4 * e + 2], g[4 * e + 3]);
+    float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!first) fold4(sv, cv, s4[e], c4[e]);
+    if (last) {
+      s4[e] = make_float4(sv.x + cv.x, sv.y + cv.y, sv.z + cv.z, sv.w + cv.w);
+    } else {
+      s4[e] = sv;
+      c4[e] = cv;
+    }
+  }
+}
+
+// Re <w | g> over one pencil (n complex values; g interleaved), FP32
+template <int n>
+__device__ __forceinline__ float pencil_dot(const cpx<float> (&w)[n], const float* g) {
+  float d = 0.f;
+#pragma unroll
+  for (int e = 0; e < n; ++e) d = fmaf(w[e].x, g[2 * e], fmaf(w[e].y, g[2 * e + 1], d));
+  return d;
+}
 
 template <int n>
 __device__ __forceinline__ void load_pencil_global(cpx<float> (&v)[n], const float2* __restrict__ p) {
@@ -447,6 +506,40 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     for (int ps = 0; ps < PPT; ++ps) TmemRow<G::ROW>::store(trow0 + (uint32_t)(ps * G::ROW), z);
   }
 
+  // compensated accumulation over the k' groups (one group per k'): APPLY / OCC keep the
+  // running sums in the item's output region ([x][y][z]) and in args.comp; ENERGY / DOT add
+  // group dots to dsum (FP64)
+  const size_t oofs = split * args.split_stride + ((size_t)k * args.n_own + bandc) * G::N;
+  const float2* lhs = (MODE == MODE_DOT) ? args.part2 + ((size_t)k * args.n_own + bandc) * ostr : own;
+  double dsum = 0.0;
+  auto fold = [&](bool first, bool last) {
+    if (!warp_on) return;
+#pragma unroll 1
+    for (int ps = 0; ps < PPT; ++ps) {
+      if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
+      const uint32_t trow = trow0 + (uint32_t)(ps * G::ROW);
+      float acc[G::ROW];
+      TmemRow<G::ROW>::load(trow, acc);
+      if constexpr (MODE == MODE_APPLY || MODE == MODE_OCC) {
+        if (active) {
+          const size_t o = oofs + (size_t)(t + ps * TS) * n;
+          fold_group<n>(acc, reinterpret_cast<float4*>(args.out + o), reinterpret_cast<float4*>(args.comp + o),
+                        first, last);
+        }
+      } else {
+        cpx<float> w[n];
+        load_pencil<n>(w, lhs, t + ps * TS, blk);
+        dsum += (double)pencil_dot<n>(w, acc);
+      }
+      if (!last) {
+#pragma unroll
+        for (int e = 0; e < G::ROW; ++e) acc[e] = 0.f;
+        TmemRow<G::ROW>::store(trow, acc);
+      }
+    }
+  };
+  if (kp_begin == kp_end) fold(true, true);  // an empty k' range: zeros
+
   for (int kp = kp_begin; kp < kp_end; ++kp) {
     // q = k_i - k_j: APPLY-like modes own i (at k) and pair with j at kp; OCC owns j (at k)
     const int qrow = (MODE == MODE_OCC) ? args.qidx[kp * args.nk_own + k] : args.qidx[k * args.nk_part + kp];
@@ -472,37 +565,12 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
         if (warp_on) stage_z_inverse<n, EPI_WCONJ, PPT, TS>(g, t, part, trow0, blk);
       }
     }
+    fold(kp == kp_begin, kp == kp_end - 1);
   }
 
-  if constexpr (MODE == MODE_APPLY || MODE == MODE_OCC) {
-    if (!warp_on) return;
-    float2* obase = args.out + split * args.split_stride + ((size_t)k * args.n_own + bandc) * G::N;
-#pragma unroll 1
-    for (int ps = 0; ps < PPT; ++ps) {
-      if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
-      const Pencil<n> pc(t + ps * TS);
-      float acc[G::ROW];
-      TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
-      if (active) {
-        float4* o = reinterpret_cast<float4*>(obase + pc.zg);
-#pragma unroll
-        for (int e = 0; e < n / 2; ++e) o[e] = make_float4(acc[4 * e], acc[4 * e + 1], acc[4 * e + 2], acc[4 * e + 3]);
-      }
-    }
-  } else {
-    // FP64 dot of the accumulator with u_i (ENERGY) or ybar_i (DOT), per owner.
-    const float2* lhs = (MODE == MODE_ENERGY) ? own : args.part2 + ((size_t)k * args.n_own + bandc) * ostr;
-    double d = 0.0;
-#pragma unroll 1
-    for (int ps = 0; ps < PPT && warp_on; ++ps) {
-      if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
-      float acc[G::ROW];
-      TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
-      cpx<float> w[n];
-      load_pencil<n>(w, lhs, t + ps * TS, blk);
-#pragma unroll
-      for (int e = 0; e < n; ++e) d += (double)w[e].x * (double)acc[2 * e] + (double)w[e].y * (double)acc[2 * e + 1];
-    }
+  if constexpr (MODE == MODE_ENERGY || MODE == MODE_DOT) {
+    // FP64 sum of the group dots with u_i (ENERGY) or ybar_i (DOT), per owner
+    const double d = dsum;
     __syncthreads();  // the grid buffers are free now; reuse them for the per-thread partials
     double* red = reinterpret_cast<double*>(smem4);
     red[tid] = (valid && warp_on) ? d : 0.0;

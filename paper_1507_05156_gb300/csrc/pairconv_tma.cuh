@@ -119,14 +119,7 @@ __device__ __forceinline__ void stage_z_inverse_staged(const float2* g, int t, c
 //                part (18^3: 3 instead of 4) and gives each scheduler more warps to hide
 //                shared-memory latency.  Its X stage takes the pencils in the bank-spread
 //                order of x_pencil (no bank conflicts where the pitch P differs from n).
-//   LayoutSplit: one pencil per thread for the first R = 128 floor(n^2 / 128) pencils (whole
-//                warps, the same count on every scheduler), plus four warps, one per scheduler,
-//                that transform the L = n^2 - R pencils left over with their DFT split over
-//                lanes (below), L / 4 each.  For 20^3 (R = 384, L = 16) this replaces a thirteenth
-//                warp, which gave one scheduler four full pencil passes per stage against three
-//                on the others, by warps whose pass costs a fraction of one and runs beside the
-//                regular ones.
-// TMEM columns of a warp: [acc (PPT pencils) | kernel rows (PPT) | owner u_i (PPT) | extra].
+// TMEM columns of a warp: [acc (PPT pencils) | kernel rows (PPT) | owner u_i (PPT)].
 // ---------------------------------------------------------------------------------------
 
 // XP: with one pencil per thread, the X-stage pencils go to threads in the bank-spread order
@@ -169,297 +162,12 @@ struct LayoutLin {
   // 1.25 ms; warp-local 16^3 14.40 -> 14.23 ms, 8^3 1.87 -> 1.84 ms.)
   static constexpr bool GROUPED = 32 % n == 0 && (G::T == 1 || TS % 32 == 0);
   static __device__ __forceinline__ void group_sync(int) { __syncwarp(); }
-  // pencils beyond the regular ones (LayoutSplit): none here
-  static __device__ __forceinline__ bool regular(int) { return true; }
-  static __device__ __forceinline__ void extra_init(int, const float2*, uint32_t) {}
-  static __device__ __forceinline__ void extra_store(int, float2*, uint32_t, bool) {}
-  static __device__ __forceinline__ double extra_dot(int, const float2*, uint32_t) { return 0.0; }
 };
 
 template <int n>
 struct LayoutSeq : LayoutLin<n, 2> {};
 template <int n>
 struct LayoutOne : LayoutLin<n, 1> {};
-
-// --- DFT of one pencil split over lanes (prime-factor form, Sec. "Good-Thomas") -------------
-// n = N1 N2 with gcd(N1, N2) = 1.  With posA(a, b) = (N2 a + N1 b) mod n and
-// crt(k1, k2) the k with k = k1 (mod N1), k = k2 (mod N2), the DFT X[crt(k1, k2)] =
-// sum_b w_N2^(b k2) sum_a w_N1^(a k1) x[posA(a, b)] splits into
-//   pass A: for each b (one lane), the N1-point DFT over a, written back to posA(k1, b);
-//   pass B: for each k1 (one lane), the N2-point DFT over b of the values at posA(k1, b),
-//           written to crt(k1, k2).
-// When N2 = 1 (mod N1) the positions a lane reads in pass B are the ones it writes, so every
-// pass works in place on a set of positions no other lane of the pass touches.
-__host__ __device__ constexpr int inv_mod_c(int a, int m) {
-  int x = 1;
-  while ((a * x) % m != 1 % m) ++x;
-  return x;
-}
-
-template <int n>
-struct SplitGeo {
-  static constexpr int N1 = pfa_n1(n);
-  static constexpr int N2 = N1 > 0 ? n / N1 : 1;
-  static constexpr int NN = n * n;
-  static constexpr int R = NN / 128 * 128;                 // regular pencils (whole warps)
-  static constexpr int L = NN - R;                         // split pencils
-  static constexpr int PER = L / 4;                        // split pencils per scheduler
-  static constexpr int E1 = N1 > 1 ? (N2 * inv_mod_c(N2 % N1, N1)) % n : 0;
-  static constexpr int E2 = N1 > 1 ? (N1 * inv_mod_c(N1 % N2, N2)) % n : 0;
-  static constexpr bool OK = N1 > 1 && R > 0 && L > 0 && L % 4 == 0 && PER * N2 <= 32 && N2 % N1 == 1 &&
-                             Geo<n>::T == 1 && Geo<n>::ZFAST_Y == 1;
-  static constexpr int HOST0 = R / 32;                     // warps HOST0 .. HOST0 + 3 take them
-  // extra TMEM columns of a hosting lane: owner u_i at its pass-A positions (2 N1 floats),
-  // accumulator there (2 N1), kernel values at its pass-B positions (N2, padded)
-  static constexpr int C_OWN = 0, C_ACC = 2 * N1, C_KER = 4 * N1;
-  static constexpr int KW = N2 <= 4 ? 4 : (N2 <= 6 ? 6 : 8);
-  static constexpr int COLS = (4 * N1 + KW + 7) / 8 * 8;
-  static __host__ __device__ __forceinline__ int posA(int a, int b) {  // a, b < n: one wrap at most
-    const int v = N2 * a + N1 * b;
-    return v >= n ? v - n : v;
-  }
-  static __host__ __device__ __forceinline__ int crt(int k1e1, int k2) {  // k1e1 = (k1 E1) mod n
-    const int v = k1e1 + (k2 * E2) % n;
-    return v >= n ? v - n : v;
-  }
-};
-
-template <int n>
-struct LayoutSplit {
-  using G = Geo<n>;
-  using SG = SplitGeo<n>;
-  using S = StageGeo<n>;
-  static constexpr int PPT = 1;
-  static constexpr int TS = SG::OK ? SG::R + 128 : G::NN;
-  static constexpr int THREADS = TS, WARPS = TS / 32;
-  static constexpr int GRID_CPX = G::GRID_CPX;
-  static constexpr bool OK = SG::OK && THREADS <= 1024;
-  static constexpr int TAB = G::ROW;
-  static constexpr int OWN = TAB + n;
-  static constexpr int EXTRA = OWN + G::ROW;
-  static constexpr int COLS_PER_WARP = EXTRA + SG::COLS;
-  // the regular pencils 0 .. R-1 (pencil = thread in every stage: with the split pencils
-  // beside them, the bank-spread X order measured slower, 35.3 against 34.7 ms at 20^3)
-  using Reg = LayoutLin<n, 1, false>;
-  static __device__ __forceinline__ bool regular(int t) { return t < SG::R; }
-  // block barriers only
-  static constexpr bool GROUPED = false;
-  static __device__ __forceinline__ void group_sync(int) {}
-
-  // role of this lane in the hosting warp: s = scheduler, A: (pencil, b), B: (pencil, k1)
-  struct Roles {
-    bool host, a_on, b_on;
-    int pa, b, pb, k1, k1e1;
-    __device__ __forceinline__ explicit Roles(int t) {
-      const int warp = t >> 5, lane = t & 31;
-      host = warp >= SG::HOST0;
-      const int first = SG::R + (warp - SG::HOST0) * SG::PER;
-      a_on = host && lane < SG::PER * SG::N2;
-      b_on = host && lane < SG::PER * SG::N1;
-      // lanes without a role keep an in-range pencil (its index also selects table entries)
-      pa = a_on ? first + lane / SG::N2 : SG::R;
-      b = lane % SG::N2;
-      pb = b_on ? first + lane / SG::N1 : SG::R;
-      k1 = lane % SG::N1;
-      k1e1 = (k1 * SG::E1) % n;
-    }
-  };
-
-  template <int DIR>
-  static __device__ __forceinline__ void pass_a(float2* g, int base, int stride, int b) {
-    cpx<float> v[SG::N1];
-#pragma unroll
-    for (int a = 0; a < SG::N1; ++a) {
-      const float2 w = g[base + SG::posA(a, b) * stride];
-      v[a] = {w.x, w.y};
-    }
-    fft<SG::N1, DIR, float>(v);
-#pragma unroll
-    for (int a = 0; a < SG::N1; ++a) g[base + SG::posA(a, b) * stride] = make_float2(v[a].x, v[a].y);
-  }
-  template <int DIR>
-  static __device__ __forceinline__ void pass_b(float2* g, int base, int stride, int k1, int k1e1) {
-    cpx<float> v[SG::N2];
-#pragma unroll
-    for (int b = 0; b < SG::N2; ++b) {
-      const float2 w = g[base + SG::posA(k1, b) * stride];
-      v[b] = {w.x, w.y};
-    }
-    fft<SG::N2, DIR, float>(v);
-#pragma unroll
-    for (int k2 = 0; k2 < SG::N2; ++k2) g[base + SG::crt(k1e1, k2) * stride] = make_float2(v[k2].x, v[k2].y);
-  }
-
-  static __device__ __forceinline__ int zg(int t, int ps) { return Reg::zg(t, ps); }
-
-  static __device__ __forceinline__ void z_forward(float2* g, int t, bool valid, const float2* stg, uint32_t trow0) {
-    const Roles r(t);
-    if (r.host) {  // warp-uniform
-      float uo[2 * SG::N1];
-      TmemRow<2 * SG::N1>::load(trow0 + (uint32_t)(EXTRA + SG::C_OWN), uo);
-      if (r.a_on) {
-        const Pencil<n> pc(r.pa);
-        const float2* srow = stg + (pc.zg / n) * S::SP;
-        cpx<float> v[SG::N1];
-#pragma unroll
-        for (int a = 0; a < SG::N1; ++a) {
-          const float2 w = srow[SG::posA(a, r.b)];
-          v[a] = {w.x * uo[2 * a] + w.y * uo[2 * a + 1], w.x * uo[2 * a + 1] - w.y * uo[2 * a]};
-        }
-        fft<SG::N1, -1, float>(v);
-#pragma unroll
-        for (int a = 0; a < SG::N1; ++a) g[pc.zs + SG::posA(a, r.b)] = make_float2(v[a].x, v[a].y);
-      }
-      __syncwarp();
-      if (r.b_on) pass_b<-1>(g, Pencil<n>(r.pb).zs, 1, r.k1, r.k1e1);
-    }
-    if (regular(t)) Reg::z_forward(g, t, valid, stg, trow0);
-  }
-
-  template <int DIR>
-  static __device__ __forceinline__ void y(float2* g, int t, bool valid) {
-    const Roles r(t);
-    if (r.host) {
-      if (r.a_on) pass_a<DIR>(g, Pencil<n>(r.pa).ys, G::P, r.b);
-      __syncwarp();
-      if (r.b_on) pass_b<DIR>(g, Pencil<n>(r.pb).ys, G::P, r.k1, r.k1e1);
-    }
-    if (regular(t)) Reg::template y<DIR>(g, t, valid);
-  }
-
-  static __device__ __forceinline__ void x(float2* g, int t, bool valid, uint32_t trow0, float f) {
-    const Roles r(t);
-    if (r.host) {
-      float kv[SG::KW];
-      TmemRow<SG::KW>::load(trow0 + (uint32_t)(EXTRA + SG::C_KER), kv);
-      const int xa = Pencil<n>(r.pa).xs;
-      if (r.a_on) pass_a<-1>(g, xa, G::Q, r.b);
-      __syncwarp();
-      if (r.b_on) {
-        const int base = Pencil<n>(r.pb).xs;
-        cpx<float> v[SG::N2];
-#pragma unroll
-        for (int b = 0; b < SG::N2; ++b) {
-          const float2 w = g[base + SG::posA(r.k1, b) * G::Q];
-          v[b] = {w.x, w.y};
-        }
-        fft<SG::N2, -1, float>(v);  // v[k2] = X[crt(k1, k2)]
-#pragma unroll
-        for (int k2 = 0; k2 < SG::N2; ++k2) {
-          const float w = kv[k2] * f;
-          v[k2].x *= w;
-          v[k2].y *= w;
-        }
-        fft<SG::N2, +1, float>(v);  // back to b, still at fixed k1
-#pragma unroll
-        for (int b = 0; b < SG::N2; ++b) g[base + SG::posA(r.k1, b) * G::Q] = make_float2(v[b].x, v[b].y);
-      }
-      __syncwarp();
-      if (r.a_on) pass_a<+1>(g, xa, G::Q, r.b);
-    }
-    if (regular(t)) Reg::x(g, t, valid, trow0, f);
-  }
-
-  static __device__ __forceinline__ void z_inverse(const float2* g_, int t, const float2* stg, uint32_t trow0) {
-    const Roles r(t);
-    if (r.host) {
-      float2* g = const_cast<float2*>(g_);  // the split pencils pass through the grid in place
-      if (r.b_on) {
-        // natural order -> (k1, b): inverse N2-point DFTs first, in place on the lane's set
-        const int base = Pencil<n>(r.pb).zs;
-        cpx<float> v[SG::N2];
-#pragma unroll
-        for (int k2 = 0; k2 < SG::N2; ++k2) {
-          const float2 w = g[base + SG::crt(r.k1e1, k2)];
-          v[k2] = {w.x, w.y};
-        }
-        fft<SG::N2, +1, float>(v);
-#pragma unroll
-        for (int b = 0; b < SG::N2; ++b) g[base + SG::posA(r.k1, b)] = make_float2(v[b].x, v[b].y);
-      }
-      __syncwarp();
-      float acc[2 * SG::N1];
-      const uint32_t tacc = trow0 + (uint32_t)(EXTRA + SG::C_ACC);
-      TmemRow<2 * SG::N1>::load(tacc, acc);
-      if (r.a_on) {
-        const Pencil<n> pc(r.pa);
-        cpx<float> v[SG::N1];
-#pragma unroll
-        for (int a = 0; a < SG::N1; ++a) {
-          const float2 w = g[pc.zs + SG::posA(a, r.b)];
-          v[a] = {w.x, w.y};
-        }
-        fft<SG::N1, +1, float>(v);  // v[a] = phi at posA(a, b)
-        const float2* srow = stg + (pc.zg / n) * S::SP;
-#pragma unroll
-        for (int a = 0; a < SG::N1; ++a) {
-          const float2 w = srow[SG::posA(a, r.b)];
-          acc[2 * a] = fmaf(w.x, v[a].x, fmaf(-w.y, v[a].y, acc[2 * a]));
-          acc[2 * a + 1] = fmaf(w.x, v[a].y, fmaf(w.y, v[a].x, acc[2 * a + 1]));
-        }
-      }
-      TmemRow<2 * SG::N1>::store(tacc, acc);
-      __syncwarp();  // the next pair's Z forward rewrites these positions from other lanes
-    }
-    if (regular(t)) Reg::z_inverse(g_, t, stg, trow0);
-  }
-
-  static __device__ __forceinline__ void cache_row(int t, uint32_t trow0, const float* __restrict__ vrow, float scale) {
-    const Roles r(t);
-    if (r.host) {
-      float kv[SG::KW];
-#pragma unroll
-      for (int k2 = 0; k2 < SG::KW; ++k2)
-        kv[k2] = (r.b_on && k2 < SG::N2) ? __ldg(vrow + SG::crt(r.k1e1, k2) * G::NN + r.pb) * scale
-                                         : 0.f;
-      TmemRow<SG::KW>::store(trow0 + (uint32_t)(EXTRA + SG::C_KER), kv);
-    }
-    if (regular(t)) Reg::cache_row(t, trow0, vrow, scale);
-  }
-
-  static __device__ __forceinline__ void extra_init(int t, const float2* own, uint32_t trow0) {
-    const Roles r(t);
-    if (!r.host) return;
-    float w[2 * SG::N1], z[2 * SG::N1];
-    const int zg0 = Pencil<n>(r.pa).zg;
-#pragma unroll
-    for (int a = 0; a < SG::N1; ++a) {
-      const float2 u = r.a_on ? __ldg(own + zg0 + SG::posA(a, r.b)) : make_float2(0.f, 0.f);
-      w[2 * a] = u.x;
-      w[2 * a + 1] = u.y;
-      z[2 * a] = z[2 * a + 1] = 0.f;
-    }
-    TmemRow<2 * SG::N1>::store(trow0 + (uint32_t)(EXTRA + SG::C_OWN), w);
-    TmemRow<2 * SG::N1>::store(trow0 + (uint32_t)(EXTRA + SG::C_ACC), z);
-  }
-  static __device__ __forceinline__ void extra_store(int t, float2* obase, uint32_t trow0, bool active) {
-    const Roles r(t);
-    if (!r.host) return;
-    float acc[2 * SG::N1];
-    TmemRow<2 * SG::N1>::load(trow0 + (uint32_t)(EXTRA + SG::C_ACC), acc);
-    if (active && r.a_on) {
-      const int zg0 = Pencil<n>(r.pa).zg;
-#pragma unroll
-      for (int a = 0; a < SG::N1; ++a) obase[zg0 + SG::posA(a, r.b)] = make_float2(acc[2 * a], acc[2 * a + 1]);
-    }
-  }
-  static __device__ __forceinline__ double extra_dot(int t, const float2* lhs, uint32_t trow0) {
-    const Roles r(t);
-    if (!r.host) return 0.0;
-    float acc[2 * SG::N1];
-    TmemRow<2 * SG::N1>::load(trow0 + (uint32_t)(EXTRA + SG::C_ACC), acc);
-    double d = 0.0;
-    if (r.a_on) {
-      const int zg0 = Pencil<n>(r.pa).zg;
-#pragma unroll
-      for (int a = 0; a < SG::N1; ++a) {
-        const float2 w = __ldg(lhs + zg0 + SG::posA(a, r.b));
-        d += (double)w.x * (double)acc[2 * a] + (double)w.y * (double)acc[2 * a + 1];
-      }
-    }
-    return d;
-  }
-};
 
 // Occupations of one work item's partners, cached in shared memory when they fit.
 constexpr int kOccCache = 1024;
@@ -552,7 +260,7 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
   }
 
   // owner orbital into TMEM, accumulators to zero
-  const bool reg = on && Lay::regular(t);  // warp-uniform
+  const bool reg = on;  // warp-uniform
 #pragma unroll 1
   for (int ps = 0; ps < (reg ? Lay::PPT : 0); ++ps) {
     cpx<float> w[n];
@@ -568,7 +276,45 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
     for (int e = 0; e < G::ROW; ++e) r[e] = 0.f;
     TmemRow<G::ROW>::store(trow0 + (uint32_t)(ps * G::ROW), r);
   }
-  if (on) Lay::extra_init(t, own, trow0);
+
+  // compensated accumulation over the k' groups of the item: APPLY keeps the running sums in
+  // its output region (s) and in args.comp (c); ENERGY / DOT add group dots to dsum (FP64)
+  const size_t oofs = split * args.split_stride + ((size_t)k * args.n_own + bandc) * G::N;
+  const float2* lhs = (MODE == MODE_DOT) ? args.part2 + ((size_t)k * args.n_own + bandc) * G::N : own;
+  double dsum = 0.0;
+  int folds = 0;
+  auto fold = [&](bool last) {
+#pragma unroll 1
+    for (int ps = 0; ps < (reg ? Lay::PPT : 0); ++ps) {
+      const uint32_t trow = trow0 + (uint32_t)(ps * G::ROW);
+      float acc[G::ROW];
+      TmemRow<G::ROW>::load(trow, acc);
+      if constexpr (MODE == MODE_APPLY) {
+        if (active) {
+          const size_t o = oofs + Lay::zg(t, ps);
+          fold_group<n>(acc, reinterpret_cast<float4*>(args.out + o), reinterpret_cast<float4*>(args.comp + o),
+                        folds == 0, last);
+        }
+      } else {
+        cpx<float> w[n];
+        if constexpr (MODE == MODE_ENERGY) {
+          float r[G::ROW];
+          TmemRow<G::ROW>::load(town + (uint32_t)(ps * G::ROW), r);
+#pragma unroll
+          for (int e = 0; e < n; ++e) w[e] = {r[2 * e], r[2 * e + 1]};
+        } else {
+          load_pencil_global<n>(w, lhs + Lay::zg(t, ps));
+        }
+        dsum += (double)pencil_dot<n>(w, acc);
+      }
+      if (!last) {
+#pragma unroll
+        for (int e = 0; e < G::ROW; ++e) acc[e] = 0.f;
+        TmemRow<G::ROW>::store(trow, acc);
+      }
+    }
+    ++folds;
+  };
 
   int buf = 0;
   int cur_kp = -1;
@@ -576,6 +322,7 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
     const int kp = kp_begin + q / args.n_part;
     const float f = item_occ(sh.occ, args, kp_begin, q);
     if (kp != cur_kp) {
+      if (cur_kp >= 0) fold(false);
       const int qrow = args.qidx[k * args.nk_part + kp];
       if (on) Lay::cache_row(t, trow0, args.vtab + (size_t)qrow * G::N, args.scale);
       cur_kp = kp;
@@ -629,32 +376,11 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
     mbar_wait_bounded(&sh.mbar[1], phase1);
   }
 
-  if constexpr (MODE == MODE_APPLY) {
-    float2* obase = args.out + split * args.split_stride + ((size_t)k * args.n_own + bandc) * G::N;
-#pragma unroll 1
-    for (int ps = 0; ps < (reg ? Lay::PPT : 0); ++ps) {
-      float acc[G::ROW];
-      TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
-      if (active) {
-        float4* o = reinterpret_cast<float4*>(obase + Lay::zg(t, ps));
-#pragma unroll
-        for (int e = 0; e < n / 2; ++e) o[e] = make_float4(acc[4 * e], acc[4 * e + 1], acc[4 * e + 2], acc[4 * e + 3]);
-      }
-    }
-    if (on) Lay::extra_store(t, obase, trow0, active);
-  } else {
-    const float2* lhs = (MODE == MODE_ENERGY) ? own : args.part2 + ((size_t)k * args.n_own + bandc) * G::N;
-    double d = 0.0;
-#pragma unroll 1
-    for (int ps = 0; ps < (reg ? Lay::PPT : 0); ++ps) {
-      float acc[G::ROW];
-      TmemRow<G::ROW>::load(trow0 + (uint32_t)(ps * G::ROW), acc);
-      cpx<float> w[n];
-      load_pencil_global<n>(w, lhs + Lay::zg(t, ps));
-#pragma unroll
-      for (int e = 0; e < n; ++e) d += (double)w[e].x * (double)acc[2 * e] + (double)w[e].y * (double)acc[2 * e + 1];
-    }
-    if (on) d += Lay::extra_dot(t, lhs, trow0);
+  // the last group (with no partner at all, the accumulators still hold zeros: one fold
+  // writes them)
+  fold(true);
+  if constexpr (MODE != MODE_APPLY) {
+    const double d = dsum;
     __syncthreads();
     double* red = reinterpret_cast<double*>(sbase);
     red[tid] = valid ? d : 0.0;

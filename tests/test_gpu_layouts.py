@@ -1,12 +1,11 @@
 """Each pencil layout of the fused kernels against the FP64 oracle.
 
 The layout is chosen per plan through HSE_BLOCKS_PER_SM: for the staged-partner kernel -1 two
-pencils per thread, -2 one pencil per thread, -3 one pencil per thread plus the lane-split
-pencils of 20^3; for the pencil-load kernel 1 one CTA per SM with uncapped registers (two
+pencils per thread, -2 one pencil per thread; for the pencil-load kernel 1 one CTA per SM with uncapped registers (two
 pencils per thread on 9 warps at 24^3), 2 two CTAs per SM where they fit (16^3), and 3 the
 ragged 24^3 form (12 warps, a second pencil for the first 192 threads; the default there).
-For every
-layout the test runs V_x u (owner = target apply), the exchange energy (energy epilogue) and
+The pencil-load kernel reads pencil-blocked copies of the orbitals by default; the cases with
+HSE_PENCIL_BLOCKS=0 run it on the caller's [x][y][z] arrays.  For every layout the test runs V_x u (owner = target apply), the exchange energy (energy epilogue) and
 the full vector-Jacobian product, whose d/d omega term runs the owner = target dot epilogue
 (Sec. II C; Eq. "Fock" and its derivative with respect to omega).
 """
@@ -19,7 +18,9 @@ from paper_1507_05156_gb300 import hse, inputs
 
 pytestmark = pytest.mark.gpu
 
-LAYOUT_CASES = [(12, -1), (12, -2), (16, -1), (16, -2), (16, 2), (18, -1), (18, -2), (20, -1), (20, -2), (20, -3), (8, -1), (8, -2), (24, 1), (24, 3)]
+LAYOUT_CASES = [(12, -1, 1), (12, -2, 1), (16, -1, 1), (16, -2, 1), (16, 2, 1), (18, -1, 1), (18, -2, 1),
+                (20, -1, 1), (20, -2, 1), (8, -1, 1), (8, -2, 1), (24, 1, 1), (24, 3, 1),
+                (24, 3, 0), (16, -2, 0), (20, -2, 0)]
 
 
 def _dev(x, dtype):
@@ -31,9 +32,10 @@ def _rel(got, ref):
     return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
 
 
-@pytest.mark.parametrize("n,variant", LAYOUT_CASES)
-def test_staged_layout_apply_energy_vjp(n, variant, monkeypatch):
+@pytest.mark.parametrize("n,variant,blocks", LAYOUT_CASES)
+def test_staged_layout_apply_energy_vjp(n, variant, blocks, monkeypatch):
     monkeypatch.setenv("HSE_BLOCKS_PER_SM", str(variant))
+    monkeypatch.setenv("HSE_PENCIL_BLOCKS", str(blocks))
     grid = (n, n, n)
     lattice = inputs.cubic_lattice(inputs.A_SI)
     rng = np.random.default_rng(1000 + 10 * n - variant)
