@@ -280,7 +280,7 @@ struct hse_plan_s {
   int nsplit[3] = {1, 1, 1};  // k'-loop splits of the fused kernel per OwnerRole
   float2* split_buf = nullptr;  // [nsplit][nk_own][n_own][N] partial outputs when nsplit > 1
   size_t split_buf_elems = 0;
-  float2* comp_buf = nullptr;   // [nsplit][nk_own][n_own][N] compensation sums (APPLY / OCC)
+  float2* comp_buf = nullptr;   // [nsplit][nk_own][n_own][2][blocked] running sums s, c (APPLY / OCC)
   // pencil-blocked copies of the orbital arrays a pencil-load launch reads (allocated on first
   // use, grown when a larger call comes)
   float2* blk_buf = nullptr;
@@ -305,7 +305,7 @@ struct hse_plan_s {
   std::vector<BatchCell> h_cells;       // launch arguments, pointers refreshed per call
   std::vector<float2*> cell_split;      // per cell [kMaxBatchSplit][nk][n_tgt][N]
   std::vector<float2*> cell_blk;        // pencil-load cells: blocked u_tgt then u_occ (else null)
-  std::vector<float2*> cell_comp;       // per cell [min(kMaxBatchSplit, nk)][nk][n_tgt][N] compensation sums
+  std::vector<float2*> cell_comp;       // per cell [min(kMaxBatchSplit, nk)][nk][n_tgt][2][blocked] running sums
   BatchCell* d_cells = nullptr;
   BatchItem* d_items = nullptr;         // staged-partner items, then pencil-load items
   int* d_counter = nullptr;             // [2]: one per list
@@ -566,7 +566,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
       if (need * sizeof(float2) > ((size_t)4 << 30)) best = 1;  // keep split buffers modest
       plan->nsplit[o] = best;
       if (best > 1) buf = std::max(buf, need);
-      if (o != ROLE_ENERGY) comp = std::max(comp, (size_t)best * k_own[o] * owners[o] * N);
+      if (o != ROLE_ENERGY) comp = std::max(comp, (size_t)best * k_own[o] * owners[o] * 2 * blocked_stride(n1));
     }
     if (buf) {
       HSE_TRY(cudaMalloc(&plan->split_buf, buf * sizeof(float2)));
@@ -1229,7 +1229,8 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
     plan->cell_split.push_back(buf);
     float2* comp = nullptr;
     if (e == cudaSuccess)
-      e = cudaMalloc(&comp, (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * q.n_tgt * sub->N * sizeof(float2));
+      e = cudaMalloc(&comp, (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * q.n_tgt * 2 * blocked_stride(q.grid[0]) *
+                                sizeof(float2));
     plan->cell_comp.push_back(comp);
     float2* blk = nullptr;
     int sp = 0, br = 0;

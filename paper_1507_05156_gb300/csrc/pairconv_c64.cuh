@@ -127,7 +127,9 @@ struct PairArgs {
   int inject;           // test hook: 1 = the staged kernel never issues its first partner copy
   int blk;              // pencil-load kernel: own, part and part2 are in the pencil-blocked
                         // layout (OrbBlk below) instead of [x][y][z]; out stays [x][y][z]
-  float2* comp;         // APPLY / OCC: compensation sums, the shape of out (split_stride apart)
+  float2* comp;         // APPLY / OCC: running sums s, c of the compensated accumulation: per
+                        // owner orbital of each split, s then c in the pencil-blocked layout
+                        // (2 OrbBlk::NBK complex), owners in the order of out
 };
 
 // ---------------------------------------------------------------------------------------
@@ -135,9 +137,11 @@ struct PairArgs {
 // every k' and every occupied band).  The TMEM accumulator of a pencil holds the sum over the
 // bands of one k' (a group, in FP32).  When the group ends it is added to the pencil's running
 // sum s with Knuth's TwoSum, whose exact rounding error is added to a second running sum c;
-// the pencil's result is s + c.  s lives in the output (or the work item's split partial), c in
-// PairArgs::comp at the same offset; only the thread that owns the pencil touches them.  The
-// dot epilogues (energy, d/d omega) instead add each group's FP32 pencil dot to an FP64 sum.
+// the pencil's result is s + c, written to the output (or the work item's split partial) by
+// the last fold.  s and c live in PairArgs::comp in the pencil-blocked layout (a warp's 32
+// pencils move as 512 contiguous bytes per access); only the thread that owns a pencil touches
+// its sums.  The dot epilogues (energy, d/d omega) instead add each group's FP32 pencil dot to
+// an FP64 sum.
 // ---------------------------------------------------------------------------------------
 
 // a + b = s + err exactly, s = fl(a + b) (TwoSum; no fast-math reassociation in this build)
@@ -160,23 +164,32 @@ __device__ __forceinline__ void fold4(float4& sv, float4& cv, const float4 s0, c
   cv.w = c0.w + er;
 }
 
-// Folds one group row g (a z-pencil, 2n floats) into the running sums at s4 / c4 (n/2 float4
-// each, global).  first: s = g, c = 0 (nothing is read).  last: the final s + c is written to
-// s4 and c4 is left alone.
+// Folds one group row g (z-pencil p, 2n floats) into the running sums of its orbital: s at
+// sums (n/2 float4 per pencil, pencil-blocked), c at sums + NBK/2 float4.  first: s = g (c is
+// not written); second: c is still zero (not read); last: the final s + c goes to out4 (the
+// pencil in [x][y][z] order, n/2 float4).  With first and last together out4 = g.
 template <int n>
-__device__ __forceinline__ void fold_group(const float* g, float4* s4, float4* c4, bool first, bool last) {
+__device__ __forceinline__ void fold_group(const float* g, float4* __restrict__ sums, int p, float4* out4,
+                                           bool first, bool second, bool last) {
+  float4* s4 = sums + (size_t)(p >> 5) * (n / 2) * 32 + (p & 31);
+  float4* c4 = s4 + blocked_stride(n) / 2;
 #pragma unroll
   for (int e = 0; e < n / 2; ++e) {
     float4 sv = make_float4(g[4 * e], g[4 * e + 1], g[4 * e + 2], g[4 * e + 3]);
     float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (!first) fold4(sv, cv, s4[e], c4[e]);
+    if (!first) fold4(sv, cv, s4[32 * e], second ? make_float4(0.f, 0.f, 0.f, 0.f) : c4[32 * e]);
     if (last) {
-      s4[e] = make_float4(sv.x + cv.x, sv.y + cv.y, sv.z + cv.z, sv.w + cv.w);
+      out4[e] = make_float4(sv.x + cv.x, sv.y + cv.y, sv.z + cv.z, sv.w + cv.w);
     } else {
-      s4[e] = sv;
-      c4[e] = cv;
+      s4[32 * e] = sv;
+      if (!first) c4[32 * e] = cv;
     }
   }
+}
+
+// running sums of owner orbital `orb` (counted in the order of out, splits included)
+__device__ __forceinline__ float4* sums_of(const PairArgs& a, size_t orb, size_t nbk) {
+  return reinterpret_cast<float4*>(a.comp + orb * 2 * nbk);
 }
 
 // Re <w | g> over one pencil (n complex values; g interleaved), FP32
@@ -510,9 +523,10 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
   // running sums in the item's output region ([x][y][z]) and in args.comp; ENERGY / DOT add
   // group dots to dsum (FP64)
   const size_t oofs = split * args.split_stride + ((size_t)k * args.n_own + bandc) * G::N;
+  float4* sums = (MODE == MODE_APPLY || MODE == MODE_OCC) ? sums_of(args, oofs / G::N, OrbBlk<n>::NBK) : nullptr;
   const float2* lhs = (MODE == MODE_DOT) ? args.part2 + ((size_t)k * args.n_own + bandc) * ostr : own;
   double dsum = 0.0;
-  auto fold = [&](bool first, bool last) {
+  auto fold = [&](bool first, bool second, bool last) {
     if (!warp_on) return;
 #pragma unroll 1
     for (int ps = 0; ps < PPT; ++ps) {
@@ -522,9 +536,8 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
       TmemRow<G::ROW>::load(trow, acc);
       if constexpr (MODE == MODE_APPLY || MODE == MODE_OCC) {
         if (active) {
-          const size_t o = oofs + (size_t)(t + ps * TS) * n;
-          fold_group<n>(acc, reinterpret_cast<float4*>(args.out + o), reinterpret_cast<float4*>(args.comp + o),
-                        first, last);
+          const int p = t + ps * TS;
+          fold_group<n>(acc, sums, p, reinterpret_cast<float4*>(args.out + oofs + (size_t)p * n), first, second, last);
         }
       } else {
         cpx<float> w[n];
@@ -538,7 +551,7 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
       }
     }
   };
-  if (kp_begin == kp_end) fold(true, true);  // an empty k' range: zeros
+  if (kp_begin == kp_end) fold(true, false, true);  // an empty k' range: zeros
 
   for (int kp = kp_begin; kp < kp_end; ++kp) {
     // q = k_i - k_j: APPLY-like modes own i (at k) and pair with j at kp; OCC owns j (at k)
@@ -565,7 +578,7 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
         if (warp_on) stage_z_inverse<n, EPI_WCONJ, PPT, TS>(g, t, part, trow0, blk);
       }
     }
-    fold(kp == kp_begin, kp == kp_end - 1);
+    fold(kp == kp_begin, kp == kp_begin + 1, kp == kp_end - 1);
   }
 
   if constexpr (MODE == MODE_ENERGY || MODE == MODE_DOT) {

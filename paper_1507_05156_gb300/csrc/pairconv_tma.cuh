@@ -280,6 +280,7 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
   // compensated accumulation over the k' groups of the item: APPLY keeps the running sums in
   // its output region (s) and in args.comp (c); ENERGY / DOT add group dots to dsum (FP64)
   const size_t oofs = split * args.split_stride + ((size_t)k * args.n_own + bandc) * G::N;
+  float4* sums = (MODE == MODE_APPLY) ? sums_of(args, oofs / G::N, OrbBlk<n>::NBK) : nullptr;
   const float2* lhs = (MODE == MODE_DOT) ? args.part2 + ((size_t)k * args.n_own + bandc) * G::N : own;
   double dsum = 0.0;
   int folds = 0;
@@ -291,9 +292,9 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
       TmemRow<G::ROW>::load(trow, acc);
       if constexpr (MODE == MODE_APPLY) {
         if (active) {
-          const size_t o = oofs + Lay::zg(t, ps);
-          fold_group<n>(acc, reinterpret_cast<float4*>(args.out + o), reinterpret_cast<float4*>(args.comp + o),
-                        folds == 0, last);
+          const int zg = Lay::zg(t, ps);
+          fold_group<n>(acc, sums, zg / n, reinterpret_cast<float4*>(args.out + oofs + zg), folds == 0, folds == 1,
+                        last);
         }
       } else {
         cpx<float> w[n];
