@@ -187,17 +187,6 @@ __device__ __forceinline__ void fold_group(const float* g, float4* __restrict__ 
   }
 }
 
-// Bulk prefetch into L2 of the running sums (s and c) of the 32-pencil block holding pencil p:
-// two contiguous ranges of (n/2) 32 float4 each.  One lane per warp issues it.
-template <int n>
-__device__ __forceinline__ void prefetch_sums_block(const float4* sums, int p) {
-  const float4* s4 = sums + (size_t)(p >> 5) * (n / 2) * 32;
-  const float4* c4 = s4 + blocked_stride(n) / 2;
-  constexpr uint32_t bytes = (n / 2) * 32 * 16;
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s4), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c4), "r"(bytes) : "memory");
-}
-
 // running sums of owner orbital `orb` (counted in the order of out, splits included)
 __device__ __forceinline__ float4* sums_of(const PairArgs& a, size_t orb, size_t nbk) {
   return reinterpret_cast<float4*>(a.comp + orb * 2 * nbk);
@@ -569,14 +558,6 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     const int qrow = (MODE == MODE_OCC) ? args.qidx[kp * args.nk_own + k] : args.qidx[k * args.nk_part + kp];
     if (warp_on) cache_kernel_row<n, PPT, false, n * n, TS>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
     for (int j = 0; j < args.n_part; ++j) {
-      if constexpr (MODE == MODE_APPLY || MODE == MODE_OCC) {
-        // the fold after this k' reads the running sums: bring them towards L2 first
-        if (j == args.n_part - 1 && kp > kp_begin && warp_on && active && (tid & 31) == 0) {
-#pragma unroll 1
-          for (int ps = 0; ps < PPT; ++ps)
-            if (TS * PPT == G::NN || t + ps * TS < G::NN) prefetch_sums_block<n>(sums, t + ps * TS);
-        }
-      }
       const float2* part = args.part + ((size_t)kp * args.n_part + j) * ostr;
       if constexpr (MODE != MODE_OCC) {
         const float f = (float)args.occ[kp * args.n_occ + j];

@@ -339,14 +339,6 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
     if (buf) phase1 ^= 1u; else phase0 ^= 1u;
     const float2* stg = stage + buf * S::STAGE_CPX;
     const int qn = next_partner(sh.occ, args, kp_begin, q + 1, npairs);
-    if constexpr (MODE == MODE_APPLY) {
-      // the last pair of a k' group after the item's first: the fold after it reads the
-      // running sums, so bring them towards L2 now
-      if (folds > 0 && (qn >= npairs || kp_begin + qn / args.n_part != kp) && reg && active && lane == 0) {
-#pragma unroll 1
-        for (int ps = 0; ps < Lay::PPT; ++ps) prefetch_sums_block<n>(sums, Lay::zg(t, ps) / n);
-      }
-    }
     // refill stage[buf ^ 1] with the next partner once every thread is past its last read of it
     // (the previous pair's Z inverse)
     auto refill = [&]() {
