@@ -4,3 +4,4 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py`` ma
 import this package.  The CUDA library and its Python binding never do.
 """
 from .hse_oracle import *  # noqa: F401,F403
+from . import ortho  # noqa: F401
