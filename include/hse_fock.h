@@ -52,6 +52,7 @@ extern "C" {
 #define HSE_ERR_TIMEOUT          -5  /* a bounded device-side wait gave up              */
 #define HSE_ERR_NOMEM            -6  /* plan allocation failed                          */
 #define HSE_ERR_DEVICE           -7  /* a kernel recorded a failed device-side check    */
+#define HSE_ERR_SINGULAR         -8  /* orthonormalisation met a linearly dependent band */
 
 /* Arithmetic of the pair convolutions. */
 #define HSE_C64   0  /* complex64 orbitals, fused FP32 kernel, FP64 energy/omega reduction */
@@ -139,8 +140,8 @@ int hse_fock_apply_batched(hse_plan plan, const void *const *u_occ, const double
 int hse_kinetic_apply(hse_plan plan, const void *u, int nbands, const double *A, void *out,
                       hse_stream_t stream);
 
-/* Synchronises the stream, then returns HSE_OK, HSE_ERR_TIMEOUT or HSE_ERR_DEVICE from
- * the plan's device status word (and clears it), or HSE_ERR_CUDA.  Every device-side wait of
+/* Synchronises the stream, then returns HSE_OK, HSE_ERR_TIMEOUT, HSE_ERR_SINGULAR or
+ * HSE_ERR_DEVICE from the plan's device status word (and clears it), or HSE_ERR_CUDA.  Every device-side wait of
  * the library is bounded (about one second); on expiry the kernel records HSE_ERR_TIMEOUT,
  * stops waiting and returns, so the context stays usable.  Test hook: a plan created while
  * the environment variable HSE_INJECT_SKIP_FILL=1 is set never issues the first asynchronous
@@ -221,6 +222,31 @@ int hse_hartree_potential(hse_plan plan, const void *psi, const double *occ, dou
  * in the plan; later calls are asynchronous on `stream`.  Not for batched plans. */
 int hse_current(hse_plan plan, const void *psi, const double *occ, const double *A, double *J,
                 hse_stream_t stream);
+
+/* Overlap matrices of a set of orbitals, in FP64 (products and sums; complex64 orbitals are
+ * widened on load).  With cell normalisation, as everywhere in this interface:
+ *   S[k][a][b] = dV sum_r conj(u_{a,k}(r)) u_{b,k}(r),   dV = Omega / N.
+ * The 4th-order Taylor step (Sec. II C) is not unitary: max |S - 1| of the propagated
+ * orbitals is the check of a propagation.
+ *   u  device [nk][nbands][N] (the plan's dtype), nbands >= 1
+ *   S  device double [nk][nbands][nbands][2] (real, imaginary), overwritten; S[k][b][a] is
+ *      the conjugate of S[k][a][b]
+ * Asynchronous on `stream`.  Not for batched plans. */
+int hse_overlap(hse_plan plan, const void *u, int nbands, double *S, hse_stream_t stream);
+
+/* Orthonormalises the bands of every k-point in place, in band order: modified Gram-Schmidt
+ * (band a loses its component along each earlier band b < a in turn, then is divided by its
+ * norm), applied twice, with every inner product and update in FP64.  complex64 orbitals are
+ * widened into an FP64 copy and rounded once when written back; complex128 ones are updated
+ * in place.  A band that is linearly dependent on the earlier ones (its norm after the
+ * projections at most 1e-12 of its norm before them for complex128, 1e-5 for complex64, whose
+ * rounding leaves about 1e-7 of any band outside the span of the others) is set to zero and
+ * the plan's status word records HSE_ERR_SINGULAR (returned by hse_status).
+ *   u  device [nk][nbands][N] (the plan's dtype), 1 <= nbands <= 4096, overwritten
+ * complex64: the first call (or one with more bands than before) allocates an FP64 copy of
+ * the orbitals in the plan (device-wide synchronisation).  Asynchronous on `stream`
+ * otherwise.  Not for batched plans. */
+int hse_orthonormalize(hse_plan plan, void *u, int nbands, hse_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -299,6 +299,8 @@ struct hse_plan_s {
   double2* cur_work = nullptr;  // current: FP64 transforms [nk][n_occ][N]
   double* cur_partial = nullptr;  // current: [nk][n_occ][3]
   double2* hart_work = nullptr;   // Hartree potential: [N] FP64 transform
+  double2* ortho_work = nullptr;  // orthonormalisation of complex64 orbitals: FP64 copy
+  size_t ortho_elems = 0;
   // batched plans (hse_plan_create_batched)
   bool batched = false;
   std::vector<hse_plan> cells;          // one sub-plan (kernel tables) per cell
@@ -399,6 +401,7 @@ const char* hse_strerror(int code) {
     case HSE_ERR_TIMEOUT: return "device-side wait timed out";
     case HSE_ERR_NOMEM: return "out of device memory";
     case HSE_ERR_DEVICE: return "device-side check failed";
+    case HSE_ERR_SINGULAR: return "linearly dependent band in orthonormalisation";
     default: return "unknown error";
   }
 }
@@ -440,6 +443,7 @@ int hse_plan_destroy(hse_plan plan) {
   cudaFree(plan->cur_work);
   cudaFree(plan->cur_partial);
   cudaFree(plan->hart_work);
+  cudaFree(plan->ortho_work);
   cudaSetDevice(prev);
   delete plan;
   return HSE_OK;
@@ -640,7 +644,7 @@ int hse_status(hse_plan plan, hse_stream_t stream) {
   if (e != cudaSuccess) return HSE_ERR_CUDA;
   if (st != 0) {
     cudaMemset(plan->status, 0, sizeof(int));
-    return st == HSE_ERR_TIMEOUT ? HSE_ERR_TIMEOUT : HSE_ERR_DEVICE;
+    return (st == HSE_ERR_TIMEOUT || st == HSE_ERR_SINGULAR) ? st : HSE_ERR_DEVICE;
   }
   return HSE_OK;
 }
@@ -1175,6 +1179,33 @@ int hse_current(hse_plan plan, const void* psi, const double* occ, const double*
   a.kpts = plan->dkpts;
   return cuda_fail(launch_current(p.dtype == HSE_C128, psi, occ, a, plan->cur_work, plan->cur_partial,
                                   p.spin_degeneracy, J, S(stream)));
+}
+
+int hse_overlap(hse_plan plan, const void* u, int nbands, double* s_out, hse_stream_t stream) {
+  if (!plan || plan->batched || !u || !s_out || nbands < 1 || nbands > 4096 || plan->p.nk > 65535)
+    return HSE_ERR_INVALID_ARG;
+  if (!aligned16(u) || !aligned16(s_out)) return HSE_ERR_INVALID_ARG;
+  const hse_problem& p = plan->p;
+  const size_t ub = (size_t)p.nk * nbands * plan->N * elem_bytes(p.dtype);
+  if (overlaps(s_out, (size_t)p.nk * nbands * nbands * 2 * sizeof(double), u, ub)) return HSE_ERR_ALIAS;
+  return cuda_fail(launch_overlap(p.dtype == HSE_C128, u, p.nk, nbands, plan->N, plan->dV, (double2*)s_out, S(stream)));
+}
+
+int hse_orthonormalize(hse_plan plan, void* u, int nbands, hse_stream_t stream) {
+  if (!plan || plan->batched || !u || nbands < 1 || nbands > 4096) return HSE_ERR_INVALID_ARG;
+  if (!aligned16(u)) return HSE_ERR_INVALID_ARG;
+  const hse_problem& p = plan->p;
+  const size_t count = (size_t)p.nk * nbands * plan->N;
+  if (p.dtype == HSE_C64 && count > plan->ortho_elems) {
+    cudaFree(plan->ortho_work);
+    plan->ortho_work = nullptr;
+    plan->ortho_elems = 0;
+    const cudaError_t e = cudaMalloc(&plan->ortho_work, count * sizeof(double2));
+    if (e != cudaSuccess) return cuda_fail(e);
+    plan->ortho_elems = count;
+  }
+  return cuda_fail(launch_orthonormalize(p.dtype == HSE_C128, u, p.nk, nbands, plan->N, plan->dV, plan->ortho_work,
+                                         plan->status, S(stream)));
 }
 
 int hse_hartree_potential(hse_plan plan, const void* psi, const double* occ, double* vh, hse_stream_t stream) {

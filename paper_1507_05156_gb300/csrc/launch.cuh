@@ -37,6 +37,16 @@ cudaError_t launch_hartree(bool c128, const void* psi, const double* occ, const 
 cudaError_t launch_current(bool c128, const void* psi, const double* occ, const CurArgs& a, double2* work,
                            double* partial, double spin_degeneracy, double* J, cudaStream_t stream);
 
+// Overlap matrices and Gram-Schmidt orthonormalisation in FP64 (ortho.cu).
+constexpr int kStatusSingular = -8;  // HSE_ERR_SINGULAR
+// S device [nk][nb][nb] double2: S[k][a][b] = dV sum_r conj(u_{a,k}) u_{b,k}
+cudaError_t launch_overlap(bool c128, const void* u, int nk, int nb, size_t N, double dV, double2* S,
+                           cudaStream_t stream);
+// u [nk][nb][N] in place (two modified Gram-Schmidt passes); work: [nk][nb][N] double2
+// scratch for complex64 orbitals (unused for complex128); status: the plan's status word.
+cudaError_t launch_orthonormalize(bool c128, void* u, int nk, int nb, size_t N, double dV, double2* work, int* status,
+                                  cudaStream_t stream);
+
 // Fused complex64 pair-convolution launch for a cubic grid of side n (one TU per size
 // group keeps the build parallel).  Returns a cudaError_t.
 cudaError_t launch_pairconv_c64(int n, int mode, const PairArgs& args, int blocks_per_sm, cudaStream_t stream);

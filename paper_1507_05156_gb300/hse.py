@@ -27,13 +27,15 @@ HSE_C128 = 1
 ERRORS = {
     0: "HSE_OK", -1: "HSE_ERR_INVALID_ARG", -2: "HSE_ERR_UNSUPPORTED_GRID", -3: "HSE_ERR_ALIAS",
     -4: "HSE_ERR_CUDA", -5: "HSE_ERR_TIMEOUT", -6: "HSE_ERR_NOMEM", -7: "HSE_ERR_DEVICE",
+    -8: "HSE_ERR_SINGULAR",
 }
 
 #: every symbol include/hse_fock.h declares
 EXPORTS = ("hse_plan_create", "hse_plan_create_batched", "hse_plan_destroy", "hse_fock_apply",
            "hse_exchange_energy", "hse_fock_apply_vjp", "hse_fock_apply_batched", "hse_status",
            "hse_grid_supported", "hse_kernel_launches", "hse_strerror", "hse_exchange_energy_noalloc",
-           "hse_kinetic_apply", "hse_taylor_step", "hse_current", "hse_hartree_potential")
+           "hse_kinetic_apply", "hse_taylor_step", "hse_current", "hse_hartree_potential", "hse_overlap",
+           "hse_orthonormalize")
 
 
 class HseError(RuntimeError):
@@ -94,6 +96,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hse_current.restype = i
         lib.hse_hartree_potential.argtypes = [vp, vp, vp, vp, vp]
         lib.hse_hartree_potential.restype = i
+        lib.hse_overlap.argtypes = [vp, vp, i, vp, vp]
+        lib.hse_overlap.restype = i
+        lib.hse_orthonormalize.argtypes = [vp, vp, i, vp]
+        lib.hse_orthonormalize.restype = i
         lib.hse_strerror.argtypes = [i]
         lib.hse_strerror.restype = ctypes.c_char_p
         for name in ("hse_plan_create", "hse_plan_create_batched", "hse_plan_destroy", "hse_fock_apply",
@@ -382,6 +388,34 @@ def hse_current(plan: Plan, psi: torch.Tensor, occ: torch.Tensor, A, out: Option
     _dev(out, plan, (3,), torch.float64, "out")
     _check(lib.hse_current(plan.handle, _ptr(psi), _ptr(occ), _vec3(A), _ptr(out), _stream(stream)), "hse_current")
     return out
+
+
+def _bands(plan: Plan, u: torch.Tensor) -> int:
+    if u.dim() != 5 or u.shape[0] != plan.nk or tuple(u.shape[2:]) != plan.grid:
+        raise ValueError(f"u has shape {tuple(u.shape)}, expected ({plan.nk}, nbands) + {plan.grid}")
+    nb = int(u.shape[1])
+    _dev(u, plan, plan.shape(nb), plan.dtype, "u")
+    return nb
+
+
+def hse_overlap(plan: Plan, u: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """FP64 overlap matrices S[k][a][b] = dV sum_r conj(u_a) u_b (complex128 [nk][nb][nb])."""
+    lib = load_library()
+    nb = _bands(plan, u)
+    if out is None:
+        out = torch.empty((plan.nk, nb, nb), dtype=torch.complex128, device=plan.device)
+    _dev(out, plan, (plan.nk, nb, nb), torch.complex128, "out")
+    _check(lib.hse_overlap(plan.handle, _ptr(u), nb, _ptr(out), _stream(stream)), "hse_overlap")
+    return out
+
+
+def hse_orthonormalize(plan: Plan, u: torch.Tensor, stream=None) -> torch.Tensor:
+    """Orthonormalises u [nk][nb][grid] in place per k-point (FP64 modified Gram-Schmidt, twice);
+    a linearly dependent band surfaces as HSE_ERR_SINGULAR from hse_status."""
+    lib = load_library()
+    nb = _bands(plan, u)
+    _check(lib.hse_orthonormalize(plan.handle, _ptr(u), nb, _stream(stream)), "hse_orthonormalize")
+    return u
 
 
 def hse_status(plan: Plan, stream=None) -> None:

@@ -14,6 +14,8 @@
   A(t) = -(E0 / w) cos(w t) sin^2(pi t / T_d), through the library's fused Taylor step
   (hse_taylor_step, no autograd) and records the current J(t) (hse_current, Sec. II A without
   the nonlocal part) and the energy absorbed per unit volume W(t) = int J . E dt (Sec. V).
+* ``overlap_drift``: max |S - 1| of the FP64 overlap matrices of a set of orbitals
+  (hse_overlap), the check of a propagation (the Taylor step is not unitary).
 
 Every operator application runs in the CUDA library; PyTorch only holds the tensors, forms
 the Taylor sum and drives autograd.
@@ -134,12 +136,20 @@ def pulse_field(t: float, E0: float, w: float, Td: float, direction) -> np.ndarr
     return -dA_dt * np.asarray(direction, dtype=np.float64)
 
 
+def overlap_drift(plan: hse.Plan, psi: torch.Tensor) -> float:
+    """max over k, a, b of |S_ab - delta_ab|, S = dV sum_r conj(psi_a) psi_b in FP64 on the GPU."""
+    S = hse.hse_overlap(plan, psi)
+    eye = torch.eye(S.shape[1], dtype=S.dtype, device=S.device)
+    return float((S - eye).abs().max().item())
+
+
 def propagate_pulse(psi0: torch.Tensor, occ: torch.Tensor, omega: float, geom: Geometry, dt: float, nsteps: int,
                     E0: float, w: float, Td: float, direction, hartree: bool = False):
     """nsteps fused Taylor steps under the pulse.  Step s (t_s = s dt) uses h frozen at psi(t_s)
     with A(t_s) (and, with ``hartree``, the Hartree potential of psi(t_s)); J_s = J(t_s) from
     psi(t_s) and A(t_s); W by the trapezoidal rule on J . E.
-    Returns (psi(t_nsteps), J [nsteps+1][3] float64 on the device, W [nsteps+1] numpy)."""
+    Returns (psi(t_nsteps), J [nsteps+1][3] float64 on the device, W [nsteps+1] numpy, the
+    overlap drift max |S - 1| of psi(t_nsteps))."""
     plan = geom.plan(psi0.shape[1], psi0.shape[1], omega, psi0.dtype)
     bufs = [psi0.contiguous().clone(), torch.empty_like(psi0)]
     J = torch.empty((nsteps + 1, 3), dtype=torch.float64, device=psi0.device)
@@ -154,4 +164,4 @@ def propagate_pulse(psi0: torch.Tensor, occ: torch.Tensor, omega: float, geom: G
     E = np.stack([pulse_field(s * dt, E0, w, Td, direction) for s in range(nsteps + 1)])
     p = np.einsum("sc,sc->s", Jh, E)
     W = np.concatenate([[0.0], np.cumsum(0.5 * dt * (p[1:] + p[:-1]))])
-    return bufs[0], J, W
+    return bufs[0], J, W, overlap_drift(plan, bufs[0])

@@ -211,8 +211,8 @@ def test_pulse_driver_matches_oracle(dtype, tol, hartree):
     E0, w, Td, d = 0.02, 0.3, 2.0, (0.0, 0.6, 0.8)
     dt, nsteps, omega = 0.1, 12, 0.2
     geom = tdks.Geometry(grid, lattice, kpts, alpha=0.25)
-    psi, J, W = tdks.propagate_pulse(dev(u, dtype), dev(occ, torch.float64), omega, geom, dt, nsteps, E0, w, Td, d,
-                                     hartree=hartree)
+    psi, J, W, drift = tdks.propagate_pulse(dev(u, dtype), dev(occ, torch.float64), omega, geom, dt, nsteps, E0,
+                                            w, Td, d, hartree=hartree)
     r_psi, r_J, r_W = otd.propagate_pulse(u, occ, kpts, lattice, grid, omega, 0.25, dt, nsteps, E0, w, Td, d,
                                           hartree=hartree)
     assert rel(psi.cpu().numpy(), r_psi) <= tol
@@ -220,3 +220,9 @@ def test_pulse_driver_matches_oracle(dtype, tol, hartree):
     assert np.abs(J - r_J).max() <= tol * np.abs(r_J).max()
     assert np.abs(W - r_W).max() <= tol * np.abs(r_W).max() + 1e-15
     assert np.abs(r_W).max() > 0  # the pulse did work
+    # the propagator check: the FP64 overlap drift of the propagated orbitals
+    dV = abs(np.linalg.det(lattice)) / np.prod(grid)
+    r_S = oracle.ortho.overlap(r_psi, dV)
+    r_drift = np.abs(r_S - np.eye(r_S.shape[1])[None]).max()
+    assert r_drift > 1e-6  # the 4th-order Taylor step is not unitary
+    assert abs(drift - r_drift) <= 20 * tol  # S is off by about twice the orbitals' error
