@@ -230,7 +230,7 @@ int hse_current(hse_plan plan, const void *psi, const double *occ, const double 
  * orbitals is the check of a propagation.
  *   u  device [nk][nbands][N] (the plan's dtype), nbands >= 1
  *   S  device double [nk][nbands][nbands][2] (real, imaginary), overwritten; S[k][b][a] is
- *      the conjugate of S[k][a][b]
+ *      the conjugate of S[k][a][b] and the diagonal is real
  * Asynchronous on `stream`.  Not for batched plans. */
 int hse_overlap(hse_plan plan, const void *u, int nbands, double *S, hse_stream_t stream);
 

@@ -43,7 +43,8 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double* red) {
   return s;
 }
 
-// S[k][a][b] = dV sum_r conj(u_a) u_b and S[k][b][a] = conj of it: block (pair a <= b, k).
+// S[k][a][b] = dV sum_r conj(u_a) u_b and S[k][b][a] = conj of it (a real diagonal): block
+// (pair a <= b, k).
 template <typename C>
 __global__ void __launch_bounds__(kOverlapThreads) overlap_kernel(const C* __restrict__ u, int nb, size_t N, double dV,
                                                                   double2* __restrict__ S) {
@@ -65,8 +66,12 @@ __global__ void __launch_bounds__(kOverlapThreads) overlap_kernel(const C* __res
   }
   const double2 s = block_sum2(acc, red);
   if (threadIdx.x == 0) {
-    S[((size_t)k * nb + a) * nb + b] = make_double2(dV * s.x, dV * s.y);
-    S[((size_t)k * nb + b) * nb + a] = make_double2(dV * s.x, -dV * s.y);
+    if (a == b) {  // <a|a> is real: its imaginary part is rounding only
+      S[((size_t)k * nb + a) * nb + a] = make_double2(dV * s.x, 0.0);
+    } else {
+      S[((size_t)k * nb + a) * nb + b] = make_double2(dV * s.x, dV * s.y);
+      S[((size_t)k * nb + b) * nb + a] = make_double2(dV * s.x, -dV * s.y);
+    }
   }
 }
 
