@@ -135,7 +135,8 @@ struct PairArgs {
 // ---------------------------------------------------------------------------------------
 // Compensated accumulation over k' (Sec. II C, Eq. "Fock": V_x u sums the pair terms over
 // every k' and every occupied band).  The TMEM accumulator of a pencil holds the sum over the
-// bands of one k' (a group, in FP32).  When the group ends it is added to the pencil's running
+// bands of a group of consecutive k' (in FP32; fold_span k-points, so that a group holds at
+// least 16 band terms where the bands are fewer).  When the group ends it is added to the pencil's running
 // sum s with Knuth's TwoSum, whose exact rounding error is added to a second running sum c;
 // the pencil's result is s + c, written to the output (or the work item's split partial) by
 // the last fold.  s and c live in PairArgs::comp in the pencil-blocked layout (a warp's 32
@@ -143,6 +144,9 @@ struct PairArgs {
 // its sums.  The dot epilogues (energy, d/d omega) instead add each group's FP32 pencil dot to
 // an FP64 sum.
 // ---------------------------------------------------------------------------------------
+
+// k-points per fold group: one, or enough for 16 partner bands
+__host__ __device__ __forceinline__ int fold_span(int n_part) { return n_part >= 16 ? 1 : (16 + n_part - 1) / n_part; }
 
 // a + b = s + err exactly, s = fl(a + b) (TwoSum; no fast-math reassociation in this build)
 __device__ __forceinline__ float two_sum(float a, float b, float& err) {
@@ -552,6 +556,7 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     }
   };
   if (kp_begin == kp_end) fold(true, false, true);  // an empty k' range: zeros
+  const int fspan = fold_span(args.n_part);
 
   for (int kp = kp_begin; kp < kp_end; ++kp) {
     // q = k_i - k_j: APPLY-like modes own i (at k) and pair with j at kp; OCC owns j (at k)
@@ -578,7 +583,9 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
         if (warp_on) stage_z_inverse<n, EPI_WCONJ, PPT, TS>(g, t, part, trow0, blk);
       }
     }
-    fold(kp == kp_begin, kp == kp_begin + 1, kp == kp_end - 1);
+    // the end of a fold group (fold_span k-points) or of the item's k' range
+    const int grp = (kp - kp_begin) / fspan;
+    if (kp == kp_end - 1 || (kp - kp_begin + 1) % fspan == 0) fold(grp == 0, grp == 1, kp == kp_end - 1);
   }
 
   if constexpr (MODE == MODE_ENERGY || MODE == MODE_DOT) {

@@ -284,6 +284,7 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
   const float2* lhs = (MODE == MODE_DOT) ? args.part2 + ((size_t)k * args.n_own + bandc) * G::N : own;
   double dsum = 0.0;
   int folds = 0;
+  const int fspan = fold_span(args.n_part);
   auto fold = [&](bool last) {
 #pragma unroll 1
     for (int ps = 0; ps < (reg ? Lay::PPT : 0); ++ps) {
@@ -323,7 +324,8 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
     const int kp = kp_begin + q / args.n_part;
     const float f = item_occ(sh.occ, args, kp_begin, q);
     if (kp != cur_kp) {
-      if (cur_kp >= 0) fold(false);
+      // a new fold group (fold_span k-points) starts: fold the previous one
+      if (cur_kp >= 0 && (kp - kp_begin) / fspan != (cur_kp - kp_begin) / fspan) fold(false);
       const int qrow = args.qidx[k * args.nk_part + kp];
       if (on) Lay::cache_row(t, trow0, args.vtab + (size_t)qrow * G::N, args.scale);
       cur_kp = kp;
