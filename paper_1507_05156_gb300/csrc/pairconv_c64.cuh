@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
 #include "fft_reg.cuh"
 #include "tmem.cuh"
 #include "tmem_gen.cuh"
@@ -188,6 +190,61 @@ __device__ __forceinline__ void fold_group(const float* g, float4* __restrict__ 
       s4[32 * e] = sv;
       if (!first) c4[32 * e] = cv;
     }
+  }
+}
+
+// The same fold with the running sums in TMEM (the layouts that have the columns): s at ts
+// (2n columns, FP32), c at tc (n columns, bf16 pairs: c is the sum of rounding errors, about
+// 1e-7 of s, so its own 2^-9 rounding is far below the FP32 resolution of s).  Warp-wide
+// (TMEM); out4: the pencil in [x][y][z] order, written by the last fold, or null (inactive).
+template <int n>
+__device__ __forceinline__ void fold_group_tmem(const float* g, uint32_t ts, uint32_t tc, float4* out4, bool first,
+                                                bool second, bool last) {
+  float sv[2 * n], cv[2 * n];
+  if (first) {
+#pragma unroll
+    for (int e = 0; e < 2 * n; ++e) {
+      sv[e] = g[e];
+      cv[e] = 0.f;
+    }
+  } else {
+    TmemRow<2 * n>::load(ts, sv);
+    if (second) {
+#pragma unroll
+      for (int e = 0; e < 2 * n; ++e) cv[e] = 0.f;
+    } else {
+      float cp[n];
+      TmemRow<n>::load(tc, cp);
+#pragma unroll
+      for (int e = 0; e < n; ++e) {
+        const float2 c2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&cp[e]));
+        cv[2 * e] = c2.x;
+        cv[2 * e + 1] = c2.y;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 2 * n; ++e) {
+      float er;
+      sv[e] = two_sum(sv[e], g[e], er);
+      cv[e] += er;
+    }
+  }
+  if (last) {
+    if (out4) {
+#pragma unroll
+      for (int e = 0; e < n / 2; ++e)
+        out4[e] = make_float4(sv[4 * e] + cv[4 * e], sv[4 * e + 1] + cv[4 * e + 1], sv[4 * e + 2] + cv[4 * e + 2],
+                              sv[4 * e + 3] + cv[4 * e + 3]);
+    }
+  } else {
+    TmemRow<2 * n>::store(ts, sv);
+    float cp[n];
+#pragma unroll
+    for (int e = 0; e < n; ++e) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(cv[2 * e], cv[2 * e + 1]);
+      cp[e] = *reinterpret_cast<const float*>(&h);
+    }
+    TmemRow<n>::store(tc, cp);
   }
 }
 

@@ -119,7 +119,8 @@ __device__ __forceinline__ void stage_z_inverse_staged(const float2* g, int t, c
 //                part (18^3: 3 instead of 4) and gives each scheduler more warps to hide
 //                shared-memory latency.  Its X stage takes the pencils in the bank-spread
 //                order of x_pencil (no bank conflicts where the pitch P differs from n).
-// TMEM columns of a warp: [acc (PPT pencils) | kernel rows (PPT) | owner u_i (PPT)].
+// TMEM columns of a warp: [acc (PPT pencils) | kernel rows (PPT) | owner u_i (PPT) |
+// running sums s, c (PPT, where they fit)].
 // ---------------------------------------------------------------------------------------
 
 // XP: with one pencil per thread, the X-stage pencils go to threads in the bank-spread order
@@ -135,7 +136,16 @@ struct LayoutLin {
   static constexpr bool OK = G::ZFAST_Y == 1 && THREADS <= 1024;
   static constexpr int TAB = PPT * G::ROW;
   static constexpr int OWN = TAB + PPT * n;
-  static constexpr int COLS_PER_WARP = OWN + PPT * G::ROW;
+  // Where the lane quarters have room (the warps sharing one quarter take at most 512
+  // columns), the running sums of the compensated accumulation live in TMEM too: s (ROW
+  // floats) at SUMS + ps ROW and c (n columns of bf16 pairs) at CSUM + ps n.  Elsewhere
+  // (20^3: four warps share a quarter) they live in global memory (PairArgs::comp).
+  static constexpr int BASE = OWN + PPT * G::ROW;
+  static constexpr int SUMCOLS = PPT * (G::ROW + n);
+  static constexpr bool TSUMS = ((THREADS / 32 + 3) / 4) * (BASE + SUMCOLS) <= 512;
+  static constexpr int SUMS = BASE;
+  static constexpr int CSUM = BASE + PPT * G::ROW;
+  static constexpr int COLS_PER_WARP = BASE + (TSUMS ? SUMCOLS : 0);
   static __device__ __forceinline__ int zg(int t, int ps) { return Pencil<n>(t + ps * TS).zg; }
   static __device__ __forceinline__ void z_forward(float2* g, int t, bool valid, const float2* stg, uint32_t trow0) {
     stage_z_forward_staged<n, PPT>(g, t, valid, stg, trow0 + (uint32_t)OWN);
@@ -291,7 +301,12 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
       const uint32_t trow = trow0 + (uint32_t)(ps * G::ROW);
       float acc[G::ROW];
       TmemRow<G::ROW>::load(trow, acc);
-      if constexpr (MODE == MODE_APPLY) {
+      if constexpr (MODE == MODE_APPLY && Lay::TSUMS) {
+        const int zg = Lay::zg(t, ps);
+        fold_group_tmem<n>(acc, trow0 + (uint32_t)(Lay::SUMS + ps * G::ROW), trow0 + (uint32_t)(Lay::CSUM + ps * n),
+                           active ? reinterpret_cast<float4*>(args.out + oofs + zg) : nullptr, folds == 0,
+                           folds == 1, last);
+      } else if constexpr (MODE == MODE_APPLY) {
         if (active) {
           const int zg = Lay::zg(t, ps);
           fold_group<n>(acc, sums, zg / n, reinterpret_cast<float4*>(args.out + oofs + zg), folds == 0, folds == 1,
