@@ -426,7 +426,7 @@ __device__ __forceinline__ char* staged_smem_base(float4* smem4, int* status) {
   return sbase;
 }
 
-// One work item per CTA.  L: the pencil layout (LayoutSeq, LayoutOne or LayoutSplit).
+// One work item per CTA.  L: the pencil layout (LayoutSeq or LayoutOne).
 template <int n, int MODE, template <int> class L>
 __global__ void __launch_bounds__(L<n>::THREADS, 1)
     pairconv_tma_kernel(const PairArgs args, const __grid_constant__ CUtensorMap tmap) {
