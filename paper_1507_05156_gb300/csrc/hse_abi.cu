@@ -104,7 +104,7 @@ __global__ void reduce_splits(float4* __restrict__ out, const float4* __restrict
 static std::atomic<uint64_t> g_launches{0};
 constexpr int kMaxBatchSplit = 4;
 
-// The driver's tensor-map encoder, obtained through the runtime (no link against libcuda).
+// The CUDA driver API's tensor-map encoder, obtained through the runtime (no link against libcuda).
 cudaError_t make_partner_tmap(CUtensorMap* map, const void* base, int n, long long rows, int sp, int box_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
