@@ -331,6 +331,108 @@ def run_profile_case(spec: str):
     print(f"profile case {cell.name}: {cell.pairs} pair convolutions per apply", flush=True)
 
 
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (no measured figure exists for it)
+CONFIGS = ("fp64_12cube", "c64_24cube", "diff_16cube", "batched")
+
+
+def _timed(fn, steps, warmup, stream):
+    """Mean milliseconds of fn() over `steps` calls after `warmup`, CUDA events on `stream`."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_config(name: str, args):
+    """One JSON line for another workload of the method (not the headline bench): the plain FP64
+    form on the 12^3 cell, the 24^3 cell with 8^3 k-points and 16 + 16 bands, the
+    differentiation workload (VJP and backprop through 20 Taylor steps, 16^3, 3^3 k, 8 bands) or
+    the 32-cell uneven batch.  Inputs stay on the device; no L2 flush (each call reads far more
+    than L2 or is timed back to back, as stated in `config`)."""
+    import torch
+    from paper_1507_05156_gb300 import hse, inputs, tdks
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    steps, warmup = max(1, args.steps), max(1, args.warmup)
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic"}
+    if name == "batched":
+        cells = inputs.batched_cells()
+        plan = hse.BatchedPlan(cells)
+        uo = [torch.from_numpy(c.u_occ.astype(np.complex64)).to(dev) for c in cells]
+        oc = [torch.from_numpy(c.occ).to(dev) for c in cells]
+        out = [torch.empty_like(u) for u in uo]
+        ms = _timed(lambda: hse.hse_fock_apply_batched(plan, uo, oc, uo, out=out), steps, warmup, stream)
+        pairs = sum(c.pairs for c in cells)
+        line.update(value=pairs / ms * 1e3, ms_per_step=ms, steps=steps, warmup=warmup, dtype="f32",
+                    config={"workload": "batched_32_uneven_cells", "cells": len(cells), "pairs_per_step": pairs,
+                            "l2": "not flushed (one graph replay per step, back to back)"})
+    elif name in ("fp64_12cube", "c64_24cube"):
+        w = 0 if name == "fp64_12cube" else 2
+        cell = inputs.workload(w)
+        d = torch.complex128 if w == 0 else torch.complex64
+        if w == 2:
+            steps, warmup = min(steps, 2), 1  # about 9 s per apply
+        plan = hse.Plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha, dtype=d)
+        u_occ = torch.from_numpy(cell.u_occ).to(dev, d)
+        u_tgt = torch.from_numpy(cell.u_tgt).to(dev, d)
+        occ = torch.from_numpy(cell.occ).to(dev)
+        out = torch.empty_like(u_tgt)
+        ms = _timed(lambda: hse.hse_fock_apply(plan, u_occ, occ, u_tgt, out=out), steps, warmup, stream)
+        hse.hse_status(plan)
+        flops = algorithmic_flops_per_pair(int(np.prod(cell.grid))) * cell.pairs
+        peak = FP64_NOMINAL_TFLOPS if w == 0 else FP32_PEAK_TFLOPS
+        line.update(value=cell.pairs / ms * 1e3, ms_per_step=ms, steps=steps, warmup=warmup,
+                    dtype="f64" if w == 0 else "f32",
+                    config=dict(config_dict(cell), l2="not flushed" + (" (inputs 2.7 GB > L2)" if w == 2 else "")),
+                    roofline={"bound": "alu", "achieved": flops / ms / 1e9, "peak": peak, "unit": "TFLOP/s",
+                              "frac": flops / ms / 1e9 / peak,
+                              "peak_source": "FP64 nominal" if w == 0 else "FP32 FMA lanes x max SM clock"})
+    elif name == "diff_16cube":
+        cell = inputs.workload(4)
+        res = {}
+        for d, tag in ((torch.complex64, "c64"), (torch.complex128, "c128")):
+            plan = hse.Plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha,
+                            dtype=d)
+            u = torch.from_numpy(cell.u_occ).to(dev, d)
+            occ = torch.from_numpy(cell.occ).to(dev)
+            ybar = (0.5 * u).contiguous()
+            out = torch.empty_like(u)
+            res[f"apply_ms_{tag}"] = _timed(lambda: hse.hse_fock_apply(plan, u, occ, u, out=out), steps, warmup,
+                                            stream)
+            res[f"vjp_ms_{tag}"] = _timed(lambda: hse.hse_fock_apply_vjp(plan, u, occ, u, ybar), steps, warmup,
+                                          stream)
+            res[f"energy_ms_{tag}"] = _timed(lambda: hse.hse_exchange_energy(plan, u, occ), steps, warmup, stream)
+            hse.hse_status(plan)
+        # backprop through 20 Taylor steps (dt = 0.02, E = 0.005 along x), checkpointed, complex64
+        geom = tdks.Geometry(cell.grid, cell.lattice, cell.kpts, alpha=cell.alpha)
+        psi0 = torch.from_numpy(cell.u_occ.astype(np.complex64)).to(dev)
+        occ = torch.from_numpy(cell.occ).to(dev)
+
+        def backprop():
+            psi = psi0.clone().requires_grad_(True)
+            om = torch.tensor(cell.omega, dtype=torch.float64, requires_grad=True)
+            out = tdks.propagate(psi, occ, om, geom, 0.02, 20, (0.005, 0.0, 0.0))
+            loss = (out.conj() * psi0).real.sum()
+            loss.backward()
+
+        res["backprop_20_steps_ms_c64"] = _timed(backprop, 1, 1, stream)
+        line.update(value=cell.pairs / res["vjp_ms_c64"] * 1e3, ms_per_step=res["vjp_ms_c64"], steps=steps,
+                    warmup=warmup, dtype="f32",
+                    config=dict(config_dict(cell), timed="hse_fock_apply_vjp (all three gradients), complex64",
+                                l2="not flushed (inputs 7 MB, calls back to back)"),
+                    **{k: round(v, 4) for k, v in res.items()})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,9 +444,14 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--profile-case", default=None, metavar="N,KM,NB",
                     help="only run two applies of one cell (for ncu captures of secondary kernels)")
+    ap.add_argument("--config", choices=CONFIGS, default=None,
+                    help="time another workload of the method (one JSON line) instead of the bench workload")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args.profile_case)
+        return
+    if args.config:
+        run_config(args.config, args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
