@@ -93,3 +93,16 @@ def test_null_arguments(lib):
     assert lib.hse_fock_apply_vjp(None, None, None, None, None, None, None, None, None) == -1
     assert lib.hse_status(None, None) == -1
     assert lib.hse_plan_destroy(None) == -1
+    assert lib.hse_kinetic_apply(None, None, 1, None, None, None) == -1
+    assert lib.hse_taylor_step(None, None, None, None, 0.1, None, None, None) == -1
+    assert lib.hse_current(None, None, None, None, None, None) == -1
+    assert lib.hse_hartree_potential(None, None, None, None, None) == -1
+    assert lib.hse_overlap(None, None, 1, None, None) == -1
+    assert lib.hse_orthonormalize(None, None, 1, None) == -1
+
+
+def test_error_strings(lib):
+    for code in range(-8, 0):
+        assert lib.hse_strerror(code) != b"unknown error", code
+    assert b"linearly dependent" in lib.hse_strerror(-8)
+    assert hse.ERRORS[-8] == "HSE_ERR_SINGULAR"
