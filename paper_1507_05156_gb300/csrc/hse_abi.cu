@@ -285,6 +285,12 @@ struct hse_plan_s {
   // use, grown when a larger call comes)
   float2* blk_buf = nullptr;
   size_t blk_elems = 0;
+  // MODE_OCC with the omega gradient fused in (allocated on first use): per CTA of a launch
+  // chunk one spectrum of each owner slot, and one FP64 partial per work item
+  float2* spec_buf = nullptr;
+  size_t spec_elems = 0;
+  double* wpartial = nullptr;
+  size_t wpartial_elems = 0;
   // down-sampled Fock sum
   int nkq = 0;                  // k-points of the Fock sum: nk, or nk_occ when sampled
   bool sampled = false;
@@ -320,6 +326,8 @@ struct hse_plan_s {
 };
 
 namespace {
+
+constexpr long long kSpecCtas = 152 * 8;  // CTAs per launch chunk of the fused u_occ / omega pass
 
 int cuda_fail(cudaError_t e) { return e == cudaSuccess ? HSE_OK : (e == cudaErrorMemoryAllocation ? HSE_ERR_NOMEM : HSE_ERR_CUDA); }
 
@@ -434,6 +442,8 @@ int hse_plan_destroy(hse_plan plan) {
   cudaFree(plan->split_buf);
   cudaFree(plan->comp_buf);
   cudaFree(plan->blk_buf);
+  cudaFree(plan->spec_buf);
+  cudaFree(plan->wpartial);
   cudaFree(plan->d_kocc);
   cudaFree(plan->d_kinv);
   cudaFree(plan->u_sub);
@@ -734,7 +744,39 @@ int run_pairconv(hse_plan plan, int mode, PairArgs a, int n_own, cudaStream_t st
     a.split_stride = count;
     if (a.nsplit > 1) a.out = plan->split_buf;
   }
-  cudaError_t e = launch_pairconv_c64(n, mode, a, plan->blocks_per_sm, st);
+  cudaError_t e = cudaSuccess;
+  if (mode == MODE_OCC && a.vtab2) {
+    // the omega gradient fused into the u_occ pass: launches of at most kSpecCtas CTAs, each
+    // CTA with its own spectrum scratch, and one FP64 partial per item
+    const long long items = (long long)a.nsplit * a.nk_own * a.ntiles;
+    const size_t per_cta = (size_t)slots_for(n) * blocked_stride(n);
+    const size_t spec_need = (size_t)std::min<long long>(items, kSpecCtas) * per_cta;
+    if (spec_need > plan->spec_elems) {
+      cudaFree(plan->spec_buf);
+      plan->spec_buf = nullptr;
+      plan->spec_elems = 0;
+      e = cudaMalloc(&plan->spec_buf, spec_need * sizeof(float2));
+      if (e != cudaSuccess) return cuda_fail(e);
+      plan->spec_elems = spec_need;
+    }
+    if ((size_t)items > plan->wpartial_elems) {
+      cudaFree(plan->wpartial);
+      plan->wpartial = nullptr;
+      plan->wpartial_elems = 0;
+      e = cudaMalloc(&plan->wpartial, (size_t)items * sizeof(double));
+      if (e != cudaSuccess) return cuda_fail(e);
+      plan->wpartial_elems = (size_t)items;
+    }
+    a.spec = plan->spec_buf;
+    a.partial2 = plan->wpartial;
+    for (long long c0 = 0; c0 < items && e == cudaSuccess; c0 += kSpecCtas) {
+      a.item0 = (int)c0;
+      a.item_count = (int)std::min<long long>(kSpecCtas, items - c0);
+      e = launch_pairconv_c64(n, mode, a, plan->blocks_per_sm, st);
+    }
+  } else {
+    e = launch_pairconv_c64(n, mode, a, plan->blocks_per_sm, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e);
   if ((mode == MODE_APPLY || mode == MODE_OCC) && a.nsplit > 1) {
     const size_t count4 = count / 2;  // N is even: whole float4 pairs
@@ -784,8 +826,8 @@ int scatter_occ_grad(hse_plan plan, void* grad_u_occ, cudaStream_t st) {
   return cuda_fail(cudaGetLastError());
 }
 
-int reduce(hse_plan plan, int n, double factor, double* out, cudaStream_t st) {
-  reduce_partials<<<1, 1024, 0, st>>>(plan->partial, n, factor, out);
+int reduce(hse_plan plan, int n, double factor, double* out, cudaStream_t st, const double* src = nullptr) {
+  reduce_partials<<<1, 1024, 0, st>>>(src ? src : plan->partial, n, factor, out);
   count_launch();
   return cuda_fail(cudaGetLastError());
 }
@@ -1064,7 +1106,10 @@ int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, cons
     rc = run_pairconv(plan, MODE_APPLY, a, p.n_tgt, st);
     if (rc) return rc;
   }
-  if (grad_omega) {
+  // with both, the omega gradient rides on the u_occ pass's transforms (Parseval); alone it
+  // takes a pass of its own
+  const bool fuse_w = grad_omega && grad_u_occ;
+  if (grad_omega && !fuse_w) {
     PairArgs a = base_args(plan);
     a.own = (const float2*)u_tgt;
     a.part = (const float2*)u_rows;
@@ -1089,7 +1134,13 @@ int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, cons
     a.nk_own = plan->nkq;
     a.nk_part = p.nk;
     a.n_part = p.n_tgt;
+    if (fuse_w) a.vtab2 = plan->dv32;
     rc = run_pairconv(plan, MODE_OCC, a, p.n_occ, st);
+    if (rc == HSE_OK && fuse_w) {
+      const int T = slots_for(p.grid[0]);
+      const int items = plan->nsplit[ROLE_OCC] * plan->nkq * ((p.n_occ + T - 1) / T);
+      rc = reduce(plan, items, 1.0, grad_omega, st, plan->wpartial);
+    }
     if (rc == HSE_OK && plan->sampled) rc = scatter_occ_grad(plan, grad_u_occ, st);
   }
   return rc;

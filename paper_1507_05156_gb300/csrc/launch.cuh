@@ -106,7 +106,8 @@ template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT>
 cudaError_t launch_pairconv_variant(const PairArgs& args, cudaStream_t stream) {
   cudaError_t err = pairconv_set_attr<n, MODE, MINB, PPT, TSX>();
   if (err != cudaSuccess) return err;
-  const dim3 grid((unsigned)((size_t)args.nsplit * args.nk_own * args.ntiles));
+  const dim3 grid(args.item_count > 0 ? (unsigned)args.item_count
+                                      : (unsigned)((size_t)args.nsplit * args.nk_own * args.ntiles));
   pairconv_c64_kernel<n, MODE, MINB, PPT, TSX>
       <<<grid, GeoP<n, PPT, TSX>::THREADS, pairconv_smem_bytes<n>(), stream>>>(args);
   count_launch();

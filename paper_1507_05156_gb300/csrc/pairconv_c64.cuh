@@ -132,6 +132,14 @@ struct PairArgs {
   float2* comp;         // APPLY / OCC: running sums s, c of the compensated accumulation: per
                         // owner orbital of each split, s then c in the pencil-blocked layout
                         // (2 OrbBlk::NBK complex), owners in the order of out
+  // MODE_OCC with the omega gradient fused in (vtab2 non-null): the rows d v / d omega (scaled
+  // like vtab), one FP64 partial per item, and per CTA of the launch one spectrum of each owner
+  // slot (T blocked grids, float2) kept from the first chain to the second.
+  const float* vtab2;
+  double* partial2;
+  float2* spec;
+  int item0;            // pencil-load launches: items item0 .. item0 + item_count - 1
+  int item_count;       // (0: all items)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -443,6 +451,56 @@ __device__ __forceinline__ void stage_x(float2* g, int t, bool valid, uint32_t t
   }
 }
 
+// Stage X of the two chains of MODE_OCC with the omega gradient fused in (Sec. II C, the
+// derivative of Eq. "Fock" with respect to omega).  With A = F(conj(u_j) u_i) and
+// B = F(conj(u_j) ybar_i) the unnormalised spectra the first and second chain reach here,
+//   Re sum_r conj(ybar_i) u_j K'_q(conj(u_j) u_i) (scaled by -alpha f / (N_k N))
+//     = Re sum_G dvs(G) f A(G) conj(B(G))   (Parseval; dvs = d v / d omega * scale),
+// the term the separate omega pass computes in real space.  SPEC = 1 (first chain) stores A
+// per X pencil in the pencil-blocked layout at spec; SPEC = 2 (second chain) reads it back and
+// adds the sum to dsum.  Otherwise as stage_x.
+template <int n, int SPEC, int PPT = 2, int TS = Geo<n>::NN / PPT>
+__device__ __forceinline__ void stage_x_occ(float2* g, int t, bool valid, uint32_t ttab, float f, float2* spec,
+                                            const float* __restrict__ dvrow, float dscale, double& dsum) {
+  using G = Geo<n>;
+#pragma unroll 1
+  for (int ps = 0; ps < PPT; ++ps) {
+    if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
+    const int p = t + ps * TS;
+    const Pencil<n> pc(p);
+    float tv[n];
+    TmemRow<n>::load(ttab + (uint32_t)(ps * n), tv);
+    cpx<float> v[n];
+    load_s<n, 1>(v, g, pc.xs, G::Q);
+    fft<n, -1, float>(v);
+    float4* s4 = reinterpret_cast<float4*>(spec) + (size_t)(p >> 5) * (n / 2) * 32 + (p & 31);
+    if constexpr (SPEC == 1) {
+      if (valid) {
+#pragma unroll
+        for (int e = 0; e < n / 2; ++e) s4[32 * e] = make_float4(v[2 * e].x, v[2 * e].y, v[2 * e + 1].x, v[2 * e + 1].y);
+      }
+    } else {
+      float d = 0.f;
+#pragma unroll
+      for (int e = 0; e < n / 2; ++e) {
+        const float4 a = s4[32 * e];
+        const float w0 = __ldg(dvrow + (2 * e) * G::NN + p), w1 = __ldg(dvrow + (2 * e + 1) * G::NN + p);
+        d = fmaf(w0, fmaf(a.x, v[2 * e].x, a.y * v[2 * e].y), d);
+        d = fmaf(w1, fmaf(a.z, v[2 * e + 1].x, a.w * v[2 * e + 1].y), d);
+      }
+      if (valid) dsum += (double)d * (double)(dscale * f);
+    }
+#pragma unroll
+    for (int e = 0; e < n; ++e) {
+      const float w = tv[e] * f;
+      v[e].x *= w;
+      v[e].y *= w;
+    }
+    fft<n, +1, float>(v);
+    if (valid) store_s<n, 1>(v, g, pc.xs, G::Q);
+  }
+}
+
 // Kernel row v(|G+q|) * scale of this thread's PPT X-pencils into the TMEM cache.
 template <int n, int PPT = 2, bool XP = false, int XR = n * n, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void cache_kernel_row(int t, uint32_t ttab, const float* __restrict__ vrow, float scale) {
@@ -534,13 +592,27 @@ __device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32
   __syncthreads();
 }
 
+// The same with stage_x_occ (MODE_OCC with the omega gradient fused in).
+template <int n, int SPEC, int PPT = 2, int TS = Geo<n>::NN / PPT>
+__device__ __forceinline__ void pair_middle_occ(float2* g, int t, bool valid, uint32_t ttab, float f, float2* spec,
+                                                const float* dvrow, float dscale, double& dsum, bool warp_on) {
+  __syncthreads();
+  if (warp_on) stage_y<n, -1, PPT, TS>(g, t, valid);
+  __syncthreads();
+  if (warp_on) stage_x_occ<n, SPEC, PPT, TS>(g, t, valid, ttab, f, spec, dvrow, dscale, dsum);
+  __syncthreads();
+  if (warp_on) stage_y<n, +1, PPT, TS>(g, t, valid);
+  __syncthreads();
+}
+
 // One work item `item` = (split, k, tile) of a launch.  The CTA may have more threads than
 // the item needs (the batched kernel runs every grid side in one block shape): warps with
 // warp_on == false skip all work and TMEM traffic but pass every barrier.  tbase: the CTA's
 // TMEM allocation, at least Geo<n>::TMEM_COLS columns for this block's warp count.
+// spec: this CTA's spectrum scratch (T blocked grids) when args.vtab2 is set (MODE_OCC).
 template <int n, int MODE, int PPT = 2, int TSX = Geo<n>::NN / PPT>
 __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, float4* smem4, uint32_t tbase,
-                                              bool warp_on) {
+                                              bool warp_on, float2* spec = nullptr) {
   using G = Geo<n>;
   using GP = GeoP<n, PPT, TSX>;
   constexpr int TS = GP::TS;
@@ -615,9 +687,15 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
   if (kp_begin == kp_end) fold(true, false, true);  // an empty k' range: zeros
   const int fspan = fold_span(args.n_part);
 
+  // MODE_OCC with the omega gradient fused in: this slot's spectrum scratch and FP64 sum
+  const bool fuse_w = MODE == MODE_OCC && args.vtab2 != nullptr && spec != nullptr;
+  float2* spec_slot = fuse_w ? spec + (size_t)slot * OrbBlk<n>::NBK : nullptr;
+  double wsum = 0.0;
+
   for (int kp = kp_begin; kp < kp_end; ++kp) {
     // q = k_i - k_j: APPLY-like modes own i (at k) and pair with j at kp; OCC owns j (at k)
     const int qrow = (MODE == MODE_OCC) ? args.qidx[kp * args.nk_own + k] : args.qidx[k * args.nk_part + kp];
+    const float* dvrow = fuse_w ? args.vtab2 + (size_t)qrow * G::N : nullptr;
     if (warp_on) cache_kernel_row<n, PPT, false, n * n, TS>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
     for (int j = 0; j < args.n_part; ++j) {
       const float2* part = args.part + ((size_t)kp * args.n_part + j) * ostr;
@@ -632,17 +710,38 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
         const float2* ybar = args.part2 + ((size_t)kp * args.n_part + j) * ostr;
         // chain 1: rho = conj(u_j) u_i -> phi;  acc += conj(phi) ybar_i
         if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, own, part, blk);
-        pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
+        if (fuse_w)
+          pair_middle_occ<n, 1, PPT, TS>(g, t, valid, ttab, f, spec_slot, dvrow, args.scale, wsum, warp_on);
+        else
+          pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
         if (warp_on) stage_z_inverse<n, EPI_CONJPHI, PPT, TS>(g, t, ybar, trow0, blk);
         // chain 2: sigma = conj(u_j) ybar_i -> psibar;  acc += u_i conj(psibar)
         if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, own, ybar, blk);
-        pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
+        if (fuse_w)
+          pair_middle_occ<n, 2, PPT, TS>(g, t, valid, ttab, f, spec_slot, dvrow, args.scale, wsum, warp_on);
+        else
+          pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
         if (warp_on) stage_z_inverse<n, EPI_WCONJ, PPT, TS>(g, t, part, trow0, blk);
       }
     }
     // the end of a fold group (fold_span k-points) or of the item's k' range
     const int grp = (kp - kp_begin) / fspan;
     if (kp == kp_end - 1 || (kp - kp_begin + 1) % fspan == 0) fold(grp == 0, grp == 1, kp == kp_end - 1);
+  }
+
+  if constexpr (MODE == MODE_OCC) {
+    if (fuse_w) {  // the item's share of d/d omega, one FP64 partial
+      __syncthreads();  // the grid buffers are free now; reuse them for the per-thread sums
+      double* red = reinterpret_cast<double*>(smem4);
+      red[tid] = (active && warp_on) ? wsum : 0.0;  // slots past the last band repeat band 0
+      __syncthreads();
+      if (tid == 0) {
+        double sum = 0.0;
+        for (int e = 0; e < (int)blockDim.x; ++e) sum += red[e];
+        args.partial2[item] = sum;
+      }
+      __syncthreads();
+    }
   }
 
   if constexpr (MODE == MODE_ENERGY || MODE == MODE_DOT) {
@@ -675,7 +774,9 @@ __global__ void __launch_bounds__(GeoP<n, PPT, TSX>::THREADS, MINB) pairconv_c64
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tbase = tmem_base_sh;
-  pairconv_item<n, MODE, PPT, TSX>(args, blockIdx.x, smem4, tbase, true);
+  // one spectrum scratch (T blocked grids) per CTA of the launch, for MODE_OCC with omega
+  float2* spec = args.spec ? args.spec + (size_t)blockIdx.x * Geo<n>::T * OrbBlk<n>::NBK : nullptr;
+  pairconv_item<n, MODE, PPT, TSX>(args, args.item0 + (int)blockIdx.x, smem4, tbase, true, spec);
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
