@@ -36,7 +36,12 @@ def test_omega_gradient_fused_and_alone(n, nk, n_occ, n_tgt):
     _, _, g_alone = hse.hse_fock_apply_vjp(*args, need_occ=False, need_tgt=False)
     hse.hse_status(plan)
     r_occ, _, r_om = oracle.fock_apply_vjp(u_occ, occ, u_tgt, ybar, kpts, lattice, grid, inputs.OMEGA, inputs.ALPHA)
-    assert abs(g_fused.item() - r_om) <= 1e-5 * abs(r_om)
-    assert abs(g_alone.item() - r_om) <= 1e-5 * abs(r_om)
+    # d/d omega = Re <ybar, (d V_x / d omega) u_tgt> sums terms of both signs; FP32 errors scale
+    # with the Cauchy-Schwarz bound ||ybar|| ||(d V_x / d omega) u_tgt||, not with the sum
+    dy = oracle.fock_apply(u_occ, occ, u_tgt, kpts, lattice, grid, inputs.OMEGA, inputs.ALPHA, kernel="domega")
+    scale = np.linalg.norm(ybar) * np.linalg.norm(dy)
+    assert abs(r_om) <= scale
+    assert abs(g_fused.item() - r_om) <= 1e-5 * scale
+    assert abs(g_alone.item() - r_om) <= 1e-5 * scale
     g_occ = g_occ.cpu().numpy()
     assert np.linalg.norm(g_occ - r_occ) <= 1e-5 * np.linalg.norm(r_occ)
