@@ -20,11 +20,14 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/hse_fock.h"
 #include "launch.cuh"
@@ -329,6 +332,20 @@ namespace {
 
 constexpr long long kSpecCtas = 152 * 8;  // CTAs per launch chunk of the fused u_occ / omega pass
 
+// NVTX range over one entry point (visible in Nsight Systems timelines; free without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// HSE_LOG=1: plan and autotune decisions on stderr
+bool log_on() {
+  const char* env = std::getenv("HSE_LOG");
+  return env && std::atoi(env) != 0;
+}
+
 int cuda_fail(cudaError_t e) { return e == cudaSuccess ? HSE_OK : (e == cudaErrorMemoryAllocation ? HSE_ERR_NOMEM : HSE_ERR_CUDA); }
 
 bool invert3(const double* A, double* inv) {
@@ -460,6 +477,7 @@ int hse_plan_destroy(hse_plan plan) {
 }
 
 int hse_plan_create(hse_plan* out, const hse_problem* p) {
+  const NvtxRange nvtx_range("hse_plan_create");
   if (!out) return HSE_ERR_INVALID_ARG;
   *out = nullptr;
   int rc = validate_problem(p);
@@ -641,6 +659,17 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   HSE_TRY(cudaGetLastError());
   HSE_TRY(cudaDeviceSynchronize());
 #undef HSE_TRY
+  if (log_on()) {
+    const bool c64 = p->dtype == HSE_C64;
+    std::fprintf(stderr,
+                 "hse: plan grid %dx%dx%d %s nk %d (Fock sum over %d) n_occ %d n_tgt %d: %d distinct q; "
+                 "k' splits target %d energy %d occupied %d; apply kernel %s; pencil-blocked copies %s\n",
+                 n1, n2, n3, c64 ? "complex64" : "complex128", nk, nkq, p->n_occ, p->n_tgt, plan->nq,
+                 plan->nsplit[ROLE_TGT], plan->nsplit[ROLE_ENERGY], plan->nsplit[ROLE_OCC],
+                 !c64 ? "staged FP64" : (pairconv_c64_pencil_load(n1, MODE_APPLY, plan->blocks_per_sm) ? "pencil-load"
+                                                                                                    : "staged-partner"),
+                 plan->blocked ? "on" : "off");
+  }
   *out = plan;
   return HSE_OK;
 }
@@ -1005,6 +1034,7 @@ extern "C" {
 
 int hse_fock_apply(hse_plan plan, const void* u_occ, const double* occ, const void* u_tgt, void* vx_out,
                    hse_stream_t stream) {
+  const NvtxRange nvtx_range("hse_fock_apply");
   if (!plan || !u_occ || !occ || !u_tgt || !vx_out) return HSE_ERR_INVALID_ARG;
   const hse_problem& p = plan->p;
   if (!aligned16(u_occ) || !aligned16(u_tgt) || !aligned16(vx_out)) return HSE_ERR_INVALID_ARG;
@@ -1033,6 +1063,7 @@ int hse_fock_apply(hse_plan plan, const void* u_occ, const double* occ, const vo
 }
 
 int hse_exchange_energy(hse_plan plan, const void* u_occ, const double* occ, double* e_x, hse_stream_t stream) {
+  const NvtxRange nvtx_range("hse_exchange_energy");
   if (!plan || !u_occ || !occ || !e_x) return HSE_ERR_INVALID_ARG;
   const hse_problem& p = plan->p;
   if (!aligned16(u_occ)) return HSE_ERR_INVALID_ARG;
@@ -1067,6 +1098,7 @@ int hse_exchange_energy(hse_plan plan, const void* u_occ, const double* occ, dou
 
 int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, const void* u_tgt, const void* grad_vx,
                        void* grad_u_occ, void* grad_u_tgt, double* grad_omega, hse_stream_t stream) {
+  const NvtxRange nvtx_range("hse_fock_apply_vjp");
   if (!plan || !u_occ || !occ || !u_tgt || !grad_vx) return HSE_ERR_INVALID_ARG;
   const hse_problem& p = plan->p;
   if (!aligned16(u_occ) || !aligned16(u_tgt) || !aligned16(grad_vx) || (grad_u_occ && !aligned16(grad_u_occ)) ||
@@ -1147,6 +1179,7 @@ int hse_fock_apply_vjp(hse_plan plan, const void* u_occ, const double* occ, cons
 }
 
 int hse_kinetic_apply(hse_plan plan, const void* u, int nbands, const double* A, void* out, hse_stream_t stream) {
+  const NvtxRange nvtx_range("hse_kinetic_apply");
   if (!plan || !u || !out || !A || nbands < 1) return HSE_ERR_INVALID_ARG;
   for (int c = 0; c < 3; ++c)
     if (!std::isfinite(A[c])) return HSE_ERR_INVALID_ARG;
@@ -1174,6 +1207,7 @@ int hse_kinetic_apply(hse_plan plan, const void* u, int nbands, const double* A,
 
 int hse_taylor_step(hse_plan plan, const void* psi, const double* occ, const double* A, double dt, const double* vloc,
                     void* psi_out, hse_stream_t stream) {
+  const NvtxRange nvtx_range("hse_taylor_step");
   if (!plan || plan->batched || !psi || !occ || !A || !psi_out || !std::isfinite(dt)) return HSE_ERR_INVALID_ARG;
   const hse_problem& p = plan->p;
   if (p.n_tgt != p.n_occ) return HSE_ERR_INVALID_ARG;  // the step propagates the occupied set
@@ -1208,6 +1242,7 @@ int hse_taylor_step(hse_plan plan, const void* psi, const double* occ, const dou
 }
 
 int hse_current(hse_plan plan, const void* psi, const double* occ, const double* A, double* J, hse_stream_t stream) {
+  const NvtxRange nvtx_range("hse_current");
   if (!plan || plan->batched || !psi || !occ || !A || !J) return HSE_ERR_INVALID_ARG;
   for (int c = 0; c < 3; ++c)
     if (!std::isfinite(A[c])) return HSE_ERR_INVALID_ARG;
@@ -1233,6 +1268,7 @@ int hse_current(hse_plan plan, const void* psi, const double* occ, const double*
 }
 
 int hse_overlap(hse_plan plan, const void* u, int nbands, double* s_out, hse_stream_t stream) {
+  const NvtxRange nvtx_range("hse_overlap");
   if (!plan || plan->batched || !u || !s_out || nbands < 1 || nbands > 4096 || plan->p.nk > 65535)
     return HSE_ERR_INVALID_ARG;
   if (!aligned16(u) || !aligned16(s_out)) return HSE_ERR_INVALID_ARG;
@@ -1243,6 +1279,7 @@ int hse_overlap(hse_plan plan, const void* u, int nbands, double* s_out, hse_str
 }
 
 int hse_orthonormalize(hse_plan plan, void* u, int nbands, hse_stream_t stream) {
+  const NvtxRange nvtx_range("hse_orthonormalize");
   if (!plan || plan->batched || !u || nbands < 1 || nbands > 4096) return HSE_ERR_INVALID_ARG;
   if (!aligned16(u)) return HSE_ERR_INVALID_ARG;
   const hse_problem& p = plan->p;
@@ -1260,6 +1297,7 @@ int hse_orthonormalize(hse_plan plan, void* u, int nbands, hse_stream_t stream) 
 }
 
 int hse_hartree_potential(hse_plan plan, const void* psi, const double* occ, double* vh, hse_stream_t stream) {
+  const NvtxRange nvtx_range("hse_hartree_potential");
   if (!plan || plan->batched || !psi || !occ || !vh) return HSE_ERR_INVALID_ARG;
   if (!aligned16(psi)) return HSE_ERR_INVALID_ARG;
   const hse_problem& p = plan->p;
@@ -1279,6 +1317,7 @@ int hse_hartree_potential(hse_plan plan, const void* psi, const double* occ, dou
 }
 
 int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells) {
+  const NvtxRange nvtx_range("hse_plan_create_batched");
   if (!out) return HSE_ERR_INVALID_ARG;
   *out = nullptr;
   if (!cells || ncells < 1 || ncells > 65536) return HSE_ERR_INVALID_ARG;
@@ -1338,6 +1377,7 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
 
 int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double* const* occ, const void* const* u_tgt,
                            void* const* vx_out, hse_stream_t stream) {
+  const NvtxRange nvtx_range("hse_fock_apply_batched");
   if (!plan || !plan->batched || !u_occ || !occ || !u_tgt || !vx_out) return HSE_ERR_INVALID_ARG;
   const int ncells = (int)plan->cells.size();
   for (int c = 0; c < ncells; ++c) {
@@ -1433,11 +1473,14 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
         best_ms = ms;
         best = cands[ci];
       }
+      if (e == cudaSuccess && log_on())
+        std::fprintf(stderr, "hse: batched autotune: k' split %d: %.3f ms\n", cands[ci], ms);
     }
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     if (e != cudaSuccess) return cuda_fail(e);
     plan->batch_split = best;
+    if (log_on()) std::fprintf(stderr, "hse: batched autotune: chose k' split %d\n", best);
     build_batch(plan, best, vx_out);
     // capture counter reset + persistent kernels + split reduction as one graph
     cudaGraph_t g = nullptr;
