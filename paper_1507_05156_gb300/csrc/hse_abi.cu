@@ -25,6 +25,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -344,6 +345,54 @@ struct NvtxRange {
 bool log_on() {
   const char* env = std::getenv("HSE_LOG");
   return env && std::atoi(env) != 0;
+}
+
+// Autotune cache (HSE_AUTOTUNE_CACHE=<file>): one line "<key>\t<k' split>" per batched
+// problem, the key naming the GPU and every cell (grid side, k-points, bands).  Missing or
+// unreadable files simply mean "not cached"; a failed write is ignored.
+const char* autotune_path() {
+  const char* p = std::getenv("HSE_AUTOTUNE_CACHE");
+  return (p && *p) ? p : nullptr;
+}
+
+std::string autotune_key(hse_plan plan) {
+  cudaDeviceProp prop{};
+  std::string k = cudaGetDeviceProperties(&prop, plan->device) == cudaSuccess ? prop.name : "gpu";
+  for (hse_plan c : plan->cells) {
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "|%dx%dx%d,nk%d,o%d,t%d", c->p.grid[0], c->p.grid[1], c->p.grid[2], c->p.nk,
+                  c->p.n_occ, c->p.n_tgt);
+    k += buf;
+  }
+  return k;
+}
+
+int autotune_lookup(const std::string& key) {
+  const char* path = autotune_path();
+  if (!path) return 0;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return 0;
+  int found = 0;
+  std::vector<char> line(1 << 16);
+  while (std::fgets(line.data(), (int)line.size(), f)) {
+    const char* tab = std::strchr(line.data(), '\t');
+    if (!tab) continue;
+    if ((size_t)(tab - line.data()) == key.size() && std::strncmp(line.data(), key.data(), key.size()) == 0) {
+      const int v = std::atoi(tab + 1);
+      if (v == 1 || v == 2 || v == 4) found = v;  // the last entry for the key wins
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void autotune_store(const std::string& key, int split) {
+  const char* path = autotune_path();
+  if (!path || key.size() + 16 > (1 << 16)) return;
+  if (FILE* f = std::fopen(path, "a")) {
+    std::fprintf(f, "%s\t%d\n", key.c_str(), split);
+    std::fclose(f);
+  }
 }
 
 int cuda_fail(cudaError_t e) { return e == cudaSuccess ? HSE_OK : (e == cudaErrorMemoryAllocation ? HSE_ERR_NOMEM : HSE_ERR_CUDA); }
@@ -1453,14 +1502,19 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
   }
   cudaError_t e = cudaSuccess;
   if (plan->batch_split == 0) {
-    // autotune the k'-split granularity of the work items on this first call
+    // autotune the k'-split granularity of the work items on this first call, unless the
+    // autotune cache (HSE_AUTOTUNE_CACHE) already holds a choice for this GPU and cell list
+    const std::string key = autotune_key(plan);
+    const int cached = autotune_lookup(key);
     float best_ms = 0.f;
-    int best = 1;
+    int best = cached > 0 ? cached : 1;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
-    e = cudaEventCreate(&t0);
-    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    if (cached <= 0) {
+      e = cudaEventCreate(&t0);
+      if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    }
     const int cands[3] = {1, 2, 4};
-    for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
+    for (int ci = 0; ci < (cached > 0 ? 0 : 3) && e == cudaSuccess; ++ci) {
       build_batch(plan, cands[ci], vx_out);
       e = cudaMemcpyAsync(plan->d_cells, plan->h_cells.data(), ncells * sizeof(BatchCell), cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess) e = cudaEventRecord(t0, st);
@@ -1479,6 +1533,11 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     if (e != cudaSuccess) return cuda_fail(e);
+    if (cached > 0) {
+      if (log_on()) std::fprintf(stderr, "hse: batched autotune: k' split %d from the cache\n", cached);
+    } else {
+      autotune_store(key, best);
+    }
     plan->batch_split = best;
     if (log_on()) std::fprintf(stderr, "hse: batched autotune: chose k' split %d\n", best);
     build_batch(plan, best, vx_out);

@@ -61,3 +61,23 @@ def test_uneven_batch_32_cells_matches_single_cell_path():
         ref = oracle.fock_apply(u64, c.occ, u64, c.kpts, c.lattice, c.grid, c.omega, c.alpha, targets=targets)
         got = np.stack([out[i][k, b].cpu().numpy() for k, b in targets])
         assert rel(got, ref) <= 1e-5
+
+
+def test_autotune_cache_round_trip(tmp_path, monkeypatch):
+    """HSE_AUTOTUNE_CACHE: the first batched plan times the candidate k' splits and stores its
+    choice under a key naming the GPU and the cells; a second plan with the same cells reads it
+    back (no timing runs) and computes the same result."""
+    cache = tmp_path / "autotune.tsv"
+    monkeypatch.setenv("HSE_AUTOTUNE_CACHE", str(cache))
+    cells = inputs.batched_cells(4)
+    uo = [torch.from_numpy(c.u_occ.astype(np.complex64)).cuda() for c in cells]
+    oc = [torch.from_numpy(c.occ).cuda() for c in cells]
+    first = hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)
+    torch.cuda.synchronize()
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].split("\t")[1] in ("1", "2", "4")
+    second = hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)
+    torch.cuda.synchronize()
+    assert cache.read_text().splitlines() == lines  # served from the cache, nothing appended
+    for a, b in zip(first, second):
+        assert torch.equal(a, b)
