@@ -132,7 +132,11 @@ int hse_fock_apply_vjp(hse_plan plan, const void *u_occ, const double *occ, cons
                        double *grad_omega, hse_stream_t stream);
 
 /* Batched V_x for a plan from hse_plan_create_batched: arrays of ncells HOST-side
- * pointers, each to that cell's device buffers (same layouts as hse_fock_apply). */
+ * pointers, each to that cell's device buffers (same layouts as hse_fock_apply).  The first
+ * call times three k'-split granularities of the work items (synchronising the stream) and
+ * captures the chosen launch as a CUDA graph, which later calls replay; with the environment
+ * variable HSE_AUTOTUNE_CACHE naming a file, the choice is stored there per GPU and cell list
+ * and read back by later plans instead of timing. */
 int hse_fock_apply_batched(hse_plan plan, const void *const *u_occ, const double *const *occ,
                            const void *const *u_tgt, void *const *vx_out, hse_stream_t stream);
 
