@@ -39,7 +39,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic of one launch of the fused 20^3 kernel from an ncu capture, valid only while
 # the kernel sources hash to the value recorded with it (else reported as null).
-TRAFFIC = {"sha": "3f28eb74bdf57d10", "bytes_per_launch": 1070.742272e6}
+TRAFFIC = {"sha": "e36fb2317e0dddf9", "bytes_per_launch": 1073.175808e6}
 
 
 def _code_only(src: str) -> str:
@@ -364,7 +364,16 @@ def run_profile_case(spec: str):
 
 
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (no measured figure exists for it)
-CONFIGS = ("fp64_12cube", "c64_24cube", "diff_16cube", "batched")
+
+
+def _measured_peak(key: str):
+    """A figure of MEASURED_PEAKS.json at the repository root, or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json"), encoding="utf-8") as fh:
+            return float(json.load(fh)[key])
+    except (OSError, KeyError, ValueError, TypeError):
+        return None
+CONFIGS = ("fp64_12cube", "c64_24cube", "c64_24cube_tc", "diff_16cube", "batched")
 
 
 def _timed(fn, steps, warmup, stream):
@@ -386,7 +395,7 @@ def run_config(name: str, args):
     """One JSON line for another workload of the method (not the headline bench): the plain FP64
     form on the 12^3 cell, the 24^3 cell with 8^3 k-points and 16 + 16 bands, the
     differentiation workload (VJP and backprop through 20 Taylor steps, 16^3, 3^3 k, 8 bands) or
-    the 32-cell uneven batch.  Inputs stay on the device; no L2 flush (each call reads far more
+    the 32-cell uneven batch; c64_24cube_tc is the 24^3 workload on the tensor-core option.  Inputs stay on the device; no L2 flush (each call reads far more
     than L2 or is timed back to back, as stated in `config`)."""
     import torch
     from paper_1507_05156_gb300 import hse, inputs, tdks
@@ -407,13 +416,15 @@ def run_config(name: str, args):
         line.update(value=pairs / ms * 1e3, ms_per_step=ms, steps=steps, warmup=warmup, dtype="f32",
                     config={"workload": "batched_32_uneven_cells", "cells": len(cells), "pairs_per_step": pairs,
                             "l2": "not flushed (one graph replay per step, back to back)"})
-    elif name in ("fp64_12cube", "c64_24cube"):
+    elif name in ("fp64_12cube", "c64_24cube", "c64_24cube_tc"):
         w = 0 if name == "fp64_12cube" else 2
+        tc = name == "c64_24cube_tc"
         cell = inputs.workload(w)
         d = torch.complex128 if w == 0 else torch.complex64
         if w == 2:
             steps, warmup = min(steps, 2), 1  # about 9 s per apply
-        plan = hse.Plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha, dtype=d)
+        plan = hse.Plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha, dtype=d,
+                        tensor_cores=tc)
         u_occ = torch.from_numpy(cell.u_occ).to(dev, d)
         u_tgt = torch.from_numpy(cell.u_tgt).to(dev, d)
         occ = torch.from_numpy(cell.occ).to(dev)
@@ -428,6 +439,18 @@ def run_config(name: str, args):
                     roofline={"bound": "alu", "achieved": flops / ms / 1e9, "peak": peak, "unit": "TFLOP/s",
                               "frac": flops / ms / 1e9 / peak,
                               "peak_source": "FP64 nominal" if w == 0 else "FP32 FMA lanes x max SM clock"})
+        if tc:
+            # executed tensor work: four of the six axis transforms (Y and X, both directions)
+            # as (2n)-wide real GEMMs, three split products each, per pair
+            n = cell.grid[0]
+            tflop = 4 * n * n * 3 * (2 * n) ** 2 * 2 * cell.pairs / ms / 1e9
+            peak_tc = _measured_peak("bf16_tflops")
+            line["config"]["tensor_cores"] = "Y and X transforms as split-FP16 mma.sync GEMMs"
+            line["roofline_alu_algorithmic"] = line["roofline"]
+            line["roofline"] = {"bound": "tensor", "achieved": tflop, "peak": peak_tc, "unit": "TFLOP/s",
+                                "frac": tflop / peak_tc if peak_tc else None,
+                                "peak_source": "measured bf16 dense (FP16 same nominal rate)",
+                                "note": "executed FP16 tensor flops of the Y/X GEMMs only"}
     elif name == "diff_16cube":
         cell = inputs.workload(4)
         res = {}

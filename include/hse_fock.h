@@ -57,6 +57,12 @@ extern "C" {
 /* Arithmetic of the pair convolutions. */
 #define HSE_C64   0  /* complex64 orbitals, fused FP32 kernel, FP64 energy/omega reduction */
 #define HSE_C128  1  /* complex128 orbitals, plain staged FP64 kernels                     */
+/* complex64 orbitals (as HSE_C64), the Y and X axis transforms of V_x u and E_x as split-FP16
+ * tensor-core GEMMs (hi/lo halves, three products, FP32 accumulation), the Z transforms and
+ * every other step as HSE_C64; 24^3 grids only (else HSE_ERR_UNSUPPORTED_GRID).  The VJP's
+ * u_occ pass runs the FP32 kernel.  Errors against FP64 stay within 1e-5 but are larger than
+ * HSE_C64's, and the FP32 kernel is faster on GB300; an option for study. */
+#define HSE_C64_TC 2
 
 typedef void *hse_stream_t;  /* a cudaStream_t */
 
@@ -72,7 +78,7 @@ typedef struct {
   double omega;           /* range separation (bohr^-1), > 0; the paper's mu                     */
   double alpha;           /* Fock mixing fraction, 0.25 in HSE                                   */
   double spin_degeneracy; /* g_s in E_x (2 for a closed shell); not used by V_x                  */
-  int dtype;              /* HSE_C64 or HSE_C128                                                 */
+  int dtype;              /* HSE_C64, HSE_C128 or HSE_C64_TC                                     */
   /* Down-sampled Fock sum (Sec. II C, after Eq. "Fock-DS"): the sum over the occupied
    * orbitals' k-points k' runs over nk_occ of the nk points, kocc[0..nk_occ) (HOST, distinct
    * indices into kpts, copied at plan creation), with the weight 1/nk_occ in place of 1/nk.

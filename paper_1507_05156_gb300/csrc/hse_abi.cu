@@ -279,7 +279,9 @@ struct hse_plan_s {
   size_t work_pairs = 0;
   double2* vx64 = nullptr;   // [nk][max(n_occ, n_tgt)][N]
   bool blocked = true;       // pencil-load launches read pencil-blocked copies (HSE_PENCIL_BLOCKS=0: no)
-  int blocks_per_sm = 0;     // fused-kernel variant: 0 default, -1/-2 staged-partner layouts, 1/2/3 pencil loads
+  int blocks_per_sm = 0;     // fused-kernel variant: 0 default, -1/-2 staged-partner layouts, 1/2/3 pencil loads,
+                             // kTcVariant the tensor-core form (HSE_C64_TC)
+  bool tc = false;           // created as HSE_C64_TC (p.dtype then reads HSE_C64)
   int inject = 0;            // test hook (HSE_INJECT_SKIP_FILL=1 at plan creation)
   int nsplit[3] = {1, 1, 1};  // k'-loop splits of the fused kernel per OwnerRole
   float2* split_buf = nullptr;  // [nsplit][nk_own][n_own][N] partial outputs when nsplit > 1
@@ -416,7 +418,7 @@ size_t elem_bytes(int dtype) { return dtype == HSE_C128 ? 16 : 8; }
 
 int validate_problem(const hse_problem* p) {
   if (!p) return HSE_ERR_INVALID_ARG;
-  if (p->dtype != HSE_C64 && p->dtype != HSE_C128) return HSE_ERR_INVALID_ARG;
+  if (p->dtype != HSE_C64 && p->dtype != HSE_C128 && p->dtype != HSE_C64_TC) return HSE_ERR_INVALID_ARG;
   if (p->nk < 1 || p->n_occ < 1 || p->n_tgt < 1 || !p->kpts) return HSE_ERR_INVALID_ARG;
   if (!(p->omega > 0.0) || !std::isfinite(p->omega) || !std::isfinite(p->alpha) || !std::isfinite(p->spin_degeneracy))
     return HSE_ERR_INVALID_ARG;
@@ -424,7 +426,7 @@ int validate_problem(const hse_problem* p) {
     if (p->grid[d] < 2) return HSE_ERR_INVALID_ARG;
     if (!hse_grid_supported(p->grid[d], p->dtype)) return HSE_ERR_UNSUPPORTED_GRID;
   }
-  if (p->dtype == HSE_C64 && (p->grid[0] != p->grid[1] || p->grid[1] != p->grid[2])) return HSE_ERR_UNSUPPORTED_GRID;
+  if (p->dtype != HSE_C128 && (p->grid[0] != p->grid[1] || p->grid[1] != p->grid[2])) return HSE_ERR_UNSUPPORTED_GRID;
   for (int i = 0; i < 3 * p->nk; ++i)
     if (!std::isfinite(p->kpts[i])) return HSE_ERR_INVALID_ARG;
   if (p->nk_occ < 0 || p->nk_occ > p->nk || (p->nk_occ > 0 && !p->kocc)) return HSE_ERR_INVALID_ARG;
@@ -460,6 +462,7 @@ extern "C" {
 int hse_grid_supported(int n, int dtype) {
   if (dtype == HSE_C64) return pairconv_c64_supported(n) ? 1 : 0;
   if (dtype == HSE_C128) return staged_fft_supported(n) ? 1 : 0;
+  if (dtype == HSE_C64_TC) return n == 24 ? 1 : 0;
   return 0;
 }
 
@@ -537,6 +540,11 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   hse_plan plan = new (std::nothrow) hse_plan_s();
   if (!plan) return HSE_ERR_NOMEM;
   plan->p = *p;
+  if (p->dtype == HSE_C64_TC) {
+    // complex64 throughout; the owner = target passes take the tensor-core kernel variant
+    plan->p.dtype = HSE_C64;
+    plan->tc = true;
+  }
   plan->kpts.assign(p->kpts, p->kpts + 3 * p->nk);
   plan->p.kpts = plan->kpts.data();
   plan->sampled = p->nk_occ > 0;
@@ -556,6 +564,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
     const int v = std::atoi(env);
     plan->blocks_per_sm = (v < -2 || v > 3) ? 0 : v;
   }
+  if (plan->tc) plan->blocks_per_sm = kTcVariant;
   const int n1 = p->grid[0], n2 = p->grid[1], n3 = p->grid[2];
   plan->N = n1 * n2 * n3;
   // b_i = 2 pi (A^-1)^T rows: b_i[c] = 2 pi ainv[c][i]
@@ -609,7 +618,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   HSE_TRY(cudaMalloc(&plan->dv64, nq * N * sizeof(double)));
   HSE_TRY(cudaMalloc(&plan->v32, nq * N * sizeof(float)));
   HSE_TRY(cudaMalloc(&plan->dv32, nq * N * sizeof(float)));
-  if (p->dtype == HSE_C64) {
+  if (plan->p.dtype == HSE_C64) {
     // Split the k' loop so that the work items fill the resident CTA slots in nearly whole
     // waves; the partial outputs are summed by reduce_splits.
     int sms = 0;
@@ -678,7 +687,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   HSE_TRY(cudaMemcpy(plan->qvec, qvec.data(), qvec.size() * sizeof(double), cudaMemcpyHostToDevice));
   HSE_TRY(cudaMalloc(&plan->dkpts, (size_t)nk * 3 * sizeof(double)));
   HSE_TRY(cudaMemcpy(plan->dkpts, plan->kpts.data(), (size_t)nk * 3 * sizeof(double), cudaMemcpyHostToDevice));
-  if (p->dtype == HSE_C128) {
+  if (plan->p.dtype == HSE_C128) {
     // staged batch: all (i, k', j) of one k in chunks of k' up to ~512 MB
     // the energy path runs the staged form with the occupied set as targets
     const size_t per_kp = (size_t)nown * p->n_occ;
@@ -709,13 +718,14 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   HSE_TRY(cudaDeviceSynchronize());
 #undef HSE_TRY
   if (log_on()) {
-    const bool c64 = p->dtype == HSE_C64;
+    const bool c64 = plan->p.dtype == HSE_C64;
     std::fprintf(stderr,
                  "hse: plan grid %dx%dx%d %s nk %d (Fock sum over %d) n_occ %d n_tgt %d: %d distinct q; "
                  "k' splits target %d energy %d occupied %d; apply kernel %s; pencil-blocked copies %s\n",
                  n1, n2, n3, c64 ? "complex64" : "complex128", nk, nkq, p->n_occ, p->n_tgt, plan->nq,
                  plan->nsplit[ROLE_TGT], plan->nsplit[ROLE_ENERGY], plan->nsplit[ROLE_OCC],
-                 !c64 ? "staged FP64" : (pairconv_c64_pencil_load(n1, MODE_APPLY, plan->blocks_per_sm) ? "pencil-load"
+                 !c64 ? "staged FP64" : (pairconv_c64_pencil_load(n1, MODE_APPLY, plan->blocks_per_sm)
+                                             ? (plan->tc ? "pencil-load, tensor-core Y/X" : "pencil-load")
                                                                                                     : "staged-partner"),
                  plan->blocked ? "on" : "off");
   }

@@ -86,41 +86,42 @@ bool staged_fft_supported(int L);
 
 // Template body used by the per-size translation units.  `blocks_per_sm` selects the
 // occupancy variant (1: registers uncapped; 2: two CTAs per SM where they fit).
-template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT>
+template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false>
 cudaError_t pairconv_set_attr() {
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_done[dev]) {
-    cudaError_t err = cudaFuncSetAttribute(pairconv_c64_kernel<n, MODE, MINB, PPT, TSX>,
+    cudaError_t err = cudaFuncSetAttribute(pairconv_c64_kernel<n, MODE, MINB, PPT, TSX, TC>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)pairconv_smem_bytes<n>());
+                                           (int)pairconv_smem_request<n, TC>());
     if (err != cudaSuccess) return err;
     attr_done[dev] = true;
   }
   return cudaSuccess;
 }
 
-template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT>
+template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false>
 cudaError_t launch_pairconv_variant(const PairArgs& args, cudaStream_t stream) {
-  cudaError_t err = pairconv_set_attr<n, MODE, MINB, PPT, TSX>();
+  cudaError_t err = pairconv_set_attr<n, MODE, MINB, PPT, TSX, TC>();
   if (err != cudaSuccess) return err;
   const dim3 grid(args.item_count > 0 ? (unsigned)args.item_count
                                       : (unsigned)((size_t)args.nsplit * args.nk_own * args.ntiles));
-  pairconv_c64_kernel<n, MODE, MINB, PPT, TSX>
-      <<<grid, GeoP<n, PPT, TSX>::THREADS, pairconv_smem_bytes<n>(), stream>>>(args);
+  pairconv_c64_kernel<n, MODE, MINB, PPT, TSX, TC>
+      <<<grid, GeoP<n, PPT, TSX>::THREADS, pairconv_smem_request<n, TC>(), stream>>>(args);
   count_launch();
   return cudaGetLastError();
 }
 
 // Resident CTAs per SM of a variant (0 on error).
-template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT>
+template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false>
 int pairconv_occupancy_variant() {
-  if (pairconv_set_attr<n, MODE, MINB, PPT, TSX>() != cudaSuccess) return 0;
+  if (pairconv_set_attr<n, MODE, MINB, PPT, TSX, TC>() != cudaSuccess) return 0;
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pairconv_c64_kernel<n, MODE, MINB, PPT, TSX>,
-                                                    GeoP<n, PPT, TSX>::THREADS, pairconv_smem_bytes<n>()) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pairconv_c64_kernel<n, MODE, MINB, PPT, TSX, TC>,
+                                                    GeoP<n, PPT, TSX>::THREADS,
+                                                    pairconv_smem_request<n, TC>()) != cudaSuccess)
     return 0;
   return blocks;
 }
@@ -135,6 +136,19 @@ constexpr bool pencil_ragged_fits() {
   if constexpr (Geo<n>::T == 1 && Geo<n>::NN > kRaggedThreads && Geo<n>::NN <= 2 * kRaggedThreads &&
                 (Geo<n>::NN - kRaggedThreads) % 32 == 0) {
     return GeoP<n, 2, kRaggedThreads>::TMEM_COLS <= 512;
+  } else {
+    return false;
+  }
+}
+
+// Tensor-core variant (kTcVariant): the ragged pencil-load kernel with the Y and X stages as
+// split-FP16 GEMMs (tc_dft.cuh), for the owner = target modes where 2n is a multiple of 16
+// and the grids leave room for the DFT tables.
+constexpr int kTcVariant = 4;
+template <int n, int MODE>
+constexpr bool tc_fits() {
+  if constexpr (MODE != MODE_OCC && n % 8 == 0 && pencil_ragged_fits<n>()) {
+    return Geo<n>::SMEM_BYTES + sizeof(TcTables<n>) <= 232448;
   } else {
     return false;
   }
@@ -181,7 +195,8 @@ constexpr bool tma_fits() {
 // -1 / -2 the staged-partner kernel with LayoutSeq / LayoutOne; 1 or 2 the
 // pencil-load kernel with that occupancy; 3 the ragged pencil-load kernel (pencil_ragged_fits;
 // the default of the pencil-load kernel where it exists: 24^3 99.6 -> 95.6 ms on the 4x4x4 k,
-// 16-band cell).  A variant that does not exist for the size falls back to the default.
+// 16-band cell); 4 (kTcVariant) its tensor-core form where tc_fits, else the ragged kernel.
+// A variant that does not exist for the size falls back to the default.
 template <int n, int MODE>
 constexpr int staged_layout(int variant) {
   if (variant > 0) return 0;
@@ -203,10 +218,13 @@ cudaError_t launch_pairconv_mode(const PairArgs& args, int variant, cudaStream_t
       break;
     default: break;
   }
-  if constexpr (pencil_ragged_fits<n>()) {
-    if (variant == 3 || variant <= 0) return launch_pairconv_variant<n, MODE, 1, 2, kRaggedThreads>(args, stream);
+  if constexpr (tc_fits<n, MODE>()) {
+    if (variant == kTcVariant) return launch_pairconv_variant<n, MODE, 1, 2, kRaggedThreads, true>(args, stream);
   }
-  const int blocks_per_sm = (variant <= 0 || variant == 3) ? 2 : variant;
+  if constexpr (pencil_ragged_fits<n>()) {
+    if (variant >= 3 || variant <= 0) return launch_pairconv_variant<n, MODE, 1, 2, kRaggedThreads>(args, stream);
+  }
+  const int blocks_per_sm = (variant <= 0 || variant >= 3) ? 2 : variant;
   if (blocks_per_sm >= 2 && Geo<n>::MAXB >= 2) return launch_pairconv_variant<n, MODE, Geo<n>::MAXB>(args, stream);
   return launch_pairconv_variant<n, MODE, 1>(args, stream);
 }
@@ -214,10 +232,13 @@ cudaError_t launch_pairconv_mode(const PairArgs& args, int variant, cudaStream_t
 template <int n, int MODE>
 int pairconv_occupancy_mode(int variant) {
   if (staged_layout<n, MODE>(variant) != 0) return 1;
-  if constexpr (pencil_ragged_fits<n>()) {
-    if (variant == 3 || variant <= 0) return pairconv_occupancy_variant<n, MODE, 1, 2, kRaggedThreads>();
+  if constexpr (tc_fits<n, MODE>()) {
+    if (variant == kTcVariant) return pairconv_occupancy_variant<n, MODE, 1, 2, kRaggedThreads, true>();
   }
-  const int blocks_per_sm = (variant <= 0 || variant == 3) ? 2 : variant;
+  if constexpr (pencil_ragged_fits<n>()) {
+    if (variant >= 3 || variant <= 0) return pairconv_occupancy_variant<n, MODE, 1, 2, kRaggedThreads>();
+  }
+  const int blocks_per_sm = (variant <= 0 || variant >= 3) ? 2 : variant;
   if (blocks_per_sm >= 2 && Geo<n>::MAXB >= 2) return pairconv_occupancy_variant<n, MODE, Geo<n>::MAXB>();
   return pairconv_occupancy_variant<n, MODE, 1>();
 }

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include "fft_reg.cuh"
+#include "tc_dft.cuh"
 #include "tmem.cuh"
 #include "tmem_gen.cuh"
 
@@ -580,6 +581,70 @@ __device__ __forceinline__ void stage_z_inverse(const float2* g, int t, const fl
   }
 }
 
+// Tensor-core forms of the Y and X stages (tc_dft.cuh; n = 24, PairArgs::tc).  A warp's
+// 32 pencils of each pass (whole warps: the ragged rule of the scalar stages) are two m16
+// tiles.  Every lane's loads of a tile complete before the first mma.sync of the tile, which
+// all lanes reach, so the tile's results can then be stored in place.
+template <int n, int DIR, int PPT, int TS>
+__device__ __forceinline__ void stage_y_tc(float2* g, int t, const TcTables<n>* tab) {
+  using G = Geo<n>;
+  using TG = TcGeo<n>;
+  const int lane = threadIdx.x & 31, gq = lane >> 2;
+  const uint4* W = DIR < 0 ? tab->fwd : tab->inv;
+#pragma unroll 1
+  for (int ps = 0; ps < PPT; ++ps) {
+    if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;  // whole warps past the last pencil
+    const int p0 = (t - lane) + ps * TS;
+#pragma unroll 1
+    for (int tile = 0; tile < 2; ++tile) {
+      const int pa = p0 + tile * 16 + gq, pb = pa + 8;
+      const int b0 = Pencil<n>(pa).ys, b1 = Pencil<n>(pb).ys;
+      uint32_t ah[TG::KS][4], al[TG::KS][4];
+      float s0, s1, acc[TG::NT][4];
+      tc_load_a<n>(g, b0, b1, G::P, ah, al, s0, s1);
+      tc_gemm<n>(acc, ah, al, W);
+      tc_store<n>(acc, s0, s1, g, b0, b1, G::P);
+    }
+  }
+}
+
+// X stage: forward DFT, multiply by the kernel row v * scale * f (read per element from the
+// table row vrow), inverse DFT, all in registers between the two GEMMs.
+template <int n, int PPT, int TS>
+__device__ __forceinline__ void stage_x_tc(float2* g, int t, const TcTables<n>* tab, const float* __restrict__ vrow,
+                                           float vscale) {
+  using G = Geo<n>;
+  using TG = TcGeo<n>;
+  const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+#pragma unroll 1
+  for (int ps = 0; ps < PPT; ++ps) {
+    if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
+    const int p0 = (t - lane) + ps * TS;
+#pragma unroll 1
+    for (int tile = 0; tile < 2; ++tile) {
+      const int pa = p0 + tile * 16 + gq, pb = pa + 8;
+      const int b0 = Pencil<n>(pa).xs, b1 = Pencil<n>(pb).xs;
+      uint32_t ah[TG::KS][4], al[TG::KS][4];
+      float s0, s1, acc[TG::NT][4];
+      tc_load_a<n>(g, b0, b1, G::Q, ah, al, s0, s1);
+      tc_gemm<n>(acc, ah, al, tab->fwd);
+      const float r0 = vscale / (s0 * kTcWScale), r1 = vscale / (s1 * kTcWScale);
+#pragma unroll
+      for (int nt = 0; nt < TG::NT; ++nt) {
+        const int k = nt * 4 + tq;  // complex element (x index) of this lane's accumulators
+        const float va = __ldg(vrow + k * G::NN + pa) * r0, vb = __ldg(vrow + k * G::NN + pb) * r1;
+        acc[nt][0] *= va;
+        acc[nt][1] *= va;
+        acc[nt][2] *= vb;
+        acc[nt][3] *= vb;
+      }
+      tc_acc_to_a<n>(acc, ah, al, s0, s1);
+      tc_gemm<n>(acc, ah, al, tab->inv);
+      tc_store<n>(acc, s0, s1, g, b0, b1, G::Q);
+    }
+  }
+}
+
 // One pair chain between the Z stages; all threads of the CTA call it together.
 template <int n, int PPT = 2, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32_t ttab, float f, bool warp_on = true) {
@@ -589,6 +654,20 @@ __device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32
   if (warp_on) stage_x<n, PPT, false, n * n, TS>(g, t, valid, ttab, f);
   __syncthreads();
   if (warp_on) stage_y<n, +1, PPT, TS>(g, t, valid);
+  __syncthreads();
+}
+
+// The same with the tensor-core Y and X stages (vrow, vscale: the pair's kernel row and its
+// scale times f).
+template <int n, int PPT, int TS>
+__device__ __forceinline__ void pair_middle_tc(float2* g, int t, const TcTables<n>* tab, const float* vrow,
+                                               float vscale, bool warp_on) {
+  __syncthreads();
+  if (warp_on) stage_y_tc<n, -1, PPT, TS>(g, t, tab);
+  __syncthreads();
+  if (warp_on) stage_x_tc<n, PPT, TS>(g, t, tab, vrow, vscale);
+  __syncthreads();
+  if (warp_on) stage_y_tc<n, +1, PPT, TS>(g, t, tab);
   __syncthreads();
 }
 
@@ -610,12 +689,15 @@ __device__ __forceinline__ void pair_middle_occ(float2* g, int t, bool valid, ui
 // warp_on == false skip all work and TMEM traffic but pass every barrier.  tbase: the CTA's
 // TMEM allocation, at least Geo<n>::TMEM_COLS columns for this block's warp count.
 // spec: this CTA's spectrum scratch (T blocked grids) when args.vtab2 is set (MODE_OCC).
-template <int n, int MODE, int PPT = 2, int TSX = Geo<n>::NN / PPT>
+// TC: the Y and X stages on the tensor cores (stage_y_tc / stage_x_tc; the DFT tables follow
+// the grids in shared memory), for the modes with owner = target.
+template <int n, int MODE, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false>
 __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, float4* smem4, uint32_t tbase,
                                               bool warp_on, float2* spec = nullptr) {
   using G = Geo<n>;
   using GP = GeoP<n, PPT, TSX>;
   constexpr int TS = GP::TS;
+  static_assert(!TC || MODE != MODE_OCC, "the tensor-core stages serve the owner = target modes");
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -696,14 +778,20 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     // q = k_i - k_j: APPLY-like modes own i (at k) and pair with j at kp; OCC owns j (at k)
     const int qrow = (MODE == MODE_OCC) ? args.qidx[kp * args.nk_own + k] : args.qidx[k * args.nk_part + kp];
     const float* dvrow = fuse_w ? args.vtab2 + (size_t)qrow * G::N : nullptr;
-    if (warp_on) cache_kernel_row<n, PPT, false, n * n, TS>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
+    if (warp_on && !TC) cache_kernel_row<n, PPT, false, n * n, TS>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
     for (int j = 0; j < args.n_part; ++j) {
       const float2* part = args.part + ((size_t)kp * args.n_part + j) * ostr;
       if constexpr (MODE != MODE_OCC) {
         const float f = (float)args.occ[kp * args.n_occ + j];
         if (f == 0.f) continue;  // uniform over the CTA
         if (warp_on) stage_z_forward<n, PPT, TS>(g, t, valid, part, own, blk);          // conj(u_j) u_i
-        pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
+        if constexpr (TC) {
+          const TcTables<n>* tct =
+              reinterpret_cast<const TcTables<n>*>(reinterpret_cast<const char*>(smem4) + G::SMEM_BYTES);
+          pair_middle_tc<n, PPT, TS>(g, t, tct, args.vtab + (size_t)qrow * G::N, args.scale * f, warp_on);
+        } else {
+          pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
+        }
         if (warp_on) stage_z_inverse<n, EPI_MUL, PPT, TS>(g, t, part, trow0, blk);      // acc += u_j phi
       } else {
         const float f = (float)args.occ[k * args.n_occ + bandc];
@@ -760,12 +848,14 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
   }
 }
 
-template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT>
+template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false>
 __global__ void __launch_bounds__(GeoP<n, PPT, TSX>::THREADS, MINB) pairconv_c64_kernel(const PairArgs args) {
   using G = GeoP<n, PPT, TSX>;
   extern __shared__ __align__(16) float4 smem4[];
   __shared__ uint32_t tmem_base_sh;
   const int warp = threadIdx.x >> 5;
+  if constexpr (TC)  // the DFT tables after the grids; the barrier below orders them
+    tc_build_tables<n>(reinterpret_cast<TcTables<n>*>(reinterpret_cast<char*>(smem4) + Geo<n>::SMEM_BYTES));
   if (warp == 0) {
     tmem_alloc(&tmem_base_sh, G::TMEM_COLS);
     tmem_relinquish();
@@ -776,7 +866,7 @@ __global__ void __launch_bounds__(GeoP<n, PPT, TSX>::THREADS, MINB) pairconv_c64
   const uint32_t tbase = tmem_base_sh;
   // one spectrum scratch (T blocked grids) per CTA of the launch, for MODE_OCC with omega
   float2* spec = args.spec ? args.spec + (size_t)blockIdx.x * Geo<n>::T * OrbBlk<n>::NBK : nullptr;
-  pairconv_item<n, MODE, PPT, TSX>(args, args.item0 + (int)blockIdx.x, smem4, tbase, true, spec);
+  pairconv_item<n, MODE, PPT, TSX, TC>(args, args.item0 + (int)blockIdx.x, smem4, tbase, true, spec);
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
@@ -792,6 +882,18 @@ constexpr size_t pairconv_smem_bytes() {
   constexpr int max_res = 512 / Geo<n>::TMEM_COLS;
   constexpr size_t floor_bytes = sm_smem / (size_t)(max_res + 1) + 2048;
   return Geo<n>::SMEM_BYTES > floor_bytes ? Geo<n>::SMEM_BYTES : floor_bytes;
+}
+
+// The same for the tensor-core variant: the grids, then the DFT tables.
+template <int n, bool TC>
+constexpr size_t pairconv_smem_request() {
+  if constexpr (TC) {
+    constexpr size_t need = Geo<n>::SMEM_BYTES + sizeof(TcTables<n>);
+    static_assert(Geo<n>::SMEM_BYTES % 16 == 0, "the tables need 16-byte alignment");
+    return need > pairconv_smem_bytes<n>() ? need : pairconv_smem_bytes<n>();
+  } else {
+    return pairconv_smem_bytes<n>();
+  }
 }
 
 }  // namespace hse

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libhse_fock.so")
 
 HSE_C64 = 0
 HSE_C128 = 1
+HSE_C64_TC = 2  # complex64, Y/X transforms as split-FP16 tensor-core GEMMs (24^3 grids)
 
 ERRORS = {
     0: "HSE_OK", -1: "HSE_ERR_INVALID_ARG", -2: "HSE_ERR_UNSUPPORTED_GRID", -3: "HSE_ERR_ALIAS",
@@ -131,7 +132,8 @@ def _code(dtype: torch.dtype) -> int:
     raise ValueError(f"unsupported dtype {dtype}")
 
 
-def _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype, kocc=None):
+def _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype, kocc=None,
+             tensor_cores=False):
     """HseProblem and the host arrays it points to (keep them alive with it)."""
     kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
     p = HseProblem()
@@ -145,6 +147,10 @@ def _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, d
     p.alpha = float(alpha)
     p.spin_degeneracy = float(spin_degeneracy)
     p.dtype = _code(dtype)
+    if tensor_cores:
+        if dtype != torch.complex64:
+            raise ValueError("tensor_cores needs complex64 orbitals")
+        p.dtype = HSE_C64_TC
     if kocc is None:
         p.nk_occ = 0
         ko = None
@@ -160,10 +166,13 @@ class Plan:
 
     ``kocc`` (optional) down-samples the Fock sum: the indices of the k-points whose occupied
     orbitals enter it, with weight 1/len(kocc) (Sec. II C, after Eq. "Fock-DS"); the orbital
-    arrays keep every k-point."""
+    arrays keep every k-point.
+
+    ``tensor_cores`` (complex64, 24^3 grids) runs the Y and X axis transforms of the owner =
+    target passes as split-FP16 GEMMs on the tensor cores (the library's HSE_C64_TC)."""
 
     def __init__(self, grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy=2.0,
-                 dtype=torch.complex64, device=None, kocc=None):
+                 dtype=torch.complex64, device=None, kocc=None, tensor_cores=False):
         lib = load_library()
         self.grid = tuple(int(g) for g in grid)
         self.nk = int(np.asarray(kpts).reshape(-1, 3).shape[0])
@@ -171,8 +180,10 @@ class Plan:
         self.n_occ, self.n_tgt = int(n_occ), int(n_tgt)
         self.omega, self.alpha, self.spin_degeneracy = float(omega), float(alpha), float(spin_degeneracy)
         self.dtype = dtype
+        self.tensor_cores = bool(tensor_cores)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
-        prob, self._kp = _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype, self.kocc)
+        prob, self._kp = _problem(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype, self.kocc,
+                                  self.tensor_cores)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(lib.hse_plan_create(ctypes.byref(h), ctypes.byref(prob)), "hse_plan_create")

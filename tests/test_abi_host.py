@@ -43,6 +43,11 @@ def test_strerror_and_grid_support(lib):
     assert lib.hse_grid_supported(27, hse.HSE_C64) == 0
     assert lib.hse_grid_supported(15, hse.HSE_C64) == 0  # the fused form needs an even side
     assert lib.hse_grid_supported(15, hse.HSE_C128) == 1
+    # the tensor-core option exists for the 24^3 kernel only
+    assert lib.hse_grid_supported(24, hse.HSE_C64_TC) == 1
+    for n in (8, 16, 20):
+        assert lib.hse_grid_supported(n, hse.HSE_C64_TC) == 0
+    assert lib.hse_grid_supported(24, 3) == 0  # no such dtype
 
 
 def _prob(**kw):
@@ -68,6 +73,8 @@ def _prob(**kw):
     (dict(kpts=np.zeros((2, 3)), kocc=[-1]), -1),
     (dict(kpts=np.zeros((2, 3)), kocc=[1, 1]), -1),        # repeated
     (dict(kpts=np.zeros((2, 3)), kocc=[0, 1, 0]), -1),     # more than nk
+    (dict(tensor_cores=True), -2),                 # the tensor-core option: 24^3 only
+    (dict(grid=(24, 24, 20), tensor_cores=True), -2),
 ])
 def test_plan_create_rejects_bad_problems_on_host(lib, kw, code):
     p, keep = _prob(**kw)
