@@ -39,7 +39,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic of one launch of the fused 20^3 kernel from an ncu capture, valid only while
 # the kernel sources hash to the value recorded with it (else reported as null).
-TRAFFIC = {"sha": "e36fb2317e0dddf9", "bytes_per_launch": 1073.175808e6}
+TRAFFIC = {"sha": "43f4613df6db5493", "bytes_per_launch": 1070.526976e6}
 
 
 def _code_only(src: str) -> str:
@@ -346,15 +346,18 @@ def run_cuda(args, rank, world, dist):
 
 def run_profile_case(spec: str):
     """Two applies of one seeded cell (grid side n, n_k^3 Monkhorst-Pack k-points, nb bands,
-    complex64): the launch an ncu capture of a secondary kernel selects with -s 1 -c 1.  Prints
-    no bench line."""
+    complex64; a fourth field "tc" selects the tensor-core option): the launch an ncu capture
+    of a secondary kernel selects with -s 1 -c 1.  Prints no bench line."""
     import torch
     from paper_1507_05156_gb300 import hse, inputs
-    n, km, nb = (int(x) for x in spec.split(","))
+    fields = spec.split(",")
+    n, km, nb = (int(x) for x in fields[:3])
+    tc = len(fields) > 3 and fields[3] == "tc"
     cell = inputs.make_cell(inputs.SEED_BASE + 100 + n, (n, n, n), (km, km, km), nb, name=f"c64_{n}cube_k{km}_b{nb}")
     u = torch.from_numpy(cell.u_occ.astype(np.complex64)).cuda()
     occ = torch.from_numpy(cell.occ).cuda()
-    plan = hse.get_plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha)
+    plan = hse.Plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha,
+                    tensor_cores=tc)
     out = torch.empty_like(u)
     for _ in range(2):
         hse.hse_fock_apply(plan, u, occ, u, out=out)
@@ -497,7 +500,7 @@ def main():
     ap.add_argument("--cpu-targets", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--profile-case", default=None, metavar="N,KM,NB",
+    ap.add_argument("--profile-case", default=None, metavar="N,KM,NB[,tc]",
                     help="only run two applies of one cell (for ncu captures of secondary kernels)")
     ap.add_argument("--config", choices=CONFIGS, default=None,
                     help="time another workload of the method (one JSON line) instead of the bench workload")

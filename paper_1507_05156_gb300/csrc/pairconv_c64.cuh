@@ -24,7 +24,6 @@
 #include <cuda_bf16.h>
 
 #include "fft_reg.cuh"
-#include "tc_dft.cuh"
 #include "tmem.cuh"
 #include "tmem_gen.cuh"
 
@@ -581,70 +580,6 @@ __device__ __forceinline__ void stage_z_inverse(const float2* g, int t, const fl
   }
 }
 
-// Tensor-core forms of the Y and X stages (tc_dft.cuh; n = 24, PairArgs::tc).  A warp's
-// 32 pencils of each pass (whole warps: the ragged rule of the scalar stages) are two m16
-// tiles.  Every lane's loads of a tile complete before the first mma.sync of the tile, which
-// all lanes reach, so the tile's results can then be stored in place.
-template <int n, int DIR, int PPT, int TS>
-__device__ __forceinline__ void stage_y_tc(float2* g, int t, const TcTables<n>* tab) {
-  using G = Geo<n>;
-  using TG = TcGeo<n>;
-  const int lane = threadIdx.x & 31, gq = lane >> 2;
-  const uint4* W = DIR < 0 ? tab->fwd : tab->inv;
-#pragma unroll 1
-  for (int ps = 0; ps < PPT; ++ps) {
-    if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;  // whole warps past the last pencil
-    const int p0 = (t - lane) + ps * TS;
-#pragma unroll 1
-    for (int tile = 0; tile < 2; ++tile) {
-      const int pa = p0 + tile * 16 + gq, pb = pa + 8;
-      const int b0 = Pencil<n>(pa).ys, b1 = Pencil<n>(pb).ys;
-      uint32_t ah[TG::KS][4], al[TG::KS][4];
-      float s0, s1, acc[TG::NT][4];
-      tc_load_a<n>(g, b0, b1, G::P, ah, al, s0, s1);
-      tc_gemm<n>(acc, ah, al, W);
-      tc_store<n>(acc, s0, s1, g, b0, b1, G::P);
-    }
-  }
-}
-
-// X stage: forward DFT, multiply by the kernel row v * scale * f (read per element from the
-// table row vrow), inverse DFT, all in registers between the two GEMMs.
-template <int n, int PPT, int TS>
-__device__ __forceinline__ void stage_x_tc(float2* g, int t, const TcTables<n>* tab, const float* __restrict__ vrow,
-                                           float vscale) {
-  using G = Geo<n>;
-  using TG = TcGeo<n>;
-  const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
-#pragma unroll 1
-  for (int ps = 0; ps < PPT; ++ps) {
-    if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
-    const int p0 = (t - lane) + ps * TS;
-#pragma unroll 1
-    for (int tile = 0; tile < 2; ++tile) {
-      const int pa = p0 + tile * 16 + gq, pb = pa + 8;
-      const int b0 = Pencil<n>(pa).xs, b1 = Pencil<n>(pb).xs;
-      uint32_t ah[TG::KS][4], al[TG::KS][4];
-      float s0, s1, acc[TG::NT][4];
-      tc_load_a<n>(g, b0, b1, G::Q, ah, al, s0, s1);
-      tc_gemm<n>(acc, ah, al, tab->fwd);
-      const float r0 = vscale / (s0 * kTcWScale), r1 = vscale / (s1 * kTcWScale);
-#pragma unroll
-      for (int nt = 0; nt < TG::NT; ++nt) {
-        const int k = nt * 4 + tq;  // complex element (x index) of this lane's accumulators
-        const float va = __ldg(vrow + k * G::NN + pa) * r0, vb = __ldg(vrow + k * G::NN + pb) * r1;
-        acc[nt][0] *= va;
-        acc[nt][1] *= va;
-        acc[nt][2] *= vb;
-        acc[nt][3] *= vb;
-      }
-      tc_acc_to_a<n>(acc, ah, al, s0, s1);
-      tc_gemm<n>(acc, ah, al, tab->inv);
-      tc_store<n>(acc, s0, s1, g, b0, b1, G::Q);
-    }
-  }
-}
-
 // One pair chain between the Z stages; all threads of the CTA call it together.
 template <int n, int PPT = 2, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32_t ttab, float f, bool warp_on = true) {
@@ -657,19 +592,12 @@ __device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32
   __syncthreads();
 }
 
-// The same with the tensor-core Y and X stages (vrow, vscale: the pair's kernel row and its
-// scale times f).
-template <int n, int PPT, int TS>
-__device__ __forceinline__ void pair_middle_tc(float2* g, int t, const TcTables<n>* tab, const float* vrow,
-                                               float vscale, bool warp_on) {
-  __syncthreads();
-  if (warp_on) stage_y_tc<n, -1, PPT, TS>(g, t, tab);
-  __syncthreads();
-  if (warp_on) stage_x_tc<n, PPT, TS>(g, t, tab, vrow, vscale);
-  __syncthreads();
-  if (warp_on) stage_y_tc<n, +1, PPT, TS>(g, t, tab);
-  __syncthreads();
-}
+}  // namespace hse
+
+// the tensor-core Y and X stages (pair_middle_tc), which use the definitions above
+#include "pairconv_tc.cuh"
+
+namespace hse {
 
 // The same with stage_x_occ (MODE_OCC with the omega gradient fused in).
 template <int n, int SPEC, int PPT = 2, int TS = Geo<n>::NN / PPT>

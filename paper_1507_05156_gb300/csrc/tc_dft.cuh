@@ -61,14 +61,31 @@ __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint
 
 constexpr float kTcWScale = 16384.f;  // 2^14
 
+// cos and sin of 2 pi m / n, m < n, rounded to FP32 at compile time
+template <int n>
+struct TcTrig {
+  float c[n], s[n];
+};
+template <int n>
+constexpr TcTrig<n> make_tc_trig() {
+  TcTrig<n> t{};
+  for (int m = 0; m < n; ++m) {
+    t.c[m] = (float)trig2pi(m, n, 0);
+    t.s[m] = (float)trig2pi(m, n, 1);
+  }
+  return t;
+}
+template <int n>
+__device__ const TcTrig<n> kTcTrig = make_tc_trig<n>();
+
 // W[K][N] (real form above), times 2^14
 template <int n, int DIR>
 __device__ __forceinline__ float tc_w(int K, int N) {
   const int j = K >> 1, c = K & 1, k = N >> 1, d = N & 1;
   const int jk = (j * k) % n;
-  const double cs = trig2pi(jk, n, 0), sn = DIR * trig2pi(jk, n, 1);
-  const double w = (c == d) ? cs : (c == 0 ? sn : -sn);
-  return (float)(w * (double)kTcWScale);
+  const float cs = kTcTrig<n>.c[jk], sn = DIR * kTcTrig<n>.s[jk];
+  const float w = (c == d) ? cs : (c == 0 ? sn : -sn);
+  return w * kTcWScale;
 }
 
 // Fill both tables (all threads of the block; a barrier must follow).
@@ -128,6 +145,30 @@ __device__ __forceinline__ void tc_gemm(float (&acc)[TcGeo<n>::NT][4], const uin
       mma_f16(acc[nt], ah[kk], b.x, b.y);
       mma_f16(acc[nt], ah[kk], b.z, b.w);
       mma_f16(acc[nt], al[kk], b.x, b.y);
+    }
+  }
+}
+
+// The same for two tiles at once (independent accumulator chains interleaved, each B
+// fragment loaded once for both).
+template <int n>
+__device__ __forceinline__ void tc_gemm2(float (&acc)[2][TcGeo<n>::NT][4], const uint32_t (&ah)[2][TcGeo<n>::KS][4],
+                                         const uint32_t (&al)[2][TcGeo<n>::KS][4], const uint4* __restrict__ tab) {
+  using TG = TcGeo<n>;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int nt = 0; nt < TG::NT; ++nt) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) acc[u][nt][0] = acc[u][nt][1] = acc[u][nt][2] = acc[u][nt][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < TG::KS; ++kk) {
+      const uint4 b = tab[(kk * TG::NT + nt) * 32 + lane];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        mma_f16(acc[u][nt], ah[u][kk], b.x, b.y);
+        mma_f16(acc[u][nt], ah[u][kk], b.z, b.w);
+        mma_f16(acc[u][nt], al[u][kk], b.x, b.y);
+      }
     }
   }
 }
