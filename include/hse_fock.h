@@ -109,8 +109,9 @@ int hse_plan_destroy(hse_plan plan);
  *   occ    device [nk][n_occ]      occupations f_{j,k'} (double)
  *   u_tgt  device [nk][n_tgt][N]   target orbitals u_{i,k}; may equal u_occ
  *   vx_out device [nk][n_tgt][N]   result, overwritten; must not overlap any input
- * Complex64 or complex128 per the plan's dtype.  Complex64 pair terms are summed over the bands
- * of each k' in FP32 and over k' with compensation (TwoSum).  Asynchronous on `stream`, except
+ * Complex64 or complex128 per the plan's dtype (complex64 for HSE_C64_TC).  Complex64 pair
+ * terms are summed over the bands of each k' in FP32 and over k' with compensation (TwoSum).
+ * Asynchronous on `stream`, except
  * that a complex64 call running the pencil-load kernel (24^3 grids here, and the VJP with
  * respect to u_occ at every size) copies the orbitals it reads into plan scratch in a
  * pencil-blocked layout, which the first such call (or one needing more than before)
