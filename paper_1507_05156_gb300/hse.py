@@ -204,15 +204,17 @@ _plan_cache: Dict[tuple, Plan] = {}
 
 
 def get_plan(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy=2.0,
-             dtype=torch.complex64, device=None, kocc=None) -> Plan:
+             dtype=torch.complex64, device=None, kocc=None, tensor_cores=False) -> Plan:
     """Plans are cached by every parameter that enters them."""
     dev = torch.cuda.current_device() if device is None else torch.device(device).index
     key = (tuple(int(g) for g in grid), np.asarray(lattice, np.float64).tobytes(),
            np.asarray(kpts, np.float64).tobytes(), int(n_occ), int(n_tgt), float(omega), float(alpha),
-           float(spin_degeneracy), dtype, dev, None if kocc is None else tuple(int(k) for k in kocc))
+           float(spin_degeneracy), dtype, dev, None if kocc is None else tuple(int(k) for k in kocc),
+           bool(tensor_cores))
     plan = _plan_cache.get(key)
     if plan is None:
-        plan = Plan(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype, device=dev, kocc=kocc)
+        plan = Plan(grid, lattice, kpts, n_occ, n_tgt, omega, alpha, spin_degeneracy, dtype, device=dev, kocc=kocc,
+                    tensor_cores=tensor_cores)
         _plan_cache[key] = plan
     return plan
 

@@ -95,3 +95,34 @@ def test_tc_option_refuses_other_grids_and_dtypes():
     with pytest.raises(ValueError):
         hse.Plan(GRID, lattice, np.zeros((1, 3)), 2, 2, inputs.OMEGA, inputs.ALPHA, dtype=torch.complex128,
                  tensor_cores=True)
+
+
+def test_tc_full_24cube_workload_sampled_targets():
+    """The timed tensor-core workload (24^3 grid, 8x8x8 k-mesh, 16 occupied + 16 empty targets,
+    134,217,728 pair convolutions per apply) in the launch configuration the benchmark times:
+    three sampled targets against the oracle element by element, and the exchange energy of
+    the tensor-core energy pass against an FP64 dot of the tensor-core apply output."""
+    c = inputs.workload(2)
+    u_tgt = torch.from_numpy(c.u_tgt.astype(np.complex64)).cuda()
+    u_occ = u_tgt[:, :c.n_occ].contiguous()
+    occ = torch.from_numpy(c.occ).cuda()
+    plan = hse.Plan(c.grid, c.lattice, c.kpts, c.n_occ, c.n_tgt, c.omega, c.alpha, tensor_cores=True)
+    out = hse.hse_fock_apply(plan, u_occ, occ, u_tgt)
+    hse.hse_status(plan)
+    targets = [(0, 0), (261, 15), (511, 31)]
+    uo = c.u_occ.astype(np.complex64).astype(np.complex128)
+    ut = c.u_tgt.astype(np.complex64).astype(np.complex128)
+    ref = oracle.fock_apply(uo, c.occ, ut, c.kpts, c.lattice, c.grid, c.omega, c.alpha, targets=targets)
+    got = np.stack([out[k, i].cpu().numpy() for k, i in targets])
+    err = _rel(got, ref)
+    print(f"24^3 x 8^3 k tensor-core apply, sampled targets: relative error vs FP64 {err:.3e}")
+    assert err <= TOL
+    plan_e = hse.Plan(c.grid, c.lattice, c.kpts, c.n_occ, c.n_occ, c.omega, c.alpha, tensor_cores=True)
+    e = hse.hse_exchange_energy(plan_e, u_occ, occ).item()
+    hse.hse_status(plan_e)
+    vx = out[:, :c.n_occ].to(torch.complex128)
+    dV = abs(np.linalg.det(c.lattice)) / c.npts
+    dots = (torch.conj(u_occ.to(torch.complex128)) * vx).real.sum(dim=(2, 3, 4))
+    e_ref = 0.5 * 2.0 * dV / c.nk * float((occ * dots).sum())
+    assert e < 0
+    assert abs(e - e_ref) <= 1e-6 * abs(e_ref)
