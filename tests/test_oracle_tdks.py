@@ -26,6 +26,25 @@ def test_kinetic_on_plane_wave_closed_form():
     np.testing.assert_allclose(out, 0.5 * (g @ g) * u, atol=1e-12)
 
 
+def test_hamiltonian_on_plane_wave_with_local_potential_closed_form():
+    """alpha = 0: h = T[A] + v_loc (Sec. II A, Eq. "tdks-h"), so on a plane wave u = e^{iG.r}
+    and v_loc(r) = c + d cos(G1.r), built here from the grid positions,
+    h u = (1/2 |G + k + A|^2 + c + d cos(G1.r)) u point by point."""
+    grid = (6, 5, 4)
+    b = 2 * np.pi * np.linalg.inv(TRICLINIC).T
+    r = _positions(grid, TRICLINIC)
+    G = 1 * b[0] + 2 * b[1] - 1 * b[2]
+    G1 = 2 * b[0] - 1 * b[2]
+    u = np.exp(1j * (r @ G))[None, None]
+    k = np.array([[0.07, 0.12, -0.04]])
+    A = np.array([-0.01, 0.02, 0.03])
+    c, d = 0.35, -0.8
+    vloc = c + d * np.cos(r @ G1)
+    out = td.hamiltonian_apply(u, np.ones((1, 1)), u, k, TRICLINIC, grid, A, 0.2, 0.0, vloc)
+    g = G + k[0] + A
+    np.testing.assert_allclose(out, (0.5 * (g @ g) + vloc) * u, atol=1e-12)
+
+
 def test_taylor_norm_drift_closed_form():
     """alpha = 0, A = 0, a plane-wave orbital with kinetic energy e: one step multiplies it by
     sum_{n<=4} (-i e dt)^n/n!, whose squared modulus is 1 - (e dt)^6/72 + (e dt)^8/576."""
