@@ -416,9 +416,13 @@ def run_config(name: str, args):
         out = [torch.empty_like(u) for u in uo]
         ms = _timed(lambda: hse.hse_fock_apply_batched(plan, uo, oc, uo, out=out), steps, warmup, stream)
         pairs = sum(c.pairs for c in cells)
+        flops = sum(algorithmic_flops_per_pair(int(np.prod(c.grid))) * c.pairs for c in cells)
         line.update(value=pairs / ms * 1e3, ms_per_step=ms, steps=steps, warmup=warmup, dtype="f32",
                     config={"workload": "batched_32_uneven_cells", "cells": len(cells), "pairs_per_step": pairs,
-                            "l2": "not flushed (one graph replay per step, back to back)"})
+                            "l2": "not flushed (one graph replay per step, back to back)"},
+                    roofline={"bound": "alu", "achieved": flops / ms / 1e9, "peak": FP32_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": flops / ms / 1e9 / FP32_PEAK_TFLOPS,
+                              "peak_source": "FP32 FMA lanes x max SM clock"})
     elif name in ("fp64_12cube", "c64_24cube", "c64_24cube_tc"):
         w = 0 if name == "fp64_12cube" else 2
         tc = name == "c64_24cube_tc"
@@ -483,6 +487,12 @@ def run_config(name: str, args):
             loss.backward()
 
         res["backprop_20_steps_ms_c64"] = _timed(backprop, 1, 1, stream)
+        # the VJP executes three pair convolutions per pair (one for u_tgt, two for u_occ)
+        vflops = 3 * algorithmic_flops_per_pair(int(np.prod(cell.grid))) * cell.pairs
+        line["roofline"] = {"bound": "alu", "achieved": vflops / res["vjp_ms_c64"] / 1e9, "peak": FP32_PEAK_TFLOPS,
+                            "unit": "TFLOP/s", "frac": vflops / res["vjp_ms_c64"] / 1e9 / FP32_PEAK_TFLOPS,
+                            "peak_source": "FP32 FMA lanes x max SM clock",
+                            "note": "three executed pair convolutions per pair of the forward"}
         line.update(value=cell.pairs / res["vjp_ms_c64"] * 1e3, ms_per_step=res["vjp_ms_c64"], steps=steps,
                     warmup=warmup, dtype="f32",
                     config=dict(config_dict(cell), timed="hse_fock_apply_vjp (all three gradients), complex64",
