@@ -346,11 +346,25 @@ def run_cuda(args, rank, world, dist):
 
 def run_profile_case(spec: str):
     """Two applies of one seeded cell (grid side n, n_k^3 Monkhorst-Pack k-points, nb bands,
-    complex64; a fourth field "tc" selects the tensor-core option): the launch an ncu capture
-    of a secondary kernel selects with -s 1 -c 1.  Prints no bench line."""
+    complex64; a fourth field "tc" selects the tensor-core option; "batched,C" runs the first C
+    cells of the uneven batch instead): the launch an ncu capture of a secondary kernel selects
+    with -s 1 -c 1.  Prints no bench line."""
     import torch
     from paper_1507_05156_gb300 import hse, inputs
     fields = spec.split(",")
+    if fields[0] == "batched":  # "batched,C": two calls on the first C cells of the uneven batch
+        cells = inputs.batched_cells(int(fields[1]))
+        plan = hse.BatchedPlan(cells)
+        uo = [torch.from_numpy(c.u_occ.astype(np.complex64)).cuda() for c in cells]
+        oc = [torch.from_numpy(c.occ).cuda() for c in cells]
+        out = [torch.empty_like(u) for u in uo]
+        for _ in range(2):
+            hse.hse_fock_apply_batched(plan, uo, oc, uo, out=out)
+        torch.cuda.synchronize()
+        hse.hse_status(plan)
+        print(f"profile case batched_{len(cells)}: {sum(c.pairs for c in cells)} pair convolutions per call",
+              flush=True)
+        return
     n, km, nb = (int(x) for x in fields[:3])
     tc = len(fields) > 3 and fields[3] == "tc"
     cell = inputs.make_cell(inputs.SEED_BASE + 100 + n, (n, n, n), (km, km, km), nb, name=f"c64_{n}cube_k{km}_b{nb}")
@@ -510,7 +524,7 @@ def main():
     ap.add_argument("--cpu-targets", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--profile-case", default=None, metavar="N,KM,NB[,tc]",
+    ap.add_argument("--profile-case", default=None, metavar="N,KM,NB[,tc] | batched,C",
                     help="only run two applies of one cell (for ncu captures of secondary kernels)")
     ap.add_argument("--config", choices=CONFIGS, default=None,
                     help="time another workload of the method (one JSON line) instead of the bench workload")
