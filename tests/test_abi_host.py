@@ -83,6 +83,31 @@ def test_plan_create_rejects_bad_problems_on_host(lib, kw, code):
     assert not h.value
 
 
+@pytest.mark.parametrize("field,value,code", [
+    ("dtype", 3, -1),                  # no such dtype
+    ("dtype", -1, -1),
+    ("nk", 0, -1),
+    ("alpha", float("inf"), -1),
+    ("spin_degeneracy", float("nan"), -1),
+    ("omega", -0.1, -1),
+])
+def test_plan_create_rejects_bad_fields_on_host(lib, field, value, code):
+    """Fields set on the marshalled struct directly (values the binding would not produce)."""
+    p, keep = _prob()
+    setattr(p, field, value)
+    h = ctypes.c_void_p(123)
+    assert lib.hse_plan_create(ctypes.byref(h), ctypes.byref(p)) == code
+    assert not h.value
+
+
+def test_batched_plans_refuse_tensor_core_cells(lib):
+    p, keep = _prob(grid=(24, 24, 24), tensor_cores=True)
+    cells = (hse.HseProblem * 1)(p)
+    h = ctypes.c_void_p(123)
+    assert lib.hse_plan_create_batched(ctypes.byref(h), cells, 1) == -2
+    assert not h.value
+
+
 def test_batched_plans_refuse_down_sampling(lib):
     p, keep = _prob(kpts=np.zeros((2, 3)), kocc=[1])
     cells = (hse.HseProblem * 1)(p)
