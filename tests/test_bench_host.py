@@ -1,0 +1,55 @@
+"""Host helpers of bench.py that the JSON line is built from (no GPU needed): the algorithmic
+work per pair, the code-only source hash that guards the recorded DRAM traffic, and the
+reading of the measured peaks."""
+import json
+import math
+
+import numpy as np
+
+import bench
+from paper_1507_05156_gb300 import inputs
+
+
+def test_algorithmic_flops_per_pair_is_two_ffts_plus_pointwise_work():
+    # 10 N log2 N (two 3-D FFTs at 5 N log2 N) + 16 N (pair product 6, kernel 2, MAC 8)
+    for n in (12, 16, 20, 24):
+        N = n ** 3
+        assert bench.algorithmic_flops_per_pair(N) == 10.0 * N * math.log2(N) + 16.0 * N
+    # the bench workload's figure per apply: 1,048,576 pairs at 20^3
+    c = inputs.workload(1)
+    assert c.pairs == 64 * 16 * 64 * 16
+    assert abs(bench.algorithmic_flops_per_pair(8000) * c.pairs - 1.2216e12) < 1e9
+
+
+def test_fp32_peak_is_lanes_times_clock():
+    assert abs(bench.FP32_PEAK_TFLOPS - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+
+
+def test_code_only_ignores_comments_and_blank_lines():
+    a = "int x = 1;  // one\n/* block\n comment */\n\nint y = 2;\n"
+    b = "int x = 1;\n// other words\nint y = 2;   \n"
+    assert bench._code_only(a) == bench._code_only(b) == "int x = 1;\nint y = 2;"
+    assert bench._code_only("int x = 1;\n") != bench._code_only("int x = 2;\n")
+
+
+def test_kernel_source_sha_is_stable_and_short():
+    s = bench.kernel_source_sha()
+    assert s == bench.kernel_source_sha()
+    assert len(s) == 16 and all(ch in "0123456789abcdef" for ch in s)
+
+
+def test_measured_peak_reads_the_file_or_returns_none(tmp_path, monkeypatch):
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"bf16_tflops": 1928.7, "hbm_gbs": "x"}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._measured_peak("bf16_tflops") == 1928.7
+    assert bench._measured_peak("hbm_gbs") is None      # not a number
+    assert bench._measured_peak("missing") is None
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path / "nowhere"))
+    assert bench._measured_peak("bf16_tflops") is None
+
+
+def test_workload_shapes_match_the_stated_configs():
+    w = {k: inputs.WORKLOADS[k] for k in inputs.WORKLOADS}
+    assert w[1]["grid"] == (20, 20, 20) and w[1]["kmesh"] == (4, 4, 4) and w[1]["n_occ"] == 16
+    assert w[2]["grid"] == (24, 24, 24) and w[2]["kmesh"] == (8, 8, 8) and w[2]["n_occ"] + w[2]["n_empty"] == 32
+    assert np.prod(w[0]["kmesh"]) == 8 and np.prod(w[4]["kmesh"]) == 27
