@@ -1,10 +1,13 @@
 """Benchmark of the HSE Fock-like exchange hot path (one JSON line on rank 0).
 
-A step is one hse_fock_apply over the whole workload: every ordered pair
-(i, k; j, k') of the 20^3-grid, 4x4x4 Monkhorst-Pack, 16-band silicon-like cell goes
-through pair density -> 3-D FFT -> screened kernel -> inverse FFT -> multiply-accumulate
-(1,048,576 pair convolutions).  Inputs are seeded synthetic orbitals already resident in
-HBM; L2 (129 MB) is flushed by a 256 MB write between timed steps, outside the events.
+A step is one hse_fock_apply over the whole workload: every ordered pair (i, k; j, k') of
+the 24^3-grid, 8x8x8 Monkhorst-Pack (512 k-points) silicon-like cell with 16 occupied bands
+and 32 target bands (the 16 occupied + 16 empty ones) goes through pair density -> 3-D FFT ->
+screened kernel -> inverse FFT -> multiply-accumulate (134,217,728 pair convolutions).  This
+is the largest single-GPU configuration of the method's workloads.  Inputs are seeded
+synthetic orbitals already resident in HBM; they (2.7 GB) are far larger than L2 (129 MB),
+so no flush is needed between steps.  The 20^3, 4x4x4 k, 16-band cell is reported beside it
+(key "c64_20cube").
 
   python bench.py [--gpus N --steps K --warmup W] [--impl cuda|reference]
 
@@ -31,15 +34,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "HSE V_xψ orbital-pair convolutions/sec and % roofline at stated err vs FP64"
 UNIT = "pair-convolutions/s"
-WORKLOAD = 1  # the 20^3 grid, 64 k-point, 16-band workload
+WORKLOAD = 2  # the 24^3 grid, 512 k-point, 16 occupied + 32 target band workload
+SECOND = 1    # the 20^3 grid, 64 k-point, 16-band workload (an extra key of the line)
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes of an SM (4 schedulers x 32)
+DEFAULT_SM_MHZ = 2070.0  # maximum SM clock of a GB300, used when no measured figure exists
 
-# FP32 ALU peak of a GB300 from unit counts and clocks: 152 SMs x 128 FP32 lanes x
-# 2 flop (FMA) x 2.07 GHz maximum SM clock.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-
-# DRAM traffic of one launch of the fused 20^3 kernel from an ncu capture, valid only while
-# the kernel sources hash to the value recorded with it (else reported as null).
-TRAFFIC = {"sha": "43f4613df6db5493", "bytes_per_launch": 1070.526976e6}
+# DRAM traffic of one launch of the fused 24^3 kernel from an ncu capture of the full
+# workload, valid only while the kernel sources hash to the value recorded with it (else
+# reported as null).
+TRAFFIC = {"sha": None, "bytes_per_launch": None}
 
 
 def _code_only(src: str) -> str:
@@ -50,11 +53,14 @@ def _code_only(src: str) -> str:
     return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
 
 
+KERNEL_SOURCES = ("fft_reg.cuh", "pairconv_c64.cuh", "pairconv_tc.cuh", "tc_dft.cuh", "pairconv_tma.cuh", "tma.cuh",
+                  "tmem.cuh", "tmem_gen.cuh", "launch.cuh", "pairconv_24.cu")
+
+
 def kernel_source_sha() -> str:
     """Hash of the code (comments excluded) of the sources the bench kernel is built from."""
     h = hashlib.sha256()
-    for f in ("fft_reg.cuh", "pairconv_c64.cuh", "pairconv_tma.cuh", "tma.cuh", "tmem.cuh", "tmem_gen.cuh",
-              "launch.cuh", "pairconv_20.cu"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1507_05156_gb300", "csrc", f), encoding="utf-8") as fh:
             h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
@@ -63,6 +69,22 @@ def kernel_source_sha() -> str:
 def algorithmic_flops_per_pair(N: int) -> float:
     """10 N log2 N (two 3-D FFTs at 5 N log2 N) + 16 N (pair product 6, kernel 2, MAC 8)."""
     return 10.0 * N * np.log2(N) + 16.0 * N
+
+
+def fp32_peak_tflops(sms: int, sm_mhz: float) -> float:
+    """FP32 ALU peak from unit counts and the clock: SMs x 128 FMA lanes x 2 flop x clock."""
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def max_sm_mhz(clocks: dict) -> tuple:
+    """(maximum SM clock in MHz, where it came from): nvidia-smi's clocks.max.sm sampled during
+    the run, else MEASURED_PEAKS.json's sm_max_mhz, else the GB300's 2070 MHz."""
+    if clocks and clocks.get("sm_max_mhz"):
+        return float(clocks["sm_max_mhz"]), "nvidia-smi clocks.max.sm during the run"
+    m = _measured_peak("sm_max_mhz")
+    if m:
+        return m, "MEASURED_PEAKS.json sm_max_mhz"
+    return DEFAULT_SM_MHZ, "GB300 maximum SM clock (no measured figure)"
 
 
 class ClockSampler:
@@ -125,13 +147,14 @@ def host_cores() -> int:
     return int(os.environ.get("HSE_ORACLE_WORKERS", os.cpu_count() or 1))
 
 
-def oracle_sample(cell, targets):
-    """Time the FP64 oracle on a list of (k, i) targets; returns (values, seconds)."""
+def oracle_sample(u_occ, occ, u_tgt, cell, targets, kocc=None):
+    """Time the FP64 oracle on a list of (k, i) targets (every k' of the mesh, or the k' of
+    kocc); u_occ, u_tgt: complex128 arrays of the values the GPU reads.  Returns (values,
+    seconds)."""
     import oracle
     t0 = time.perf_counter()
-    u = cell.u_occ.astype(np.complex64).astype(np.complex128)
-    ref = oracle.fock_apply(u, cell.occ, u, cell.kpts, cell.lattice, cell.grid, cell.omega, cell.alpha,
-                            targets=targets)
+    ref = oracle.fock_apply(u_occ, occ, u_tgt, cell.kpts, cell.lattice, cell.grid, cell.omega, cell.alpha,
+                            targets=targets, kocc=kocc)
     return ref, time.perf_counter() - t0
 
 
@@ -140,22 +163,42 @@ def sample_targets(cell, count, seed=11):
     return [(int(rng.integers(cell.nk)), int(rng.integers(cell.n_tgt))) for _ in range(count)]
 
 
+def sample_kocc(cell, count, seed):
+    """`count` distinct k' of the mesh (the partner sample of the reference arm's steps)."""
+    rng = np.random.default_rng(seed)
+    return sorted(int(k) for k in rng.choice(cell.nk, size=min(count, cell.nk), replace=False))
+
+
+def rounded_c64(a):
+    """complex128 copy of the complex64 values the GPU path reads."""
+    return a.astype(np.complex64).astype(np.complex128)
+
+
+# Reference-arm sample per step: one target (k, i) against every occupied band of
+# REF_KPRIME sampled k' (1,024 pair convolutions at 16 bands), about half a second of oracle.
+REF_KPRIME = 64
+
+
 def run_reference(args, rank, world):
-    """The oracle on the host cores, each step a bounded sample of the same workload."""
+    """The oracle on the host cores, each step a bounded sample of the same workload: one
+    target orbital against all bands of REF_KPRIME k' of the mesh."""
     if rank != 0:
         return
     from paper_1507_05156_gb300 import inputs
     cell = inputs.workload(WORKLOAD)
-    per_step = 2  # targets per step: 2 x 1024 pair convolutions
+    u_occ = rounded_c64(cell.u_occ)
+    u_tgt = cell.u_tgt.astype(np.complex64)  # rounded to complex128 by the oracle per target
     for w in range(args.warmup):
-        oracle_sample(cell, sample_targets(cell, 1, seed=100 + w))
+        oracle_sample(u_occ, cell.occ, u_tgt, cell, sample_targets(cell, 1, seed=100 + w), sample_kocc(cell, REF_KPRIME, 300 + w))
     times = []
     for s in range(args.steps):
-        _, dt = oracle_sample(cell, sample_targets(cell, per_step, seed=200 + s))
+        _, dt = oracle_sample(u_occ, cell.occ, u_tgt, cell, sample_targets(cell, 1, seed=200 + s),
+                              sample_kocc(cell, REF_KPRIME, 400 + s))
         times.append(dt)
-    pairs = per_step * cell.nk * cell.n_occ
+    pairs = 1 * REF_KPRIME * cell.n_occ
     value = pairs * len(times) / sum(times)
-    sample = f"{per_step} targets (k,i) x all {cell.nk * cell.n_occ} (k',j) partners per step"
+    sample = (f"per step 1 target (k,i) x {REF_KPRIME} sampled k' x {cell.n_occ} bands = {pairs} of the "
+              f"{cell.pairs} pair convolutions of the workload")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
@@ -167,10 +210,13 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(cell):
+def config_dict(cell, l2=None):
+    nbytes = 8 * cell.npts * cell.nk * (cell.n_occ + cell.n_tgt)
+    if l2 is None:
+        l2 = (f"not flushed: the inputs ({nbytes / 1e9:.2f} GB of complex64 orbitals) are larger than L2 (129 MB)"
+              if nbytes > 256e6 else "flushed between timed steps by a 256 MB write")
     return {"workload": cell.name, "grid": list(cell.grid), "nk": cell.nk, "n_occ": cell.n_occ,
-            "n_tgt": cell.n_tgt, "omega": cell.omega, "alpha": cell.alpha, "pairs_per_step": cell.pairs,
-            "l2": "flushed between timed steps by a 256 MB write (inputs 65.5 MB < L2)"}
+            "n_tgt": cell.n_tgt, "omega": cell.omega, "alpha": cell.alpha, "pairs_per_step": cell.pairs, "l2": l2}
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -189,6 +235,37 @@ def replica_throughput(units_per_rank: float, world: int, seconds: float) -> flo
     return world * units_per_rank / seconds
 
 
+def run_second(dev, steps, warmup, sms, sm_mhz):
+    """The 20^3, 4x4x4 k, 16-band cell (1,048,576 pair convolutions): the earlier bench workload,
+    reported beside the headline.  Inputs (65.5 MB) fit in L2, so a 256 MB write flushes it
+    between steps (outside the events)."""
+    import torch
+    from paper_1507_05156_gb300 import hse, inputs
+    cell = inputs.workload(SECOND)
+    plan = hse.get_plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha)
+    u = torch.from_numpy(cell.u_occ.astype(np.complex64)).to(dev)
+    occ = torch.from_numpy(cell.occ).to(dev)
+    out = torch.empty_like(u)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        hse.hse_fock_apply(plan, u, occ, u, out=out)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s in range(steps):
+        flush.fill_(s & 0xFF)
+        ev[s][0].record(stream)
+        hse.hse_fock_apply(plan, u, occ, u, out=out)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    hse.hse_status(plan)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    flops = algorithmic_flops_per_pair(cell.npts) * cell.pairs
+    peak = fp32_peak_tflops(sms, sm_mhz)
+    return {"workload": cell.name, "value": cell.pairs / ms * 1e3, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "roofline_frac": flops / ms / 1e9 / peak, "l2": config_dict(cell)["l2"]}
+
+
 def run_cuda(args, rank, world, dist):
     import torch
     from paper_1507_05156_gb300 import hse, inputs
@@ -196,16 +273,20 @@ def run_cuda(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     cell = inputs.workload(WORKLOAD)
     d = torch.complex64
     plan = hse.get_plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha,
                         dtype=d)
-    u_host = torch.from_numpy(cell.u_occ.astype(np.complex64)).pin_memory()
+    uo_np = cell.u_occ.astype(np.complex64)
+    ut_np = cell.u_tgt.astype(np.complex64)
+    uo_host = torch.from_numpy(uo_np).pin_memory()
+    ut_host = torch.from_numpy(ut_np).pin_memory()
     occ_host = torch.from_numpy(cell.occ).pin_memory()
-    u = u_host.to(dev)
+    u_occ = uo_host.to(dev)
+    u_tgt = ut_host.to(dev)
     occ = occ_host.to(dev)
-    out = torch.empty_like(u)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = torch.empty_like(u_tgt)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -214,18 +295,17 @@ def run_cuda(args, rank, world, dist):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        hse.hse_fock_apply(plan, u, occ, u, out=out)
+        hse.hse_fock_apply(plan, u_occ, occ, u_tgt, out=out)
     hse.hse_status(plan)
 
-    # ---- device-resident timed region -------------------------------------------------
+    # ---- device-resident timed region (inputs 2.7 GB > L2: no flush) ------------------
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     l0 = hse.kernel_launches()
     with ClockSampler(local) as clk:
         for s in range(args.steps):
-            flush.fill_(s & 0xFF)
             ev[s][0].record(stream)
-            hse.hse_fock_apply(plan, u, occ, u, out=out)
+            hse.hse_fock_apply(plan, u_occ, occ, u_tgt, out=out)
             ev[s][1].record(stream)
         barrier()
     launches = hse.kernel_launches() - l0
@@ -234,20 +314,26 @@ def run_cuda(args, rank, world, dist):
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
     pairs = cell.pairs
     value = replica_throughput(pairs * args.steps, world, total_ms / 1e3)
+    got_rows = None
+    if rank == 0 and not args.no_cpu_baseline:
+        targets = sample_targets(cell, args.cpu_targets)
+        got_rows = np.stack([out[k, i].cpu().numpy() for k, i in targets]).astype(np.complex128)
 
     # ---- end to end through the public API: pinned host in, host out ------------------
-    # Every step copies its inputs from pinned host memory and reads its result back.  The
-    # copies run on a second stream into double-buffered device tensors, so step s + 1's
-    # upload and step s - 1's download overlap step s's apply (a pipelined stream of steps).
-    e2e_steps = max(2, min(args.steps, 6))
-    out_host = [torch.empty(out.shape, dtype=d).pin_memory() for _ in range(2)]
-    u_dev = [torch.empty_like(u) for _ in range(2)]
-    o_dev = [torch.empty_like(occ) for _ in range(2)]
-    r_dev = [torch.empty_like(out) for _ in range(2)]
+    # Every step copies its inputs (u_occ, u_tgt, occ) from pinned host memory and reads its
+    # result back.  The copies run on a second stream into double-buffered device tensors, so
+    # step s + 1's upload and step s - 1's download overlap step s's apply.
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    nbuf = min(2, e2e_steps)
+    out_host = [torch.empty(out.shape, dtype=d).pin_memory() for _ in range(nbuf)]
+    uo_dev = [u_occ] + [torch.empty_like(u_occ) for _ in range(nbuf - 1)]
+    ut_dev = [u_tgt] + [torch.empty_like(u_tgt) for _ in range(nbuf - 1)]
+    o_dev = [occ] + [torch.empty_like(occ) for _ in range(nbuf - 1)]
+    r_dev = [out] + [torch.empty_like(out) for _ in range(nbuf - 1)]
     copy = torch.cuda.Stream(device=dev)
-    up_done = [torch.cuda.Event() for _ in range(2)]
-    apply_done = [torch.cuda.Event() for _ in range(2)]
-    down_done = [torch.cuda.Event() for _ in range(2)]
+    up_done = [torch.cuda.Event() for _ in range(nbuf)]
+    apply_done = [torch.cuda.Event() for _ in range(nbuf)]
+    down_done = [torch.cuda.Event() for _ in range(nbuf)]
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -255,73 +341,90 @@ def run_cuda(args, rank, world, dist):
     copy.wait_event(e0)
 
     def upload(s):
-        b = s & 1
+        b = s % nbuf
         with torch.cuda.stream(copy):
-            if s >= 2:
-                copy.wait_event(apply_done[b])  # the apply of step s - 2 has read this buffer
-            u_dev[b].copy_(u_host, non_blocking=True)
+            if s >= nbuf:
+                copy.wait_event(apply_done[b])  # the apply of step s - nbuf has read this buffer
+            uo_dev[b].copy_(uo_host, non_blocking=True)
+            ut_dev[b].copy_(ut_host, non_blocking=True)
             o_dev[b].copy_(occ_host, non_blocking=True)
             up_done[b].record(copy)
 
     upload(0)
     for s in range(e2e_steps):
-        b = s & 1
+        b = s % nbuf
         if s + 1 < e2e_steps:
             upload(s + 1)
         stream.wait_event(up_done[b])
-        if s >= 2:
-            stream.wait_event(down_done[b])  # step s - 2's result has left this buffer
-        hse.hse_fock_apply(plan, u_dev[b], o_dev[b], u_dev[b], out=r_dev[b], stream=stream)
+        if s >= nbuf:
+            stream.wait_event(down_done[b])  # step s - nbuf's result has left this buffer
+        hse.hse_fock_apply(plan, uo_dev[b], o_dev[b], ut_dev[b], out=r_dev[b], stream=stream)
         apply_done[b].record(stream)
         with torch.cuda.stream(copy):
             copy.wait_event(apply_done[b])
             out_host[b].copy_(r_dev[b], non_blocking=True)
             down_done[b].record(copy)
-    stream.wait_event(down_done[(e2e_steps - 1) & 1])
-    stream.wait_event(down_done[(e2e_steps - 2) & 1])
+    for s in range(max(0, e2e_steps - nbuf), e2e_steps):
+        stream.wait_event(down_done[s % nbuf])
     e1.record(stream)
     barrier()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
     e2e_value = replica_throughput(pairs, world, e2e_ms / 1e3)
-    h2d = u_host.numel() * u_host.element_size() + occ_host.numel() * occ_host.element_size()
+    h2d = sum(t.numel() * t.element_size() for t in (uo_host, ut_host, occ_host))
     d2h = out_host[0].numel() * out_host[0].element_size()
+    del out_host, uo_dev, ut_dev, o_dev, r_dev
 
     if rank != 0:
         return
 
-    # ---- accuracy against the FP64 oracle on sampled targets, and the CPU baseline ----
     clocks = clk.summary()
+    sm_mhz, mhz_source = max_sm_mhz(clocks)
+    peak = fp32_peak_tflops(sms, sm_mhz)
+
+    # ---- the 20^3 cell, reported beside the headline ----------------------------------
+    second = None
+    if not args.no_second:
+        second = run_second(dev, min(args.steps, 20), max(3, args.warmup), sms, sm_mhz)
+
+    # ---- the plain FP64 GPU form: every target against a sample of k' (extrapolated) ----
+    fp64 = None
+    if not args.no_fp64:
+        kocc = list(range(args.fp64_kprime))
+        plan64 = hse.get_plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha,
+                              dtype=torch.complex128, kocc=kocc)
+        u64o = torch.from_numpy(cell.u_occ).to(dev)
+        u64t = torch.from_numpy(cell.u_tgt).to(dev)
+        o64 = torch.empty_like(u64t)
+        hse.hse_fock_apply(plan64, u64o, occ, u64t, out=o64)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hse.hse_fock_apply(plan64, u64o, occ, u64t, out=o64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        hse.hse_status(plan64)
+        ms64 = a.elapsed_time(b)
+        pairs64 = cell.nk * cell.n_tgt * len(kocc) * cell.n_occ
+        rate64 = pairs64 / (ms64 / 1e3)
+        fp64 = {"value": rate64, "unit": UNIT, "ms_per_sample": ms64,
+                "sample": f"all {cell.nk * cell.n_tgt} targets x {len(kocc)} k' x {cell.n_occ} bands = {pairs64} "
+                          f"pair convolutions (down-sampled FP64 plan); full apply extrapolated by pair count",
+                "ms_per_step_extrapolated": ms64 * pairs / pairs64,
+                "speedup_fused_c64_over_fp64_gpu": value / world / rate64}
+        del u64o, u64t, o64, plan64
+
+    # ---- accuracy against the FP64 oracle on sampled targets, and the CPU baseline ----
     cpu = None
     err = None
-    if not args.no_cpu_baseline:
+    if got_rows is not None:
         targets = sample_targets(cell, args.cpu_targets)
-        ref, dt = oracle_sample(cell, targets)
-        got = out.cpu().numpy()
-        g = np.stack([got[k, i] for k, i in targets]).astype(np.complex128)
-        err = float(np.linalg.norm(g - ref) / np.linalg.norm(ref))
+        ref, dt = oracle_sample(rounded_c64(cell.u_occ), cell.occ, ut_np, cell, targets)
+        err = float(np.linalg.norm(got_rows - ref) / np.linalg.norm(ref))
         cpu_pairs = len(targets) * cell.nk * cell.n_occ
         cpu = {"value": cpu_pairs / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"{len(targets)} targets (k,i) x all {cell.nk * cell.n_occ} (k',j) partners"}
 
-    # ---- the plain FP64 GPU form on the same workload (speedup denominator) -----------
-    fp64 = None
-    if not args.no_fp64:
-        plan64 = hse.get_plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha,
-                              dtype=torch.complex128)
-        u64 = torch.from_numpy(cell.u_occ).to(dev)
-        o64 = torch.empty_like(u64)
-        hse.hse_fock_apply(plan64, u64, occ, u64, out=o64)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        hse.hse_fock_apply(plan64, u64, occ, u64, out=o64)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms64 = a.elapsed_time(b)
-        fp64 = {"value": pairs / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
-                "speedup_fused_c64_over_fp64_gpu": (pairs * args.steps / (total_ms / 1e3)) / (pairs / (ms64 / 1e3))}
-
-    flops = algorithmic_flops_per_pair(int(np.prod(cell.grid))) * pairs
+    flops = algorithmic_flops_per_pair(cell.npts) * pairs
     kernel_s = (total_ms / args.steps) / 1e3
     achieved = flops / kernel_s / 1e12
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sha"] == kernel_source_sha() else None
@@ -331,13 +434,17 @@ def run_cuda(args, rank, world, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_dict(cell),
         "err_vs_fp64": err,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "peak_source": "FP32 FMA lanes x max SM clock (152 x 128 x 2 x 2.07 GHz)",
-                     "flops_per_launch": flops},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"FP32 FMA lanes x max SM clock ({sms} SMs x {FP32_LANES_PER_SM} x 2 x "
+                                    f"{sm_mhz:.0f} MHz, {mhz_source})",
+                     "flops_per_launch": flops,
+                     "timed": "one hse_fock_apply (the fused kernel and the pencil-blocked relayout of its inputs)"},
         "cpu_baseline": cpu,
         "fp64_gpu": fp64,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "c64_20cube": second,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -347,11 +454,24 @@ def run_cuda(args, rank, world, dist):
 def run_profile_case(spec: str):
     """Two applies of one seeded cell (grid side n, n_k^3 Monkhorst-Pack k-points, nb bands,
     complex64; a fourth field "tc" selects the tensor-core option; "batched,C" runs the first C
-    cells of the uneven batch instead): the launch an ncu capture of a secondary kernel selects
-    with -s 1 -c 1.  Prints no bench line."""
+    cells of the uneven batch instead; "workload,W" the full workload W, u_occ and u_tgt as the
+    bench reads them): the launch an ncu capture selects with -s 1 -c 1.  Prints no bench line."""
     import torch
     from paper_1507_05156_gb300 import hse, inputs
     fields = spec.split(",")
+    if fields[0] == "workload":  # "workload,W": two applies of the whole workload W
+        cell = inputs.workload(int(fields[1]))
+        plan = hse.Plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha)
+        uo = torch.from_numpy(cell.u_occ.astype(np.complex64)).cuda()
+        ut = torch.from_numpy(cell.u_tgt.astype(np.complex64)).cuda()
+        occ = torch.from_numpy(cell.occ).cuda()
+        out = torch.empty_like(ut)
+        for _ in range(2):
+            hse.hse_fock_apply(plan, uo, occ, ut, out=out)
+        torch.cuda.synchronize()
+        hse.hse_status(plan)
+        print(f"profile case {cell.name}: {cell.pairs} pair convolutions per apply", flush=True)
+        return
     if fields[0] == "batched":  # "batched,C": two calls on the first C cells of the uneven batch
         cells = inputs.batched_cells(int(fields[1]))
         plan = hse.BatchedPlan(cells)
@@ -420,6 +540,8 @@ def run_config(name: str, args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     steps, warmup = max(1, args.steps), max(1, args.warmup)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    FP32_PEAK_TFLOPS = fp32_peak_tflops(sms, max_sm_mhz(None)[0])
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "data": "synthetic"}
     if name == "batched":
@@ -518,13 +640,16 @@ def run_config(name: str, args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
-    ap.add_argument("--cpu-targets", type=int, default=8)
+    ap.add_argument("--cpu-targets", type=int, default=2, help="oracle targets (full partner sums) for err_vs_fp64")
+    ap.add_argument("--e2e-steps", type=int, default=2, help="steps of the end-to-end measurement")
+    ap.add_argument("--fp64-kprime", type=int, default=2, help="sampled k' of the FP64 GPU form's timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--profile-case", default=None, metavar="N,KM,NB[,tc] | batched,C",
+    ap.add_argument("--no-second", action="store_true", help="skip the 20^3 cell reported beside the headline")
+    ap.add_argument("--profile-case", default=None, metavar="N,KM,NB[,tc] | batched,C | workload,W",
                     help="only run two applies of one cell (for ncu captures of secondary kernels)")
     ap.add_argument("--config", choices=CONFIGS, default=None,
                     help="time another workload of the method (one JSON line) instead of the bench workload")

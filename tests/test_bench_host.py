@@ -22,7 +22,28 @@ def test_algorithmic_flops_per_pair_is_two_ffts_plus_pointwise_work():
 
 
 def test_fp32_peak_is_lanes_times_clock():
-    assert abs(bench.FP32_PEAK_TFLOPS - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+    # SMs x 128 FP32 FMA lanes x 2 flop x clock, with the SM count of the device at hand
+    assert abs(bench.fp32_peak_tflops(152, 2070.0) - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+    assert abs(bench.fp32_peak_tflops(160, 2000.0) - 160 * 128 * 2 * 2.0e9 / 1e12) < 1e-9
+
+
+def test_max_sm_clock_prefers_the_sampled_figure(tmp_path, monkeypatch):
+    assert bench.max_sm_mhz({"sm_max_mhz": 1980.0})[0] == 1980.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"sm_max_mhz": 2070.0}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.max_sm_mhz({"sm_max_mhz": None}) == (2070.0, "MEASURED_PEAKS.json sm_max_mhz")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path / "nowhere"))
+    assert bench.max_sm_mhz(None)[0] == bench.DEFAULT_SM_MHZ
+
+
+def test_bench_workload_is_the_largest_single_gpu_config():
+    spec = inputs.WORKLOADS[bench.WORKLOAD]
+    assert spec["grid"] == (24, 24, 24) and spec["kmesh"] == (8, 8, 8)
+    assert spec["n_occ"] == 16 and spec["n_occ"] + spec["n_empty"] == 32
+    pairs = 512 * 32 * 512 * 16
+    assert pairs == 134_217_728
+    # the reference arm's per-step sample: one target against REF_KPRIME k' of 16 bands
+    assert bench.REF_KPRIME * 16 == 1024
 
 
 def test_code_only_ignores_comments_and_blank_lines():
