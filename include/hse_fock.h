@@ -183,15 +183,20 @@ const char *hse_strerror(int code);
  *
  * Scratch: one static __device__ array of HSE_NOALLOC_SCRATCH_BYTES (4 MiB) that every GPU
  * loading this library holds until the process exits.  It must hold
- *   align256(24 nk) + align256(4 nk^2) + align256(4 nk^2 N) + align256(8 nk n_occ) bytes
- * (N = grid points, align256 rounds up to 256); larger problems return HSE_ERR_INVALID_ARG
- * before any device work.  Example: a 12^3 grid with 8 k-points needs about 0.44 MiB.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.  All calls
- * share the one array and each call overwrites all of it that it reads, but calls that
- * overlap on the GPU (other streams, other host threads) race on it: serialise them.
- * p->kpts is read on the host (copied with cudaMemcpyAsync on `stream`); u_occ, occ and
- * e_x are device pointers as for hse_exchange_energy.  Asynchronous on `stream`. */
+ *   256 + align256(4 nk^2) + align256(4 nk^2 N) + align256(8 nk n_occ) bytes
+ * (N = grid points, align256 rounds up to 256), and nk must be at most 128; larger problems
+ * return HSE_ERR_INVALID_ARG before any device work.  Example: a 12^3 grid with 8 k-points
+ * needs about 0.44 MiB, a 24^3 grid with 8 k-points about 3.4 MiB.
+ * Set-up: the first call on each device (and the first after that device's context has been
+ * replaced, e.g. by cudaDeviceReset) looks up the array's device address with
+ * cudaGetSymbolAddress, with that device current; make that first call before any stream
+ * capture.  All calls share the one array and each call clears or overwrites all of it that
+ * it reads, but calls that overlap on the GPU (other streams, other host threads) race on it:
+ * serialise them.  p->kpts is read on the host during the call and reaches the kernels by
+ * value (the call copies nothing from host memory); u_occ, occ and e_x are device pointers
+ * as for hse_exchange_energy.  Asynchronous on `stream`.  There is no plan, so no status
+ * word for hse_status: if a bounded device-side wait of the call gives up, *e_x is set to NaN
+ * (the test hook HSE_INJECT_SKIP_FILL=1 of hse_status applies here too, read at each call). */
 #define HSE_NOALLOC_SCRATCH_BYTES (4u << 20)
 int hse_exchange_energy_noalloc(const hse_problem *p, const void *u_occ, const double *occ,
                                 double *e_x, hse_stream_t stream);
