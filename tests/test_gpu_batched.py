@@ -40,8 +40,9 @@ def test_small_mixed_batch_vs_oracle_and_graph_replay():
 
 def test_uneven_batch_32_cells_matches_single_cell_path():
     """32 cells, grids from {12,16,18,20,24}^3, k-meshes 2^3..4^3, 4..16 bands: the batched
-    launch against the single-cell launches (same arithmetic, different schedules), and a
-    sample of targets of the smallest cells against the oracle."""
+    launch against the single-cell launches (same arithmetic, different schedules), and one
+    seeded target (k, i) of every cell, 24^3 cells included, element by element against the
+    oracle (its full sum over the cell's k' and bands)."""
     cells = inputs.batched_cells()
     assert len(cells) == 32
     plan = hse.BatchedPlan(cells)
@@ -53,14 +54,17 @@ def test_uneven_batch_32_cells_matches_single_cell_path():
         p1 = hse.get_plan(c.grid, c.lattice, c.kpts, c.n_occ, c.n_tgt, c.omega, c.alpha, dtype=torch.complex64)
         single = hse.hse_fock_apply(p1, u, o, u)
         assert float((x - single).abs().max() / single.abs().max()) <= 1e-5
-    smallest = sorted(range(32), key=lambda i: cells[i].pairs * cells[i].npts)[:3]
-    for i in smallest:
-        c = cells[i]
+    rng = np.random.default_rng(77)
+    errs = []
+    for i, c in enumerate(cells):
         u64 = c.u_occ.astype(np.complex64).astype(np.complex128)
-        targets = [(0, 0), (len(c.kpts) - 1, c.n_tgt - 1)]
+        targets = [(int(rng.integers(len(c.kpts))), int(rng.integers(c.n_tgt)))]
         ref = oracle.fock_apply(u64, c.occ, u64, c.kpts, c.lattice, c.grid, c.omega, c.alpha, targets=targets)
         got = np.stack([out[i][k, b].cpu().numpy() for k, b in targets])
-        assert rel(got, ref) <= 1e-5
+        errs.append((c.name, rel(got, ref)))
+    print("batched cells vs oracle (one target each):", ", ".join(f"{n} {e:.1e}" for n, e in errs))
+    assert any(c.grid[0] == 24 for c in cells)
+    assert max(e for _, e in errs) <= 1e-5
 
 
 def test_autotune_cache_round_trip(tmp_path, monkeypatch):

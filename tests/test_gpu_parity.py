@@ -206,9 +206,10 @@ def test_many_partners_beyond_occupation_cache():
 
 def test_workload_24cube_k8_sampled_and_energy_consistency():
     """24^3 grid, 8x8x8 k-mesh (512 k), 16 occupied + 16 empty targets: 134,217,728 pair
-    convolutions in one apply.  Two sampled targets (an occupied and an empty band) are
-    checked element by element against the oracle; the FP64 exchange-energy reduction is
-    checked against an FP64 dot of the full complex64 output computed on the host."""
+    convolutions in one apply.  Three sampled targets (occupied and empty bands) are checked
+    element by element against the oracle, and so are their expectation values
+    dV <u_i|V_x u_i>; the FP64 exchange-energy reduction is checked against an FP64 dot of the
+    full complex64 output computed on the host."""
     c = inputs.workload(2)
     d = torch.complex64
     u_tgt = torch.from_numpy(c.u_tgt.astype(np.complex64)).cuda()
@@ -217,12 +218,20 @@ def test_workload_24cube_k8_sampled_and_energy_consistency():
     plan = hse.get_plan(c.grid, c.lattice, c.kpts, c.n_occ, c.n_tgt, c.omega, c.alpha, dtype=d)
     out = hse.hse_fock_apply(plan, u_occ, occ, u_tgt)
     hse.hse_status(plan)
-    targets = [(137, 5), (402, 23)]
+    targets = [(137, 5), (402, 23), (9, 0)]
     uo = c.u_occ.astype(np.complex64).astype(np.complex128)
     ut = c.u_tgt.astype(np.complex64).astype(np.complex128)
     ref = oracle.fock_apply(uo, c.occ, ut, c.kpts, c.lattice, c.grid, c.omega, c.alpha, targets=targets)
     got = np.stack([out[k, i].cpu().numpy() for k, i in targets])
     assert rel_err(got, ref) <= 1e-5
+    # per-target expectation values dV <u_i | V_x u_i> (the terms of E_x, Sec. V Eq. "Eex01"):
+    # the oracle's against the GPU output's, both reduced in FP64 on the host
+    dV = abs(np.linalg.det(c.lattice)) / c.npts
+    for t, (k, i) in enumerate(targets):
+        e_ref = dV * np.real(np.vdot(ut[k, i], ref[t]))
+        e_gpu = dV * np.real(np.vdot(ut[k, i], got[t].astype(np.complex128)))
+        assert e_ref < 0
+        assert abs(e_gpu - e_ref) <= 1e-6 * abs(e_ref), (k, i, e_gpu, e_ref)
     # E_x from the fused energy epilogue vs an FP64 dot of the apply output (occupied block)
     plan_e = hse.get_plan(c.grid, c.lattice, c.kpts, c.n_occ, c.n_occ, c.omega, c.alpha, dtype=d)
     e = hse.hse_exchange_energy(plan_e, u_occ, occ).item()

@@ -7,7 +7,7 @@
   dt = 0.02, uniform field 0.005 along x, backpropagated with per-step checkpointing; the
   gradient w.r.t. omega and a directional derivative w.r.t. the initial orbitals are checked
   against central finite differences of the same propagation (complex128), and the complex64
-  run against the complex128 one.
+  run against the complex128 one within a bound derived from the FP32 rounding per step.
 """
 import numpy as np
 import pytest
@@ -131,9 +131,22 @@ def test_differentiation_workload_gradients_vs_finite_differences():
     _loss(psi_T32, w.to(torch.complex64)).backward()
     with torch.no_grad():
         psi_T64 = run(psi0, c.omega)
-    assert rel(psi_T32.detach().cpu().numpy(), psi_T64.cpu().numpy()) <= 1e-5
-    assert rel(p32.grad.cpu().numpy(), g_psi.cpu().numpy()) <= 1e-4
-    assert abs(float(om32.grad) - g_om) <= 1e-4 * abs(g_om)
+    e_fwd = rel(psi_T32.detach().cpu().numpy(), psi_T64.cpu().numpy())
+    e_psi = rel(p32.grad.cpu().numpy(), g_psi.cpu().numpy())
+    e_om = abs(float(om32.grad) - g_om) / abs(g_om)
+    print(f"complex64 vs complex128 through {nsteps} steps: psi(T) {e_fwd:.2e}, d/dpsi0 {e_psi:.2e}, "
+          f"d/domega {e_om:.2e}")
+    # Bound (derived, not fitted): each complex64 step rounds the state to FP32 in the four
+    # additions of its Taylor terms (4 x 6e-8 = 2.4e-7 relative) and adds the FP32 error of its
+    # operator applications scaled by the terms' size (dt |h| about 0.12 on these band-limited
+    # orbitals, times about 1.5e-7 per V_x application at 16^3: < 2e-8).  The step maps are
+    # close to unitary, so over 20 steps the errors add at most linearly: 20 x 2.6e-7 = 5.2e-6
+    # for psi(T).  The backward sweep re-runs the forward and applies the adjoint of every step
+    # with the same per-step error, which at most doubles that for the gradients: about 1e-5,
+    # the stated complex64 tolerance.
+    assert e_fwd <= 5.2e-6
+    assert e_psi <= 1e-5
+    assert e_om <= 1e-5
 
 
 # ---------------------------------------------------------------------------
