@@ -279,10 +279,12 @@ struct hse_plan_s {
   size_t work_pairs = 0;
   double2* vx64 = nullptr;   // [nk][max(n_occ, n_tgt)][N]
   bool blocked = true;       // pencil-load launches read pencil-blocked copies (HSE_PENCIL_BLOCKS=0: no)
-  int blocks_per_sm = 0;     // fused-kernel variant: 0 default, -1/-2 staged-partner layouts, 1/2/3 pencil loads,
+  int blocks_per_sm = 0;     // fused-kernel variant: 0 default, -1/-2 staged-partner layouts, 1/2/3/5 pencil loads,
                              // kTcVariant the tensor-core form (HSE_C64_TC)
   bool tc = false;           // created as HSE_C64_TC (p.dtype then reads HSE_C64)
   int inject = 0;            // test hook (HSE_INJECT_SKIP_FILL=1 at plan creation)
+  long long alloc_count = 0;   // device allocations made by this plan so far (plan_malloc)
+  long long fail_alloc_at = -1;  // test hook (HSE_FAIL_ALLOC_AT=k at plan creation): allocation k fails
   int nsplit[3] = {1, 1, 1};  // k'-loop splits of the fused kernel per OwnerRole
   float2* split_buf = nullptr;  // [nsplit][nk_own][n_own][N] partial outputs when nsplit > 1
   size_t split_buf_elems = 0;
@@ -398,6 +400,25 @@ void autotune_store(const std::string& key, int split) {
 }
 
 int cuda_fail(cudaError_t e) { return e == cudaSuccess ? HSE_OK : (e == cudaErrorMemoryAllocation ? HSE_ERR_NOMEM : HSE_ERR_CUDA); }
+
+// Every device allocation of a plan goes through here.  Test hook: a plan created while the
+// environment variable HSE_FAIL_ALLOC_AT=k is set has its k-th allocation (0-based, counted
+// over the plan's life, creation included) fail as if the device were out of memory, without
+// allocating anything, so that the clean-up of every failure path can be checked.
+template <class T>
+cudaError_t plan_malloc(hse_plan plan, T** p, size_t bytes) {
+  if (plan->alloc_count++ == plan->fail_alloc_at) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc((void**)p, bytes);
+}
+
+// HSE_FAIL_ALLOC_AT, read when a plan is created (-1: the hook is off).
+long long fail_alloc_from_env() {
+  const char* env = std::getenv("HSE_FAIL_ALLOC_AT");
+  return env ? std::atoll(env) : -1;
+}
 
 bool invert3(const double* A, double* inv) {
   const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
@@ -559,10 +580,11 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   plan->p.kocc = plan->sampled ? plan->kocc.data() : nullptr;
   cudaGetDevice(&plan->device);
   if (const char* env = std::getenv("HSE_INJECT_SKIP_FILL")) plan->inject = std::atoi(env) == 1 ? 1 : 0;
+  plan->fail_alloc_at = fail_alloc_from_env();
   if (const char* env = std::getenv("HSE_PENCIL_BLOCKS")) plan->blocked = std::atoi(env) != 0;
   if (const char* env = std::getenv("HSE_BLOCKS_PER_SM")) {
     const int v = std::atoi(env);
-    plan->blocks_per_sm = (v < -2 || v > 3) ? 0 : v;
+    plan->blocks_per_sm = (v < -2 || v > 5 || v == kTcVariant) ? 0 : v;
   }
   if (plan->tc) plan->blocks_per_sm = kTcVariant;
   const int n1 = p->grid[0], n2 = p->grid[1], n3 = p->grid[2];
@@ -612,12 +634,12 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
       return rc;                   \
     }                              \
   } while (0)
-  HSE_TRY(cudaMalloc(&plan->qidx, qidx.size() * sizeof(int)));
-  HSE_TRY(cudaMalloc(&plan->qvec, qvec.size() * sizeof(double)));
-  HSE_TRY(cudaMalloc(&plan->v64, nq * N * sizeof(double)));
-  HSE_TRY(cudaMalloc(&plan->dv64, nq * N * sizeof(double)));
-  HSE_TRY(cudaMalloc(&plan->v32, nq * N * sizeof(float)));
-  HSE_TRY(cudaMalloc(&plan->dv32, nq * N * sizeof(float)));
+  HSE_TRY(plan_malloc(plan, &plan->qidx, qidx.size() * sizeof(int)));
+  HSE_TRY(plan_malloc(plan, &plan->qvec, qvec.size() * sizeof(double)));
+  HSE_TRY(plan_malloc(plan, &plan->v64, nq * N * sizeof(double)));
+  HSE_TRY(plan_malloc(plan, &plan->dv64, nq * N * sizeof(double)));
+  HSE_TRY(plan_malloc(plan, &plan->v32, nq * N * sizeof(float)));
+  HSE_TRY(plan_malloc(plan, &plan->dv32, nq * N * sizeof(float)));
   if (plan->p.dtype == HSE_C64) {
     // Split the k' loop so that the work items fill the resident CTA slots in nearly whole
     // waves; the partial outputs are summed by reduce_splits.
@@ -659,33 +681,33 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
       if (o != ROLE_ENERGY) comp = std::max(comp, (size_t)best * k_own[o] * owners[o] * 2 * blocked_stride(n1));
     }
     if (buf) {
-      HSE_TRY(cudaMalloc(&plan->split_buf, buf * sizeof(float2)));
+      HSE_TRY(plan_malloc(plan, &plan->split_buf, buf * sizeof(float2)));
       plan->split_buf_elems = buf;
     }
-    HSE_TRY(cudaMalloc(&plan->comp_buf, comp * sizeof(float2)));
+    HSE_TRY(plan_malloc(plan, &plan->comp_buf, comp * sizeof(float2)));
   }
   {
     const size_t np = std::max((size_t)plan->nsplit[ROLE_TGT] * nk * p->n_tgt,
                                (size_t)plan->nsplit[ROLE_ENERGY] * nk * p->n_occ);
-    HSE_TRY(cudaMalloc(&plan->partial, std::max(np, (size_t)nk * nown) * sizeof(double)));
+    HSE_TRY(plan_malloc(plan, &plan->partial, std::max(np, (size_t)nk * nown) * sizeof(double)));
   }
   if (plan->sampled) {
     std::vector<int> kinv(nk, -1);
     for (int i = 0; i < nkq; ++i) kinv[plan->kocc[i]] = i;
     const size_t sub_bytes = (size_t)nkq * p->n_occ * N * elem_bytes(p->dtype);
-    HSE_TRY(cudaMalloc(&plan->d_kocc, (size_t)nkq * sizeof(int)));
-    HSE_TRY(cudaMalloc(&plan->d_kinv, (size_t)nk * sizeof(int)));
+    HSE_TRY(plan_malloc(plan, &plan->d_kocc, (size_t)nkq * sizeof(int)));
+    HSE_TRY(plan_malloc(plan, &plan->d_kinv, (size_t)nk * sizeof(int)));
     HSE_TRY(cudaMemcpy(plan->d_kocc, plan->kocc.data(), (size_t)nkq * sizeof(int), cudaMemcpyHostToDevice));
     HSE_TRY(cudaMemcpy(plan->d_kinv, kinv.data(), (size_t)nk * sizeof(int), cudaMemcpyHostToDevice));
-    HSE_TRY(cudaMalloc(&plan->u_sub, sub_bytes));
-    HSE_TRY(cudaMalloc(&plan->g_sub, sub_bytes));
-    HSE_TRY(cudaMalloc(&plan->occ_sub, (size_t)nkq * p->n_occ * sizeof(double)));
+    HSE_TRY(plan_malloc(plan, &plan->u_sub, sub_bytes));
+    HSE_TRY(plan_malloc(plan, &plan->g_sub, sub_bytes));
+    HSE_TRY(plan_malloc(plan, &plan->occ_sub, (size_t)nkq * p->n_occ * sizeof(double)));
   }
-  HSE_TRY(cudaMalloc(&plan->status, sizeof(int)));
+  HSE_TRY(plan_malloc(plan, &plan->status, sizeof(int)));
   HSE_TRY(cudaMemset(plan->status, 0, sizeof(int)));
   HSE_TRY(cudaMemcpy(plan->qidx, qidx.data(), qidx.size() * sizeof(int), cudaMemcpyHostToDevice));
   HSE_TRY(cudaMemcpy(plan->qvec, qvec.data(), qvec.size() * sizeof(double), cudaMemcpyHostToDevice));
-  HSE_TRY(cudaMalloc(&plan->dkpts, (size_t)nk * 3 * sizeof(double)));
+  HSE_TRY(plan_malloc(plan, &plan->dkpts, (size_t)nk * 3 * sizeof(double)));
   HSE_TRY(cudaMemcpy(plan->dkpts, plan->kpts.data(), (size_t)nk * 3 * sizeof(double), cudaMemcpyHostToDevice));
   if (plan->p.dtype == HSE_C128) {
     // staged batch: all (i, k', j) of one k in chunks of k' up to ~512 MB
@@ -695,8 +717,8 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
     nkp = std::min<size_t>(nkp, (size_t)nkq);
     // at least two occupied x target batches: the VJP w.r.t. u_occ runs two at a time
     plan->work_pairs = std::max(nkp * per_kp, 2 * (size_t)p->n_occ * p->n_tgt);
-    HSE_TRY(cudaMalloc(&plan->work, plan->work_pairs * N * sizeof(double2)));
-    HSE_TRY(cudaMalloc(&plan->vx64, (size_t)nk * nown * N * sizeof(double2)));
+    HSE_TRY(plan_malloc(plan, &plan->work, plan->work_pairs * N * sizeof(double2)));
+    HSE_TRY(plan_malloc(plan, &plan->vx64, (size_t)nk * nown * N * sizeof(double2)));
   }
   TableArgs t{};
   t.qvec = plan->qvec;
@@ -787,7 +809,7 @@ int to_blocked(hse_plan plan, int mode, PairArgs& a, cudaStream_t st) {
     cudaFree(plan->blk_buf);
     plan->blk_buf = nullptr;
     plan->blk_elems = 0;
-    const cudaError_t e = cudaMalloc(&plan->blk_buf, need * sizeof(float2));
+    const cudaError_t e = plan_malloc(plan, &plan->blk_buf, need * sizeof(float2));
     if (e != cudaSuccess) return cuda_fail(e);
     plan->blk_elems = need;
   }
@@ -843,7 +865,7 @@ int run_pairconv(hse_plan plan, int mode, PairArgs a, int n_own, cudaStream_t st
       cudaFree(plan->spec_buf);
       plan->spec_buf = nullptr;
       plan->spec_elems = 0;
-      e = cudaMalloc(&plan->spec_buf, spec_need * sizeof(float2));
+      e = plan_malloc(plan, &plan->spec_buf, spec_need * sizeof(float2));
       if (e != cudaSuccess) return cuda_fail(e);
       plan->spec_elems = spec_need;
     }
@@ -851,7 +873,7 @@ int run_pairconv(hse_plan plan, int mode, PairArgs a, int n_own, cudaStream_t st
       cudaFree(plan->wpartial);
       plan->wpartial = nullptr;
       plan->wpartial_elems = 0;
-      e = cudaMalloc(&plan->wpartial, (size_t)items * sizeof(double));
+      e = plan_malloc(plan, &plan->wpartial, (size_t)items * sizeof(double));
       if (e != cudaSuccess) return cuda_fail(e);
       plan->wpartial_elems = (size_t)items;
     }
@@ -1280,7 +1302,7 @@ int hse_taylor_step(hse_plan plan, const void* psi, const double* occ, const dou
     return HSE_ERR_ALIAS;
   for (void*& b : plan->tay)
     if (!b) {
-      const cudaError_t e = cudaMalloc(&b, bytes);
+      const cudaError_t e = plan_malloc(plan, &b, bytes);
       if (e != cudaSuccess) return cuda_fail(e);
     }
   cudaStream_t st = S(stream);
@@ -1309,8 +1331,8 @@ int hse_current(hse_plan plan, const void* psi, const double* occ, const double*
   const hse_problem& p = plan->p;
   const size_t norb = (size_t)p.nk * p.n_occ;
   if (!plan->cur_work) {
-    cudaError_t e = cudaMalloc(&plan->cur_work, norb * plan->N * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc(&plan->cur_partial, norb * 3 * sizeof(double));
+    cudaError_t e = plan_malloc(plan, &plan->cur_work, norb * plan->N * sizeof(double2));
+    if (e == cudaSuccess) e = plan_malloc(plan, &plan->cur_partial, norb * 3 * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(e);
   }
   CurArgs a{};
@@ -1347,7 +1369,7 @@ int hse_orthonormalize(hse_plan plan, void* u, int nbands, hse_stream_t stream) 
     cudaFree(plan->ortho_work);
     plan->ortho_work = nullptr;
     plan->ortho_elems = 0;
-    const cudaError_t e = cudaMalloc(&plan->ortho_work, count * sizeof(double2));
+    const cudaError_t e = plan_malloc(plan, &plan->ortho_work, count * sizeof(double2));
     if (e != cudaSuccess) return cuda_fail(e);
     plan->ortho_elems = count;
   }
@@ -1361,7 +1383,7 @@ int hse_hartree_potential(hse_plan plan, const void* psi, const double* occ, dou
   if (!aligned16(psi)) return HSE_ERR_INVALID_ARG;
   const hse_problem& p = plan->p;
   if (!plan->hart_work) {
-    const cudaError_t e = cudaMalloc(&plan->hart_work, (size_t)plan->N * sizeof(double2));
+    const cudaError_t e = plan_malloc(plan, &plan->hart_work, (size_t)plan->N * sizeof(double2));
     if (e != cudaSuccess) return cuda_fail(e);
   }
   CurArgs a{};
@@ -1389,6 +1411,7 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
   hse_plan plan = new (std::nothrow) hse_plan_s();
   if (!plan) return HSE_ERR_NOMEM;
   plan->batched = true;
+  plan->fail_alloc_at = fail_alloc_from_env();
   plan->p = cells[0];
   cudaGetDevice(&plan->device);
   int rc = HSE_OK;
@@ -1405,23 +1428,23 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
     const int ntiles = (q.n_tgt + T - 1) / T;
     max_items += (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * ntiles;
     float2* buf = nullptr;
-    if (q.nk > 1) e = cudaMalloc(&buf, (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * q.n_tgt * sub->N * sizeof(float2));
+    if (q.nk > 1) e = plan_malloc(plan, &buf, (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * q.n_tgt * sub->N * sizeof(float2));
     plan->cell_split.push_back(buf);
     float2* comp = nullptr;
     if (e == cudaSuccess)
-      e = cudaMalloc(&comp, (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * q.n_tgt * 2 * blocked_stride(q.grid[0]) *
+      e = plan_malloc(plan, &comp, (size_t)std::min(kMaxBatchSplit, q.nk) * q.nk * q.n_tgt * 2 * blocked_stride(q.grid[0]) *
                                 sizeof(float2));
     plan->cell_comp.push_back(comp);
     float2* blk = nullptr;
     int sp = 0, br = 0;
     if (e == cudaSuccess && !batched_stage_geometry(q.grid[0], &sp, &br))
-      e = cudaMalloc(&blk, (size_t)q.nk * (q.n_tgt + q.n_occ) * blocked_stride(q.grid[0]) * sizeof(float2));
+      e = plan_malloc(plan, &blk, (size_t)q.nk * (q.n_tgt + q.n_occ) * blocked_stride(q.grid[0]) * sizeof(float2));
     plan->cell_blk.push_back(blk);
   }
-  if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_cells, (size_t)ncells * sizeof(BatchCell));
-  if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_items, max_items * sizeof(BatchItem));
-  if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->d_counter, 2 * sizeof(int));
-  if (rc == HSE_OK && e == cudaSuccess) e = cudaMalloc(&plan->status, sizeof(int));
+  if (rc == HSE_OK && e == cudaSuccess) e = plan_malloc(plan, &plan->d_cells, (size_t)ncells * sizeof(BatchCell));
+  if (rc == HSE_OK && e == cudaSuccess) e = plan_malloc(plan, &plan->d_items, max_items * sizeof(BatchItem));
+  if (rc == HSE_OK && e == cudaSuccess) e = plan_malloc(plan, &plan->d_counter, 2 * sizeof(int));
+  if (rc == HSE_OK && e == cudaSuccess) e = plan_malloc(plan, &plan->status, sizeof(int));
   if (rc == HSE_OK && e == cudaSuccess) e = cudaMemset(plan->status, 0, sizeof(int));
   if (rc == HSE_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking);
   if (rc == HSE_OK && e != cudaSuccess) rc = cuda_fail(e);

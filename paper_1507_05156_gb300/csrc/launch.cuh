@@ -154,6 +154,24 @@ constexpr bool tc_fits() {
   }
 }
 
+// One-pencil variant (kOneVariant, the default where it fits): the pencil-load kernel with one
+// pencil per thread, n^2 / 32 warps (24^3: 18 warps, 576 threads).  Every warp scheduler then
+// holds 4-5 warps through a stage instead of 3 (the ragged form), at most 96 registers a thread
+// (5 warps on the busiest scheduler's 16K-register file); its Z stages and folds move the
+// orbitals and accumulators in small chunks to stay within them, and its orbital loads follow
+// the L1 policy of pairconv_c64.cuh (kLdOwner, ...).  24^3, 4x4x4 k, 16 bands: 58.8 ms against
+// 66.5 ms for the ragged form.  Owner = target modes only (the VJP's u_occ pass keeps the
+// ragged form: its two chains and fused omega term need more registers).
+constexpr int kOneVariant = 5;
+template <int n>
+constexpr bool pencil_one_fits() {
+  if constexpr (Geo<n>::T == 1 && Geo<n>::NN % 32 == 0 && Geo<n>::NN <= 1024 && n % 4 == 0) {
+    return GeoP<n, 1, Geo<n>::NN>::TMEM_COLS <= 512;
+  } else {
+    return false;
+  }
+}
+
 // Staged-partner kernel (pairconv_tma.cuh): one CTA per SM.
 // Encodes the tensor map of a partner array for the staged-partner kernel of side n.
 cudaError_t make_partner_tmap(CUtensorMap* map, const void* base, int n, long long rows, int sp, int box_rows);
@@ -191,11 +209,13 @@ constexpr bool tma_fits() {
 }
 
 // Kernel variant: 0 the default (the staged-partner kernel with its default layout where it
-// exists for (n, mode), else the pencil-load kernel at the occupancy the size allows);
-// -1 / -2 the staged-partner kernel with LayoutSeq / LayoutOne; 1 or 2 the
-// pencil-load kernel with that occupancy; 3 the ragged pencil-load kernel (pencil_ragged_fits;
-// the default of the pencil-load kernel where it exists: 24^3 99.6 -> 95.6 ms on the 4x4x4 k,
-// 16-band cell); 4 (kTcVariant) its tensor-core form where tc_fits, else the ragged kernel.
+// exists for (n, mode); else the one-pencil pencil-load kernel where it exists for (n, mode);
+// else the ragged pencil-load kernel where it exists; else the pencil-load kernel at the
+// occupancy the size allows); -1 / -2 the staged-partner kernel with LayoutSeq / LayoutOne;
+// 1 or 2 the pencil-load kernel with that occupancy; 3 the ragged pencil-load kernel
+// (pencil_ragged_fits; 24^3 99.6 -> 95.6 ms on the 4x4x4 k, 16-band cell against two pencils a
+// thread on 9 warps); 4 (kTcVariant) its tensor-core form where tc_fits, else the ragged
+// kernel; 5 (kOneVariant) the one-pencil pencil-load kernel where pencil_one_fits.
 // A variant that does not exist for the size falls back to the default.
 template <int n, int MODE>
 constexpr int staged_layout(int variant) {
@@ -221,6 +241,10 @@ cudaError_t launch_pairconv_mode(const PairArgs& args, int variant, cudaStream_t
   if constexpr (tc_fits<n, MODE>()) {
     if (variant == kTcVariant) return launch_pairconv_variant<n, MODE, 1, 2, kRaggedThreads, true>(args, stream);
   }
+  if constexpr (pencil_one_fits<n>() && MODE != MODE_OCC) {
+    if (variant == kOneVariant || variant <= 0)
+      return launch_pairconv_variant<n, MODE, 1, 1, Geo<n>::NN>(args, stream);
+  }
   if constexpr (pencil_ragged_fits<n>()) {
     if (variant >= 3 || variant <= 0) return launch_pairconv_variant<n, MODE, 1, 2, kRaggedThreads>(args, stream);
   }
@@ -234,6 +258,9 @@ int pairconv_occupancy_mode(int variant) {
   if (staged_layout<n, MODE>(variant) != 0) return 1;
   if constexpr (tc_fits<n, MODE>()) {
     if (variant == kTcVariant) return pairconv_occupancy_variant<n, MODE, 1, 2, kRaggedThreads, true>();
+  }
+  if constexpr (pencil_one_fits<n>() && MODE != MODE_OCC) {
+    if (variant == kOneVariant || variant <= 0) return pairconv_occupancy_variant<n, MODE, 1, 1, Geo<n>::NN>();
   }
   if constexpr (pencil_ragged_fits<n>()) {
     if (variant >= 3 || variant <= 0) return pairconv_occupancy_variant<n, MODE, 1, 2, kRaggedThreads>();

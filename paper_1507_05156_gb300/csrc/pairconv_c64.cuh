@@ -201,6 +201,28 @@ __device__ __forceinline__ void fold_group(const float* g, float4* __restrict__ 
   }
 }
 
+// fold_group on the float4 chunks e0 .. e0 + count - 1 of the row only (g: their 4 count
+// floats), for callers that move the accumulator in pieces.
+template <int n>
+__device__ __forceinline__ void fold_chunks(const float* g, float4* __restrict__ sums, int p, float4* out4, bool first,
+                                            bool second, bool last, int e0, int count) {
+  float4* s4 = sums + (size_t)(p >> 5) * (n / 2) * 32 + (p & 31);
+  float4* c4 = s4 + blocked_stride(n) / 2;
+#pragma unroll
+  for (int i = 0; i < count; ++i) {
+    const int e = e0 + i;
+    float4 sv = make_float4(g[4 * i], g[4 * i + 1], g[4 * i + 2], g[4 * i + 3]);
+    float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!first) fold4(sv, cv, s4[32 * e], second ? make_float4(0.f, 0.f, 0.f, 0.f) : c4[32 * e]);
+    if (last) {
+      out4[e] = make_float4(sv.x + cv.x, sv.y + cv.y, sv.z + cv.z, sv.w + cv.w);
+    } else {
+      s4[32 * e] = sv;
+      if (!first) c4[32 * e] = cv;
+    }
+  }
+}
+
 // The same fold with the running sums in TMEM (the layouts that have the columns): s at ts
 // (2n columns, FP32), c at tc (n columns, bf16 pairs: c is the sum of rounding errors, about
 // 1e-7 of s, so its own 2^-9 rounding is far below the FP32 resolution of s).  Warp-wide
@@ -270,6 +292,37 @@ __device__ __forceinline__ float pencil_dot(const cpx<float> (&w)[n], const floa
   return d;
 }
 
+// L1 policy of the 16-byte chunks of a pencil-blocked orbital (a warp reads 512 contiguous
+// bytes per access) in the one-pencil-per-thread layout, whose 96-register budget spills a few
+// loop-invariant values to local memory: those reloads must hit L1.  The owner orbital is read
+// once per pair and nothing re-reads it from L1 before the next pair, so it streams past L1 (no
+// allocation); the partner is read twice per pair, in the Z forward and the Z inverse stage, so
+// its first read stays in L1 longest and its last read streams.  On the 24^3, 4x4x4 k, 16-band
+// cell: 63.8 ms with every orbital read streamed, 59.4 ms with plain loads, 58.8 ms with this.
+// The layouts with two pencils a thread (no spills) are fastest with plain loads (66.5 ms
+// against 67.1 ms with this policy) and keep them.
+enum LdPolicy : int { LD_NORMAL = 0, LD_STREAM = 1, LD_KEEP = 2 };
+constexpr int kLdOwner = LD_STREAM;
+constexpr int kLdPartnerFirst = LD_KEEP;
+constexpr int kLdPartnerLast = LD_STREAM;
+
+template <int POL>
+__device__ __forceinline__ float4 ldg_pol(const float4* p) {
+  float4 v;
+  if constexpr (POL == LD_STREAM) {
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+  } else if constexpr (POL == LD_KEEP) {
+    asm volatile("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+  } else {
+    v = __ldg(p);
+  }
+  return v;
+}
+
 template <int n>
 __device__ __forceinline__ void load_pencil_global(cpx<float> (&v)[n], const float2* __restrict__ p) {
   const float4* p4 = reinterpret_cast<const float4*>(p);
@@ -294,13 +347,13 @@ struct OrbBlk {
 };
 
 // Z-pencil p (= x n + y) of one orbital, natural (blk = 0) or pencil-blocked (blk = 1).
-template <int n>
+template <int n, int POL = LD_NORMAL>
 __device__ __forceinline__ void load_pencil(cpx<float> (&v)[n], const float2* __restrict__ orb, int p, int blk) {
   if (blk) {
     const float4* b4 = reinterpret_cast<const float4*>(orb) + (size_t)(p >> 5) * (n / 2) * 32 + (p & 31);
 #pragma unroll
     for (int e = 0; e < n / 2; ++e) {
-      const float4 w = __ldg(b4 + 32 * e);
+      const float4 w = ldg_pol<POL>(b4 + 32 * e);
       v[2 * e] = {w.x, w.y};
       v[2 * e + 1] = {w.z, w.w};
     }
@@ -526,12 +579,29 @@ __device__ __forceinline__ void stage_z_forward(float2* g, int t, bool valid, co
 #pragma unroll 1
   for (int ps = 0; ps < PPT; ++ps) {
     if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
-    const Pencil<n> pc(t + ps * TS);
-    cpx<float> v[n], w[n];
-    load_pencil<n>(w, a, t + ps * TS, blk);
-    load_pencil<n>(v, b, t + ps * TS, blk);
+    const int p = t + ps * TS;
+    const Pencil<n> pc(p);
+    cpx<float> v[n];
+    if constexpr (PPT == 1) {
+      // one pencil per thread (many warps, few registers each): the two orbitals' 16-byte
+      // chunks are read and multiplied one pair at a time, so that only one pencil is live
+      const size_t off = blk ? (size_t)(p >> 5) * (n / 2) * 32 + (p & 31) : (size_t)p * (n / 2);
+      const float4* a4 = reinterpret_cast<const float4*>(a) + off;
+      const float4* b4 = reinterpret_cast<const float4*>(b) + off;
 #pragma unroll
-    for (int e = 0; e < n; ++e) v[e] = {w[e].x * v[e].x + w[e].y * v[e].y, w[e].x * v[e].y - w[e].y * v[e].x};
+      for (int e = 0; e < n / 2; ++e) {
+        const float4 w = blk ? ldg_pol<kLdPartnerFirst>(a4 + 32 * e) : __ldg(a4 + e);
+        const float4 u = blk ? ldg_pol<kLdOwner>(b4 + 32 * e) : __ldg(b4 + e);
+        v[2 * e] = {w.x * u.x + w.y * u.y, w.x * u.y - w.y * u.x};
+        v[2 * e + 1] = {w.z * u.z + w.w * u.w, w.z * u.w - w.w * u.z};
+      }
+    } else {
+      cpx<float> w[n];
+      load_pencil<n>(w, a, p, blk);
+      load_pencil<n>(v, b, p, blk);
+#pragma unroll
+      for (int e = 0; e < n; ++e) v[e] = {w[e].x * v[e].x + w[e].y * v[e].y, w[e].x * v[e].y - w[e].y * v[e].x};
+    }
     fft<n, -1, float>(v);
     if (valid) store_s<n, G::ZVEC>(v, g, pc.zs, 1);
   }
@@ -543,6 +613,21 @@ enum Epi : int {
   EPI_WCONJ = 2,    // acc += w * conj(phi)
 };
 
+// One complex term of the Z-inverse epilogue into the accumulator (ar, ai).
+template <int EPI>
+__device__ __forceinline__ void epilogue_mac(float& ar, float& ai, const cpx<float> w, const cpx<float> v) {
+  if constexpr (EPI == EPI_MUL) {  // acc += w phi
+    ar = fmaf(w.x, v.x, fmaf(-w.y, v.y, ar));
+    ai = fmaf(w.x, v.y, fmaf(w.y, v.x, ai));
+  } else if constexpr (EPI == EPI_CONJPHI) {  // acc += conj(phi) w
+    ar = fmaf(v.x, w.x, fmaf(v.y, w.y, ar));
+    ai = fmaf(v.x, w.y, fmaf(-v.y, w.x, ai));
+  } else {  // acc += w conj(phi)
+    ar = fmaf(w.x, v.x, fmaf(w.y, v.y, ar));
+    ai = fmaf(w.y, v.x, fmaf(-w.x, v.y, ai));
+  }
+}
+
 // Z inverse for the thread's pencils, then the epilogue into each pencil's TMEM row.
 // Executed by every thread of the warp (TMEM accesses are warp-wide).
 template <int n, int EPI, int PPT = 2, int TS = Geo<n>::NN / PPT>
@@ -552,31 +637,37 @@ __device__ __forceinline__ void stage_z_inverse(const float2* g, int t, const fl
 #pragma unroll 1
   for (int ps = 0; ps < PPT; ++ps) {
     if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
-    const Pencil<n> pc(t + ps * TS);
+    const int p = t + ps * TS;
+    const Pencil<n> pc(p);
     cpx<float> v[n];
     load_s<n, G::ZVEC>(v, g, pc.zs, 1);
     fft<n, +1, float>(v);
-    float acc[G::ROW];
     const uint32_t trow = trow0 + (uint32_t)(ps * G::ROW);
-    TmemRow<G::ROW>::load(trow, acc);
-    cpx<float> w[n];
-    load_pencil<n>(w, wbase, t + ps * TS, blk);
+    if constexpr (PPT == 1 && n % 4 == 0) {
+      // one pencil per thread: the accumulator row and the partner move four complex values
+      // (eight TMEM columns, two 16-byte chunks) at a time, so that only phi stays live
+      const size_t off = blk ? (size_t)(p >> 5) * (n / 2) * 32 + (p & 31) : (size_t)p * (n / 2);
+      const float4* w4 = reinterpret_cast<const float4*>(wbase) + off;
 #pragma unroll
-    for (int e = 0; e < n; ++e) {
-      float& ar = acc[2 * e];
-      float& ai = acc[2 * e + 1];
-      if constexpr (EPI == EPI_MUL) {  // acc += w phi
-        ar = fmaf(w[e].x, v[e].x, fmaf(-w[e].y, v[e].y, ar));
-        ai = fmaf(w[e].x, v[e].y, fmaf(w[e].y, v[e].x, ai));
-      } else if constexpr (EPI == EPI_CONJPHI) {  // acc += conj(phi) w
-        ar = fmaf(v[e].x, w[e].x, fmaf(v[e].y, w[e].y, ar));
-        ai = fmaf(v[e].x, w[e].y, fmaf(-v[e].y, w[e].x, ai));
-      } else {  // acc += w conj(phi)
-        ar = fmaf(w[e].x, v[e].x, fmaf(w[e].y, v[e].y, ar));
-        ai = fmaf(w[e].y, v[e].x, fmaf(-w[e].x, v[e].y, ai));
+      for (int c = 0; c < n / 4; ++c) {
+        float acc[8];
+        tmem_ld8(trow + (uint32_t)(8 * c), acc);
+        const float4 w0 = blk ? ldg_pol<kLdPartnerLast>(w4 + 32 * (2 * c)) : __ldg(w4 + 2 * c);
+        const float4 w1 = blk ? ldg_pol<kLdPartnerLast>(w4 + 32 * (2 * c + 1)) : __ldg(w4 + 2 * c + 1);
+        const cpx<float> w[4] = {{w0.x, w0.y}, {w0.z, w0.w}, {w1.x, w1.y}, {w1.z, w1.w}};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) epilogue_mac<EPI>(acc[2 * q], acc[2 * q + 1], w[q], v[4 * c + q]);
+        tmem_st8(trow + (uint32_t)(8 * c), acc);
       }
+    } else {
+      float acc[G::ROW];
+      TmemRow<G::ROW>::load(trow, acc);
+      cpx<float> w[n];
+      load_pencil<n>(w, wbase, p, blk);
+#pragma unroll
+      for (int e = 0; e < n; ++e) epilogue_mac<EPI>(acc[2 * e], acc[2 * e + 1], w[e], v[e]);
+      TmemRow<G::ROW>::store(trow, acc);
     }
-    TmemRow<G::ROW>::store(trow, acc);
   }
 }
 
@@ -675,22 +766,51 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     for (int ps = 0; ps < PPT; ++ps) {
       if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
       const uint32_t trow = trow0 + (uint32_t)(ps * G::ROW);
-      float acc[G::ROW];
-      TmemRow<G::ROW>::load(trow, acc);
-      if constexpr (MODE == MODE_APPLY || MODE == MODE_OCC) {
-        if (active) {
-          const int p = t + ps * TS;
-          fold_group<n>(acc, sums, p, reinterpret_cast<float4*>(args.out + oofs + (size_t)p * n), first, second, last);
-        }
-      } else {
-        cpx<float> w[n];
-        load_pencil<n>(w, lhs, t + ps * TS, blk);
-        dsum += (double)pencil_dot<n>(w, acc);
-      }
-      if (!last) {
+      const int p = t + ps * TS;
+      if constexpr (PPT == 1 && n % 4 == 0) {
+        // one pencil per thread: eight accumulator columns (two 16-byte chunks) at a time
+        const size_t loff = blk ? (size_t)(p >> 5) * (n / 2) * 32 + (p & 31) : (size_t)p * (n / 2);
+        float dpart = 0.f;
 #pragma unroll
-        for (int e = 0; e < G::ROW; ++e) acc[e] = 0.f;
-        TmemRow<G::ROW>::store(trow, acc);
+        for (int c = 0; c < n / 4; ++c) {
+          float acc[8];
+          tmem_ld8(trow + (uint32_t)(8 * c), acc);
+          if constexpr (MODE == MODE_APPLY || MODE == MODE_OCC) {
+            if (active)
+              fold_chunks<n>(acc, sums, p, reinterpret_cast<float4*>(args.out + oofs + (size_t)p * n), first, second,
+                             last, 2 * c, 2);
+          } else {
+            const float4* l4 = reinterpret_cast<const float4*>(lhs) + loff;
+            const float4 w0 = blk ? ldg_pol<kLdOwner>(l4 + 32 * (2 * c)) : __ldg(l4 + 2 * c);
+            const float4 w1 = blk ? ldg_pol<kLdOwner>(l4 + 32 * (2 * c + 1)) : __ldg(l4 + 2 * c + 1);
+            dpart = fmaf(w0.x, acc[0], fmaf(w0.y, acc[1], dpart));
+            dpart = fmaf(w0.z, acc[2], fmaf(w0.w, acc[3], dpart));
+            dpart = fmaf(w1.x, acc[4], fmaf(w1.y, acc[5], dpart));
+            dpart = fmaf(w1.z, acc[6], fmaf(w1.w, acc[7], dpart));
+          }
+          if (!last) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[e] = 0.f;
+            tmem_st8(trow + (uint32_t)(8 * c), acc);
+          }
+        }
+        if constexpr (MODE == MODE_ENERGY || MODE == MODE_DOT) dsum += (double)dpart;
+      } else {
+        float acc[G::ROW];
+        TmemRow<G::ROW>::load(trow, acc);
+        if constexpr (MODE == MODE_APPLY || MODE == MODE_OCC) {
+          if (active)
+            fold_group<n>(acc, sums, p, reinterpret_cast<float4*>(args.out + oofs + (size_t)p * n), first, second, last);
+        } else {
+          cpx<float> w[n];
+          load_pencil<n>(w, lhs, p, blk);
+          dsum += (double)pencil_dot<n>(w, acc);
+        }
+        if (!last) {
+#pragma unroll
+          for (int e = 0; e < G::ROW; ++e) acc[e] = 0.f;
+          TmemRow<G::ROW>::store(trow, acc);
+        }
       }
     }
   };

@@ -3,7 +3,8 @@
 The layout is chosen per plan through HSE_BLOCKS_PER_SM: for the staged-partner kernel -1 two
 pencils per thread, -2 one pencil per thread; for the pencil-load kernel 1 one CTA per SM with uncapped registers (two
 pencils per thread on 9 warps at 24^3), 2 two CTAs per SM where they fit (16^3), and 3 the
-ragged 24^3 form (12 warps, a second pencil for the first 192 threads; the default there).
+ragged 24^3 form (12 warps, a second pencil for the first 192 threads), 5 one pencil per
+thread on 18 warps (24^3; the VJP's u_occ pass keeps the ragged form).
 The pencil-load kernel reads pencil-blocked copies of the orbitals by default; the cases with
 HSE_PENCIL_BLOCKS=0 run it on the caller's [x][y][z] arrays.  For every layout the test runs V_x u (owner = target apply), the exchange energy (energy epilogue) and
 the full vector-Jacobian product, whose d/d omega term runs the owner = target dot epilogue
@@ -20,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 LAYOUT_CASES = [(12, -1, 1), (12, -2, 1), (16, -1, 1), (16, -2, 1), (16, 2, 1), (18, -1, 1), (18, -2, 1),
                 (20, -1, 1), (20, -2, 1), (8, -1, 1), (8, -2, 1), (24, 1, 1), (24, 3, 1),
-                (24, 3, 0), (16, -2, 0), (20, -2, 0)]
+                (24, 3, 0), (16, -2, 0), (20, -2, 0), (24, 5, 1), (24, 5, 0)]
 
 
 def _dev(x, dtype):
