@@ -140,10 +140,15 @@ int hse_fock_apply_vjp(hse_plan plan, const void *u_occ, const double *occ, cons
 
 /* Batched V_x for a plan from hse_plan_create_batched: arrays of ncells HOST-side
  * pointers, each to that cell's device buffers (same layouts as hse_fock_apply).  The first
- * call times three k'-split granularities of the work items (synchronising the stream) and
- * captures the chosen launch as a CUDA graph, which later calls replay; with the environment
- * variable HSE_AUTOTUNE_CACHE naming a file, the choice is stored there per GPU and cell list
- * and read back by later plans instead of timing. */
+ * call autotunes the shape of the launch on the real inputs (synchronising the stream): the
+ * k'-split granularity of the work items (1, 2, 4), the pencil layout of the 24^3 cells (one
+ * pencil per thread or the ragged two-pencil form), the pencil layout of each staged grid side
+ * (one or two pencils per thread), and whether the two persistent kernels (24^3 cells; the
+ * other sides) run at once on two streams or one after the other; coordinate descent from the
+ * defaults, at most nine timed runs.  It then captures the chosen launch as a CUDA graph,
+ * which later calls replay.  With the environment variable HSE_AUTOTUNE_CACHE naming a file,
+ * the choice is stored there per GPU and cell list and read back by later plans instead of
+ * timing. */
 int hse_fock_apply_batched(hse_plan plan, const void *const *u_occ, const double *const *occ,
                            const void *const *u_tgt, void *const *vx_out, hse_stream_t stream);
 

@@ -6,16 +6,18 @@
 // split in two lists by the pipeline their side runs, each with its own persistent kernel:
 //   * staged-partner items (sides 8, 12, 16, 18, 20; pairconv_tma.cuh): the partner orbitals
 //     stream in by TMA from the cell's tensor map into two stage buffers, the owner orbital
-//     and the accumulators stay in Tensor Memory.  512 threads (8^3 with eight owner slots of
-//     one pencil per thread);
-//   * pencil-load items (side 24; pairconv_c64.cuh; in its ragged 12-warp form, 384 threads):
-//     orbitals are read as pencils
-//     through L1.  That kernel keeps only its own shared-memory footprint so that L1 keeps
-//     the rest of the SM's storage: with the staged kernel's 208 KB of shared memory
-//     reserved, its 24^3 items ran 37% slower.
-// Warps beyond an item's layout only take part in the block barriers.  One CTA per SM holds
-// all 512 TMEM columns for the whole launch; the stage barriers' phases carry over from item
-// to item.
+//     and the accumulators stay in Tensor Memory.  512 threads; per cell the pencil layout
+//     LayoutOne (one pencil per thread) or LayoutSeq (two), as the autotuner chose
+//     (BatchCell::layout; 12^3 runs LayoutSeq, its LayoutOne needs 576 threads);
+//   * pencil-load items (side 24; pairconv_c64.cuh): orbitals are read as pencils through L1,
+//     in the one-pencil form (18 warps, the single-cell default) or the ragged 12-warp form.
+//     That kernel keeps only its own shared-memory footprint so that L1 keeps the rest of the
+//     SM's storage: with the staged kernel's 208 KB of shared memory reserved, its 24^3 items
+//     ran 37% slower.
+// The two kernels may run on two streams at once: each takes every SM it can get, and the SMs
+// the one finishing first frees go to the other.  Warps beyond an item's layout only take part
+// in the block barriers.  One CTA per SM holds all 512 TMEM columns for the whole launch; the
+// stage barriers' phases carry over from item to item.
 #include "launch.cuh"
 
 namespace hse {
@@ -23,7 +25,6 @@ namespace hse {
 namespace {
 
 constexpr int kStagedThreads = 512;
-constexpr int kPencilThreads = kRaggedThreads;  // the ragged 24^3 form (12 warps)
 
 template <int n>
 using SeqS = GeoS<n, LayoutSeq<n>>;
@@ -34,9 +35,11 @@ static_assert(LayoutOne<20>::THREADS <= kStagedThreads && LayoutOne<8>::THREADS 
                   LayoutOne<16>::THREADS <= kStagedThreads &&
                   LayoutSeq<12>::THREADS <= kStagedThreads && LayoutOne<18>::THREADS <= kStagedThreads,
               "staged batched block too small for a side's layout");
-static_assert(GeoP<24, 2, kRaggedThreads>::THREADS <= kPencilThreads,
-              "pencil-load batched block too small");
-static_assert(OneS<8>::FITS && SeqS<12>::FITS && OneS<16>::FITS && OneS<18>::FITS && OneS<20>::FITS,
+static_assert(LayoutSeq<8>::THREADS <= kStagedThreads && LayoutSeq<16>::THREADS <= kStagedThreads &&
+                  LayoutSeq<18>::THREADS <= kStagedThreads && LayoutSeq<20>::THREADS <= kStagedThreads,
+              "staged batched block too small for a side's alternative layout");
+static_assert(OneS<8>::FITS && SeqS<12>::FITS && OneS<16>::FITS && OneS<18>::FITS && OneS<20>::FITS &&
+                  SeqS<8>::FITS && SeqS<16>::FITS && SeqS<18>::FITS && SeqS<20>::FITS,
               "staged layouts of the batched kernel must fit");
 
 // One staged item as a call of its own: each side's pipeline gets the whole register budget
@@ -86,14 +89,22 @@ __global__ void __launch_bounds__(kStagedThreads, 1) pairconv_batched_staged_ker
     const BatchItem wi = b.items[it];
     const BatchCell& c = b.cells[wi.cell];
     bool ok = true;
+#define HSE_STAGED_CASE(N)                                                                              \
+  case N:                                                                                               \
+    ok = c.layout ? staged_call<N, MODE, LayoutSeq>(c, wi.item, sbase, tbase, sh, ph0, ph1,            \
+                                                    warp < LayoutSeq<N>::WARPS)                          \
+                  : staged_call<N, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1,            \
+                                                    warp < LayoutOne<N>::WARPS);                         \
+    break;
     switch (c.n) {
-      case 8: ok = staged_call<8, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutOne<8>::WARPS); break;
+      HSE_STAGED_CASE(8)
       case 12: ok = staged_call<12, MODE, LayoutSeq>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutSeq<12>::WARPS); break;
-      case 16: ok = staged_call<16, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutOne<16>::WARPS); break;
-      case 18: ok = staged_call<18, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutOne<18>::WARPS); break;
-      case 20: ok = staged_call<20, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutOne<20>::WARPS); break;
+      HSE_STAGED_CASE(16)
+      HSE_STAGED_CASE(18)
+      HSE_STAGED_CASE(20)
       default: break;  // the host puts only the sides above in this list
     }
+#undef HSE_STAGED_CASE
     if (!ok) break;  // a bounded wait expired (uniform: read after a block barrier)
   }
   tmem_fence_before_sync();
@@ -102,8 +113,10 @@ __global__ void __launch_bounds__(kStagedThreads, 1) pairconv_batched_staged_ker
   if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kPencilThreads, 1) pairconv_batched_pencil_kernel(const BatchArgs b) {
+// PPT, TS: the pencil layout of the 24^3 items (one pencil per thread on 576 threads, or the
+// ragged form on 384).
+template <int MODE, int PPT, int TS>
+__global__ void __launch_bounds__(GeoP<24, PPT, TS>::THREADS, 1) pairconv_batched_pencil_kernel(const BatchArgs b) {
   extern __shared__ __align__(16) float4 smem4[];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int next_sh;
@@ -123,8 +136,7 @@ __global__ void __launch_bounds__(kPencilThreads, 1) pairconv_batched_pencil_ker
     const BatchCell& c = b.cells[wi.cell];
     switch (c.n) {
       case 24:
-        pairconv_item<24, MODE, 2, kRaggedThreads>(c.pa, wi.item, smem4, tbase,
-                                                   warp < GeoP<24, 2, kRaggedThreads>::WARPS);
+        pairconv_item<24, MODE, PPT, TS>(c.pa, wi.item, smem4, tbase, warp < GeoP<24, PPT, TS>::WARPS);
         break;
       default: break;  // the host puts only the sides above in this list
     }
@@ -137,8 +149,10 @@ __global__ void __launch_bounds__(kPencilThreads, 1) pairconv_batched_pencil_ker
 }
 
 constexpr size_t max_c(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t kStagedSmem = max_c(max_c(max_c(OneS<8>::SMEM_REQUEST, SeqS<12>::SMEM_REQUEST), OneS<16>::SMEM_REQUEST),
-                                     max_c(OneS<18>::SMEM_REQUEST, OneS<20>::SMEM_REQUEST));
+constexpr size_t kStagedSmem =
+    max_c(max_c(max_c(OneS<8>::SMEM_REQUEST, SeqS<12>::SMEM_REQUEST), max_c(OneS<16>::SMEM_REQUEST, OneS<18>::SMEM_REQUEST)),
+          max_c(max_c(OneS<20>::SMEM_REQUEST, SeqS<8>::SMEM_REQUEST),
+                max_c(max_c(SeqS<16>::SMEM_REQUEST, SeqS<18>::SMEM_REQUEST), SeqS<20>::SMEM_REQUEST)));
 // >= 118784: a second CTA (which would need TMEM too) never fits
 constexpr size_t kPencilSmem = max_c(Geo<24>::SMEM_BYTES, (size_t)118784);
 
@@ -170,25 +184,48 @@ bool batched_stage_geometry(int n, int* sp, int* box_rows) {
   }
 }
 
-cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& pencil, int sms, cudaStream_t stream) {
-  static bool done_s[64] = {}, done_p[64] = {};
-  cudaError_t err = set_smem(pairconv_batched_staged_kernel<MODE_APPLY>, kStagedSmem, done_s);
-  if (err == cudaSuccess) err = set_smem(pairconv_batched_pencil_kernel<MODE_APPLY>, kPencilSmem, done_p);
+template <int PPT, int TS>
+cudaError_t launch_pencil_list(const BatchArgs& pencil, int sms, cudaStream_t stream) {
+  static bool done[64] = {};
+  cudaError_t err = set_smem(pairconv_batched_pencil_kernel<MODE_APPLY, PPT, TS>, kPencilSmem, done);
   if (err != cudaSuccess) return err;
-  // the pencil-load list first: its 24^3 items are the longest, and the staged list's short
-  // items fill the tail
+  pairconv_batched_pencil_kernel<MODE_APPLY, PPT, TS>
+      <<<sms < pencil.nitems ? sms : pencil.nitems, GeoP<24, PPT, TS>::THREADS, kPencilSmem, stream>>>(pencil);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& pencil, int sms, int pencil_layout,
+                                    cudaStream_t stream, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
+  static bool done_s[64] = {};
+  cudaError_t err = set_smem(pairconv_batched_staged_kernel<MODE_APPLY>, kStagedSmem, done_s);
+  if (err != cudaSuccess) return err;
+  const bool both = pencil.nitems > 0 && staged.nitems > 0;
+  const bool fork_side = both && side && fork && join;
+  // the pencil-load list first: its 24^3 items are the longest; the staged list on the side
+  // stream (when given) starts on the SMs the pencil kernel leaves and takes over its tail
+  cudaStream_t s2 = stream;
+  if (fork_side) {
+    err = cudaEventRecord(fork, stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(side, fork, 0);
+    if (err != cudaSuccess) return err;
+    s2 = side;
+  }
   if (pencil.nitems > 0) {
-    pairconv_batched_pencil_kernel<MODE_APPLY>
-        <<<sms < pencil.nitems ? sms : pencil.nitems, kPencilThreads, kPencilSmem, stream>>>(pencil);
-    count_launch();
-    err = cudaGetLastError();
+    err = pencil_layout == kPencilRagged ? launch_pencil_list<2, kRaggedThreads>(pencil, sms, stream)
+                                         : launch_pencil_list<1, Geo<24>::NN>(pencil, sms, stream);
     if (err != cudaSuccess) return err;
   }
   if (staged.nitems > 0) {
     pairconv_batched_staged_kernel<MODE_APPLY>
-        <<<sms < staged.nitems ? sms : staged.nitems, kStagedThreads, kStagedSmem, stream>>>(staged);
+        <<<sms < staged.nitems ? sms : staged.nitems, kStagedThreads, kStagedSmem, s2>>>(staged);
     count_launch();
     err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  if (fork_side) {
+    err = cudaEventRecord(join, side);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(stream, join, 0);
   }
   return err;
 }

@@ -328,6 +328,10 @@ struct hse_plan_s {
   int nitems = 0;
   int nitems_staged = 0;
   int batch_split = 0;                  // autotuned k' split (0: not tuned yet)
+  int batch_layout24 = kPencilOne;      // autotuned pencil layout of the 24^3 items
+  bool batch_serial = false;            // autotuned: the two persistent kernels one after the other
+  cudaStream_t side_stream = nullptr;   // the staged kernel's stream when both run at once
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int sms = 0;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -383,21 +387,48 @@ int autotune_lookup(const std::string& key) {
     if (!tab) continue;
     if ((size_t)(tab - line.data()) == key.size() && std::strncmp(line.data(), key.data(), key.size()) == 0) {
       const int v = std::atoi(tab + 1);
-      if (v == 1 || v == 2 || v == 4) found = v;  // the last entry for the key wins
+      const int split = v & 7;
+      if (v > 0 && v < (1 << 10) && (split == 1 || split == 2 || split == 4)) found = v;  // the last entry wins
     }
   }
   std::fclose(f);
   return found;
 }
 
-void autotune_store(const std::string& key, int split) {
+void autotune_store(const std::string& key, int shape) {
   const char* path = autotune_path();
   if (!path || key.size() + 16 > (1 << 16)) return;
   if (FILE* f = std::fopen(path, "a")) {
-    std::fprintf(f, "%s\t%d\n", key.c_str(), split);
+    std::fprintf(f, "%s\t%d\n", key.c_str(), shape);
     std::fclose(f);
   }
 }
+
+// One point of the batched autotuner's search space, stored in the autotune cache as an int:
+// bits 0-2 the k' split (1, 2 or 4), bit 3 the ragged 24^3 layout, bit 4 the two persistent
+// kernels one after the other, bits 5-8 LayoutSeq for the staged sides 8, 16, 18, 20.  Zero
+// bits are the defaults, so a bare split (an older cache line) reads as the default shape.
+struct BatchShape {
+  int split = 1;
+  int layout24 = kPencilOne;
+  bool serial = false;
+  int seq[4] = {0, 0, 0, 0};  // sides 8, 16, 18, 20
+  int encode() const {
+    int v = split | (layout24 == kPencilRagged ? 8 : 0) | (serial ? 16 : 0);
+    for (int i = 0; i < 4; ++i) v |= seq[i] ? (32 << i) : 0;
+    return v;
+  }
+  static BatchShape decode(int v) {
+    BatchShape s;
+    s.split = v & 7;
+    s.layout24 = (v & 8) ? kPencilRagged : kPencilOne;
+    s.serial = (v & 16) != 0;
+    for (int i = 0; i < 4; ++i) s.seq[i] = (v >> (5 + i)) & 1;
+    return s;
+  }
+};
+
+int side_slot(int n) { return n == 8 ? 0 : n == 16 ? 1 : n == 18 ? 2 : n == 20 ? 3 : -1; }
 
 int cuda_fail(cudaError_t e) { return e == cudaSuccess ? HSE_OK : (e == cudaErrorMemoryAllocation ? HSE_ERR_NOMEM : HSE_ERR_CUDA); }
 
@@ -518,6 +549,9 @@ int hse_plan_destroy(hse_plan plan) {
   cudaFree(plan->d_counter);
   if (plan->graph) cudaGraphExecDestroy(plan->graph);
   if (plan->capture_stream) cudaStreamDestroy(plan->capture_stream);
+  if (plan->side_stream) cudaStreamDestroy(plan->side_stream);
+  if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+  if (plan->ev_join) cudaEventDestroy(plan->ev_join);
   cudaFree(plan->qidx);
   cudaFree(plan->qvec);
   cudaFree(plan->dkpts);
@@ -584,7 +618,7 @@ int hse_plan_create(hse_plan* out, const hse_problem* p) {
   if (const char* env = std::getenv("HSE_PENCIL_BLOCKS")) plan->blocked = std::atoi(env) != 0;
   if (const char* env = std::getenv("HSE_BLOCKS_PER_SM")) {
     const int v = std::atoi(env);
-    plan->blocks_per_sm = (v < -2 || v > 5 || v == kTcVariant) ? 0 : v;
+    plan->blocks_per_sm = (v < -2 || v > kOneVariant || v == kTcVariant) ? 0 : v;
   }
   if (plan->tc) plan->blocks_per_sm = kTcVariant;
   const int n1 = p->grid[0], n2 = p->grid[1], n3 = p->grid[2];
@@ -1032,7 +1066,9 @@ cudaError_t run_batch(hse_plan plan, cudaStream_t st) {
   const BatchArgs staged{plan->d_cells, plan->d_items, plan->nitems_staged, plan->d_counter, plan->status};
   const BatchArgs pencil{plan->d_cells, plan->d_items + plan->nitems_staged, plan->nitems - plan->nitems_staged,
                          plan->d_counter + 1, plan->status};
-  if (e == cudaSuccess) e = launch_pairconv_batched(staged, pencil, plan->sms, st);
+  if (e == cudaSuccess)
+    e = launch_pairconv_batched(staged, pencil, plan->sms, plan->batch_layout24, st,
+                                plan->batch_serial ? nullptr : plan->side_stream, plan->ev_fork, plan->ev_join);
   if (e == cudaSuccess && plan->batch_split != 1) {
     reduce_splits_batched<<<plan->sms * 4, 256, 0, st>>>(plan->d_cells, (int)plan->cells.size());
     count_launch();
@@ -1447,6 +1483,9 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
   if (rc == HSE_OK && e == cudaSuccess) e = plan_malloc(plan, &plan->status, sizeof(int));
   if (rc == HSE_OK && e == cudaSuccess) e = cudaMemset(plan->status, 0, sizeof(int));
   if (rc == HSE_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking);
+  if (rc == HSE_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->side_stream, cudaStreamNonBlocking);
+  if (rc == HSE_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming);
+  if (rc == HSE_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming);
   if (rc == HSE_OK && e != cudaSuccess) rc = cuda_fail(e);
   if (rc) {
     hse_plan_destroy(plan);
@@ -1535,45 +1574,92 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
   }
   cudaError_t e = cudaSuccess;
   if (plan->batch_split == 0) {
-    // autotune the k'-split granularity of the work items on this first call, unless the
-    // autotune cache (HSE_AUTOTUNE_CACHE) already holds a choice for this GPU and cell list
+    // Autotune the shape of the launch on this first call, unless the autotune cache
+    // (HSE_AUTOTUNE_CACHE) already holds a choice for this GPU and cell list: the k'-split
+    // granularity of the work items, the pencil layout of the 24^3 items, the pencil layout of
+    // each staged side, and whether the two persistent kernels run at once.  Coordinate
+    // descent from the defaults, each candidate timed on the real inputs.
     const std::string key = autotune_key(plan);
     const int cached = autotune_lookup(key);
-    float best_ms = 0.f;
-    int best = cached > 0 ? cached : 1;
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    bool has24 = false, present[4] = {false, false, false, false};
+    int nstaged_cells = 0;
+    for (hse_plan c : plan->cells) {
+      const int n = c->p.grid[0];
+      has24 = has24 || n == 24;
+      if (side_slot(n) >= 0) present[side_slot(n)] = true;
+      if (n != 24) ++nstaged_cells;
+    }
+    auto apply = [&](const BatchShape& s) {
+      build_batch(plan, s.split, vx_out);
+      plan->batch_layout24 = s.layout24;
+      plan->batch_serial = s.serial;
+      for (int c = 0; c < ncells; ++c) {
+        const int slot = side_slot(plan->h_cells[c].n);
+        plan->h_cells[c].layout = slot >= 0 ? s.seq[slot] : 0;
+      }
+    };
+    BatchShape best = cached > 0 ? BatchShape::decode(cached) : BatchShape();
     if (cached <= 0) {
+      cudaEvent_t t0 = nullptr, t1 = nullptr;
       e = cudaEventCreate(&t0);
       if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    }
-    const int cands[3] = {1, 2, 4};
-    for (int ci = 0; ci < (cached > 0 ? 0 : 3) && e == cudaSuccess; ++ci) {
-      build_batch(plan, cands[ci], vx_out);
-      e = cudaMemcpyAsync(plan->d_cells, plan->h_cells.data(), ncells * sizeof(BatchCell), cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess) e = cudaEventRecord(t0, st);
-      if (e == cudaSuccess) e = run_batch(plan, st);
-      if (e == cudaSuccess) e = cudaEventRecord(t1, st);
-      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-      if (e == cudaSuccess && (ci == 0 || ms < best_ms)) {
-        best_ms = ms;
-        best = cands[ci];
+      auto time_shape = [&](const BatchShape& s, float* ms) {
+        apply(s);
+        cudaError_t r = cudaMemcpyAsync(plan->d_cells, plan->h_cells.data(), ncells * sizeof(BatchCell),
+                                        cudaMemcpyHostToDevice, st);
+        if (r == cudaSuccess) r = cudaEventRecord(t0, st);
+        if (r == cudaSuccess) r = run_batch(plan, st);
+        if (r == cudaSuccess) r = cudaEventRecord(t1, st);
+        if (r == cudaSuccess) r = cudaEventSynchronize(t1);
+        if (r == cudaSuccess) r = cudaEventElapsedTime(ms, t0, t1);
+        if (r == cudaSuccess && log_on())
+          std::fprintf(stderr, "hse: batched autotune: shape %d (k' split %d, 24^3 %s, %s, LayoutSeq sides %d%d%d%d): %.3f ms\n",
+                       s.encode(), s.split, s.layout24 == kPencilRagged ? "ragged" : "one pencil",
+                       s.serial ? "serial" : "concurrent", s.seq[0], s.seq[1], s.seq[2], s.seq[3], *ms);
+        return r;
+      };
+      float best_ms = 0.f;
+      if (e == cudaSuccess) e = time_shape(best, &best_ms);
+      auto trial = [&](const BatchShape& s) {
+        float ms = 0.f;
+        if (e == cudaSuccess) e = time_shape(s, &ms);
+        if (e == cudaSuccess && ms < best_ms) {
+          best = s;
+          best_ms = ms;
+        }
+      };
+      const BatchShape base = best;
+      for (int split : {2, 4}) {
+        BatchShape s = base;
+        s.split = split;
+        trial(s);
       }
-      if (e == cudaSuccess && log_on())
-        std::fprintf(stderr, "hse: batched autotune: k' split %d: %.3f ms\n", cands[ci], ms);
+      if (has24) {
+        BatchShape s = best;
+        s.layout24 = kPencilRagged;
+        trial(s);
+      }
+      for (int i = 0; i < 4; ++i) {
+        if (!present[i]) continue;
+        BatchShape s = best;
+        s.seq[i] = 1;
+        trial(s);
+      }
+      if (has24 && nstaged_cells > 0) {
+        BatchShape s = best;
+        s.serial = true;
+        trial(s);
+      }
+      if (t0) cudaEventDestroy(t0);
+      if (t1) cudaEventDestroy(t1);
+      if (e != cudaSuccess) return cuda_fail(e);
+      autotune_store(key, best.encode());
+    } else if (log_on()) {
+      std::fprintf(stderr, "hse: batched autotune: shape %d from the cache\n", cached);
     }
-    if (t0) cudaEventDestroy(t0);
-    if (t1) cudaEventDestroy(t1);
-    if (e != cudaSuccess) return cuda_fail(e);
-    if (cached > 0) {
-      if (log_on()) std::fprintf(stderr, "hse: batched autotune: k' split %d from the cache\n", cached);
-    } else {
-      autotune_store(key, best);
-    }
-    plan->batch_split = best;
-    if (log_on()) std::fprintf(stderr, "hse: batched autotune: chose k' split %d\n", best);
-    build_batch(plan, best, vx_out);
+    plan->batch_split = best.split;
+    if (log_on()) std::fprintf(stderr, "hse: batched autotune: chose shape %d\n", best.encode());
+    apply(best);
     // capture counter reset + persistent kernels + split reduction as one graph
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal);

@@ -60,6 +60,7 @@ struct BatchCell {
   PairArgs pa;          // the cell's launch arguments (pa.out: final output or split buffer)
   float2* final_out;    // the cell's V_x u output
   int n;                // grid side
+  int layout;           // staged sides: 0 LayoutOne, 1 LayoutSeq (12^3: LayoutSeq either way)
 };
 struct BatchItem {
   int cell;             // index into the cell table
@@ -76,9 +77,16 @@ bool batched_side_supported(int n);
 // Stage geometry of the side's staged pipeline in the batched launch (pitch and box rows of
 // its tensor map); false for sides that run the pencil-load item there.
 bool batched_stage_geometry(int n, int* sp, int* box_rows);
-// The two persistent kernels of a batch: the staged-partner items and the pencil-load items
-// (either list may be empty), in stream order.
-cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& pencil, int sms, cudaStream_t stream);
+// Pencil layout of the 24^3 items of a batch: one pencil per thread (18 warps) or the ragged
+// 12-warp form.
+constexpr int kPencilOne = 0;
+constexpr int kPencilRagged = 1;
+// The two persistent kernels of a batch: the pencil-load items, then the staged-partner items
+// (either list may be empty).  With side, fork and join given, the staged kernel runs on the
+// side stream, forked from and joined back into `stream` (both kernels at once; capturable),
+// else after the pencil kernel on `stream`.
+cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& pencil, int sms, int pencil_layout,
+                                    cudaStream_t stream, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 
 // One staged FP64 1-D transform pass along an axis of length L with element stride inner.
 cudaError_t launch_staged_fft(int L, int dir, double2* work, size_t nbatch, int N, int inner, cudaStream_t stream);

@@ -142,6 +142,19 @@ struct PairArgs {
   int item_count;       // (0: all items)
 };
 
+// Work item `item` -> (split, k, tile), split slowest: the items of one k' split (one range of
+// partner orbitals) run together, so the partners a wave reads stay in L2 from wave to wave.
+struct ItemIdx {
+  int split, k, tile;
+  __device__ __forceinline__ ItemIdx(const PairArgs& a, int item) {
+    const int per_split = a.nk_own * a.ntiles;
+    split = item / per_split;
+    const int rem = item - split * per_split;
+    k = rem / a.ntiles;
+    tile = rem - k * a.ntiles;
+  }
+};
+
 // ---------------------------------------------------------------------------------------
 // Compensated accumulation over k' (Sec. II C, Eq. "Fock": V_x u sums the pair terms over
 // every k' and every occupied band).  The TMEM accumulator of a pencil holds the sum over the
@@ -732,11 +745,10 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
 
   // work item: (split, k, tile); split s covers partner k-points
   // [s nk_part / nsplit, (s+1) nk_part / nsplit)
-  const int per_split = args.nk_own * args.ntiles;
-  const int split = item / per_split;
-  const int rem = item - split * per_split;
-  const int k = rem / args.ntiles;
-  const int band = (rem - k * args.ntiles) * G::T + slot;
+  const ItemIdx it(args, item);
+  const int split = it.split;
+  const int k = it.k;
+  const int band = it.tile * G::T + slot;
   const int kp_begin = (int)(((long long)split * args.nk_part) / args.nsplit);
   const int kp_end = (int)(((long long)(split + 1) * args.nk_part) / args.nsplit);
   const bool active = valid && band < args.n_own;

@@ -232,11 +232,10 @@ __device__ __forceinline__ bool staged_item(const PairArgs& args, const CUtensor
   const uint32_t trow0 = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * S::COLS_PER_WARP);
   const uint32_t town = trow0 + (uint32_t)Lay::OWN;
 
-  const int per_split = args.nk_own * args.ntiles;
-  const int split = item / per_split;
-  const int rem = item - split * per_split;
-  const int k = rem / args.ntiles;
-  const int band = (rem - k * args.ntiles) * G::T + slot;
+  const ItemIdx it(args, item);
+  const int split = it.split;
+  const int k = it.k;
+  const int band = it.tile * G::T + slot;
   const bool active = valid && band < args.n_own;
   const int bandc = active ? band : 0;
   const int kp_begin = (int)(((long long)split * args.nk_part) / args.nsplit);

@@ -68,9 +68,10 @@ def test_uneven_batch_32_cells_matches_single_cell_path():
 
 
 def test_autotune_cache_round_trip(tmp_path, monkeypatch):
-    """HSE_AUTOTUNE_CACHE: the first batched plan times the candidate k' splits and stores its
-    choice under a key naming the GPU and the cells; a second plan with the same cells reads it
-    back (no timing runs) and computes the same result."""
+    """HSE_AUTOTUNE_CACHE: the first batched plan times the candidate launch shapes (k' split,
+    pencil layouts, serial or concurrent kernels) and stores its choice under a key naming the
+    GPU and the cells; a second plan with the same cells reads it back (no timing runs) and
+    computes the same result."""
     cache = tmp_path / "autotune.tsv"
     monkeypatch.setenv("HSE_AUTOTUNE_CACHE", str(cache))
     cells = inputs.batched_cells(4)
@@ -79,9 +80,37 @@ def test_autotune_cache_round_trip(tmp_path, monkeypatch):
     first = hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)
     torch.cuda.synchronize()
     lines = cache.read_text().splitlines()
-    assert len(lines) == 1 and lines[0].split("\t")[1] in ("1", "2", "4")
+    # the stored shape: bits 0-2 the k' split, higher bits the layouts and the serial flag
+    assert len(lines) == 1 and int(lines[0].split("\t")[1]) & 7 in (1, 2, 4)
     second = hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)
     torch.cuda.synchronize()
     assert cache.read_text().splitlines() == lines  # served from the cache, nothing appended
     for a, b in zip(first, second):
         assert torch.equal(a, b)
+
+
+def test_every_tuned_shape_vs_oracle(tmp_path, monkeypatch):
+    """The launch shapes the autotuner can choose, forced through the autotune cache: the ragged
+    24^3 layout with the two persistent kernels one after the other, two pencils a thread on
+    every staged side with a k' split of 2, and a split of 4 with the defaults; each against the
+    oracle on a batch with every supported side."""
+    cache = tmp_path / "autotune.tsv"
+    monkeypatch.setenv("HSE_AUTOTUNE_CACHE", str(cache))
+    specs = [((8, 8, 8), (2, 1, 1), 3), ((12, 12, 12), (2, 2, 1), 3), ((16, 16, 16), (1, 1, 2), 3),
+             ((18, 18, 18), (1, 2, 1), 2), ((20, 20, 20), (2, 1, 1), 2), ((24, 24, 24), (2, 1, 1), 2)]
+    cells = [inputs.make_cell(950 + i, g, km, nb) for i, (g, km, nb) in enumerate(specs)]
+    for c in cells:
+        c.u_occ = c.u_occ.astype(np.complex64).astype(np.complex128)
+        c.u_tgt = c.u_occ
+    uo = [dev(c.u_occ) for c in cells]
+    oc = [dev(c.occ, torch.float64) for c in cells]
+    refs = [oracle.fock_apply(c.u_occ, c.occ, c.u_occ, c.kpts, c.lattice, c.grid, c.omega, c.alpha) for c in cells]
+    hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)  # autotunes and stores its line
+    torch.cuda.synchronize()
+    key = cache.read_text().splitlines()[0].split("\t")[0]
+    for shape in (1 | 8 | 16, 2 | 32 | 64 | 128 | 256, 4):
+        cache.write_text(f"{key}\t{shape}\n")
+        out = hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)
+        torch.cuda.synchronize()
+        for c, o, ref in zip(cells, out, refs):
+            assert rel(o.cpu().numpy(), ref) <= 1e-5, (shape, c.grid)

@@ -4,7 +4,8 @@ The layout is chosen per plan through HSE_BLOCKS_PER_SM: for the staged-partner 
 pencils per thread, -2 one pencil per thread; for the pencil-load kernel 1 one CTA per SM with uncapped registers (two
 pencils per thread on 9 warps at 24^3), 2 two CTAs per SM where they fit (16^3), and 3 the
 ragged 24^3 form (12 warps, a second pencil for the first 192 threads), 5 one pencil per
-thread on 18 warps (24^3; the VJP's u_occ pass keeps the ragged form).
+thread on 18 warps (24^3, the default there for the owner = target passes; the VJP's u_occ
+pass keeps the ragged form).
 The pencil-load kernel reads pencil-blocked copies of the orbitals by default; the cases with
 HSE_PENCIL_BLOCKS=0 run it on the caller's [x][y][z] arrays.  For every layout the test runs V_x u (owner = target apply), the exchange energy (energy epilogue) and
 the full vector-Jacobian product, whose d/d omega term runs the owner = target dot epilogue
