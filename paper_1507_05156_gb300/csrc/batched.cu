@@ -8,7 +8,8 @@
 //     stream in by TMA from the cell's tensor map into two stage buffers, the owner orbital
 //     and the accumulators stay in Tensor Memory.  512 threads; per cell the pencil layout
 //     LayoutOne (one pencil per thread) or LayoutSeq (two), as the autotuner chose
-//     (BatchCell::layout; 12^3 runs LayoutSeq, its LayoutOne needs 576 threads);
+//     (BatchCell::layout); 12^3 cells in LayoutOne, whose four owner slots need 576 threads,
+//     form a third list with a kernel of its own;
 //   * pencil-load items (side 24; pairconv_c64.cuh): orbitals are read as pencils through L1,
 //     in the one-pencil form (18 warps, the single-cell default) or the ragged 12-warp form.
 //     That kernel keeps only its own shared-memory footprint so that L1 keeps the rest of the
@@ -43,11 +44,23 @@ static_assert(OneS<8>::FITS && SeqS<12>::FITS && OneS<16>::FITS && OneS<18>::FIT
               "staged layouts of the batched kernel must fit");
 
 // One staged item as a call of its own: each side's pipeline gets the whole register budget
-// instead of sharing one allocation with the other sides' inlined pipelines.
+// instead of sharing one allocation with the other sides' inlined pipelines.  pa: the cell's
+// launch arguments copied to shared memory; tmap: its tensor map (global memory).
 template <int n, int MODE, template <int> class L>
-__device__ __noinline__ bool staged_call(const BatchCell& c, int item, char* sbase, uint32_t tbase, StagedShared& sh,
-                                         uint32_t& ph0, uint32_t& ph1, bool on) {
-  return staged_item<n, MODE, L>(c.pa, &c.tmap, item, sbase, tbase, sh, ph0, ph1, on);
+__device__ __noinline__ bool staged_call(const PairArgs& pa, const CUtensorMap* tmap, int item, char* sbase,
+                                         uint32_t tbase, StagedShared& sh, uint32_t& ph0, uint32_t& ph1, bool on) {
+  return staged_item<n, MODE, L>(pa, tmap, item, sbase, tbase, sh, ph0, ph1, on);
+}
+
+// The cell's launch arguments into shared memory before an item (the item reads them many
+// times; from the cell table in global memory every field would be a load that the
+// register-bound pipelines cannot keep).  Every thread calls this; it synchronises the block.
+__device__ __forceinline__ void load_cell_args(PairArgs* dst, const PairArgs& src) {
+  static_assert(sizeof(PairArgs) % 8 == 0, "PairArgs copies as 8-byte words");
+  const uint64_t* s = reinterpret_cast<const uint64_t*>(&src);
+  uint64_t* d = reinterpret_cast<uint64_t*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(PairArgs) / 8); i += blockDim.x) d[i] = s[i];
+  __syncthreads();
 }
 
 // Next item of this CTA (block-uniform), or -1 when the list is exhausted.
@@ -65,6 +78,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) pairconv_batched_staged_ker
   __shared__ uint32_t tmem_base_sh;
   __shared__ StagedShared sh;
   __shared__ int next_sh;
+  __shared__ __align__(16) PairArgs pa_sh;
   char* sbase = staged_smem_base(smem4, b.status);
   if (!sbase) return;
   const int warp = threadIdx.x >> 5;
@@ -88,17 +102,21 @@ __global__ void __launch_bounds__(kStagedThreads, 1) pairconv_batched_staged_ker
     if (it < 0) break;
     const BatchItem wi = b.items[it];
     const BatchCell& c = b.cells[wi.cell];
+    load_cell_args(&pa_sh, c.pa);
     bool ok = true;
 #define HSE_STAGED_CASE(N)                                                                              \
   case N:                                                                                               \
-    ok = c.layout ? staged_call<N, MODE, LayoutSeq>(c, wi.item, sbase, tbase, sh, ph0, ph1,            \
+    ok = c.layout ? staged_call<N, MODE, LayoutSeq>(pa_sh, &c.tmap, wi.item, sbase, tbase, sh, ph0, ph1, \
                                                     warp < LayoutSeq<N>::WARPS)                          \
-                  : staged_call<N, MODE, LayoutOne>(c, wi.item, sbase, tbase, sh, ph0, ph1,            \
+                  : staged_call<N, MODE, LayoutOne>(pa_sh, &c.tmap, wi.item, sbase, tbase, sh, ph0, ph1, \
                                                     warp < LayoutOne<N>::WARPS);                         \
     break;
     switch (c.n) {
       HSE_STAGED_CASE(8)
-      case 12: ok = staged_call<12, MODE, LayoutSeq>(c, wi.item, sbase, tbase, sh, ph0, ph1, warp < LayoutSeq<12>::WARPS); break;
+      case 12:
+        ok = staged_call<12, MODE, LayoutSeq>(pa_sh, &c.tmap, wi.item, sbase, tbase, sh, ph0, ph1,
+                                              warp < LayoutSeq<12>::WARPS);
+        break;
       HSE_STAGED_CASE(16)
       HSE_STAGED_CASE(18)
       HSE_STAGED_CASE(20)
@@ -113,6 +131,50 @@ __global__ void __launch_bounds__(kStagedThreads, 1) pairconv_batched_staged_ker
   if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
+// The 12^3 items in LayoutOne (four owner slots of 144 threads, 576 threads): a kernel of its
+// own, since the 512-thread staged kernel can only run 12^3 in LayoutSeq.
+template <int MODE>
+__global__ void __launch_bounds__(LayoutOne<12>::THREADS, 1) pairconv_batched_staged12_kernel(const BatchArgs b) {
+  extern __shared__ __align__(128) float4 smem4[];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ StagedShared sh;
+  __shared__ int next_sh;
+  __shared__ __align__(16) PairArgs pa_sh;
+  char* sbase = staged_smem_base(smem4, b.status);
+  if (!sbase) return;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(&sh.mbar[0], 1);
+    mbar_init(&sh.mbar[1], 1);
+    sh.abort = 0;
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base_sh, 512);
+    tmem_relinquish();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tbase = tmem_base_sh;
+  uint32_t ph0 = 0, ph1 = 0;
+  for (;;) {
+    const int it = next_item(b, &next_sh);
+    if (it < 0) break;
+    const BatchItem wi = b.items[it];
+    const BatchCell& c = b.cells[wi.cell];
+    load_cell_args(&pa_sh, c.pa);
+    const bool ok = c.n == 12 ? staged_item<12, MODE, LayoutOne>(pa_sh, &c.tmap, wi.item, sbase, tbase, sh, ph0, ph1,
+                                                                 true)
+                              : true;  // the host puts only 12^3 cells in this list
+    if (!ok) break;
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(tbase, 512);
+}
+
 // PPT, TS: the pencil layout of the 24^3 items (one pencil per thread on 576 threads, or the
 // ragged form on 384).
 template <int MODE, int PPT, int TS>
@@ -120,6 +182,7 @@ __global__ void __launch_bounds__(GeoP<24, PPT, TS>::THREADS, 1) pairconv_batche
   extern __shared__ __align__(16) float4 smem4[];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int next_sh;
+  __shared__ __align__(16) PairArgs pa_sh;
   const int warp = threadIdx.x >> 5;
   if (warp == 0) {
     tmem_alloc(&tmem_base_sh, 512);
@@ -134,9 +197,10 @@ __global__ void __launch_bounds__(GeoP<24, PPT, TS>::THREADS, 1) pairconv_batche
     if (it < 0) break;
     const BatchItem wi = b.items[it];
     const BatchCell& c = b.cells[wi.cell];
+    load_cell_args(&pa_sh, c.pa);
     switch (c.n) {
       case 24:
-        pairconv_item<24, MODE, PPT, TS>(c.pa, wi.item, smem4, tbase, warp < GeoP<24, PPT, TS>::WARPS);
+        pairconv_item<24, MODE, PPT, TS>(pa_sh, wi.item, smem4, tbase, warp < GeoP<24, PPT, TS>::WARPS);
         break;
       default: break;  // the host puts only the sides above in this list
     }
@@ -155,6 +219,8 @@ constexpr size_t kStagedSmem =
                 max_c(max_c(SeqS<16>::SMEM_REQUEST, SeqS<18>::SMEM_REQUEST), SeqS<20>::SMEM_REQUEST)));
 // >= 118784: a second CTA (which would need TMEM too) never fits
 constexpr size_t kPencilSmem = max_c(Geo<24>::SMEM_BYTES, (size_t)118784);
+constexpr size_t kStaged12Smem = OneS<12>::SMEM_REQUEST;
+static_assert(OneS<12>::FITS, "12^3 LayoutOne must fit its batched kernel");
 
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes, bool* done) {
@@ -195,12 +261,14 @@ cudaError_t launch_pencil_list(const BatchArgs& pencil, int sms, cudaStream_t st
   return cudaGetLastError();
 }
 
-cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& pencil, int sms, int pencil_layout,
-                                    cudaStream_t stream, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
-  static bool done_s[64] = {};
+cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& staged12, const BatchArgs& pencil, int sms,
+                                    int pencil_layout, cudaStream_t stream, cudaStream_t side, cudaEvent_t fork,
+                                    cudaEvent_t join) {
+  static bool done_s[64] = {}, done_12[64] = {};
   cudaError_t err = set_smem(pairconv_batched_staged_kernel<MODE_APPLY>, kStagedSmem, done_s);
+  if (err == cudaSuccess) err = set_smem(pairconv_batched_staged12_kernel<MODE_APPLY>, kStaged12Smem, done_12);
   if (err != cudaSuccess) return err;
-  const bool both = pencil.nitems > 0 && staged.nitems > 0;
+  const bool both = pencil.nitems > 0 && (staged.nitems > 0 || staged12.nitems > 0);
   const bool fork_side = both && side && fork && join;
   // the pencil-load list first: its 24^3 items are the longest; the staged list on the side
   // stream (when given) starts on the SMs the pencil kernel leaves and takes over its tail
@@ -219,6 +287,13 @@ cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& pe
   if (staged.nitems > 0) {
     pairconv_batched_staged_kernel<MODE_APPLY>
         <<<sms < staged.nitems ? sms : staged.nitems, kStagedThreads, kStagedSmem, s2>>>(staged);
+    count_launch();
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  if (staged12.nitems > 0) {  // after the staged list, on its stream
+    pairconv_batched_staged12_kernel<MODE_APPLY>
+        <<<sms < staged12.nitems ? sms : staged12.nitems, LayoutOne<12>::THREADS, kStaged12Smem, s2>>>(staged12);
     count_launch();
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;

@@ -324,9 +324,10 @@ struct hse_plan_s {
   std::vector<float2*> cell_comp;       // per cell [min(kMaxBatchSplit, nk)][nk][n_tgt][2][blocked] running sums
   BatchCell* d_cells = nullptr;
   BatchItem* d_items = nullptr;         // staged-partner items, then pencil-load items
-  int* d_counter = nullptr;             // [2]: one per list
+  int* d_counter = nullptr;             // [3]: one per list
   int nitems = 0;
   int nitems_staged = 0;
+  int nitems_pencil = 0;
   int batch_split = 0;                  // autotuned k' split (0: not tuned yet)
   int batch_layout24 = kPencilOne;      // autotuned pencil layout of the 24^3 items
   bool batch_serial = false;            // autotuned: the two persistent kernels one after the other
@@ -405,17 +406,19 @@ void autotune_store(const std::string& key, int shape) {
 }
 
 // One point of the batched autotuner's search space, stored in the autotune cache as an int:
-// bits 0-2 the k' split (1, 2 or 4), bit 3 the ragged 24^3 layout, bit 4 the two persistent
-// kernels one after the other, bits 5-8 LayoutSeq for the staged sides 8, 16, 18, 20.  Zero
-// bits are the defaults, so a bare split (an older cache line) reads as the default shape.
+// bits 0-2 the k' split (1, 2 or 4), bit 3 the ragged 24^3 layout, bit 4 the kernels one after
+// the other, bits 5-9 LayoutSeq for the staged sides 8, 16, 18, 20, 12 (12^3 then runs in the
+// 512-thread staged kernel instead of its own LayoutOne kernel).  Zero bits are the defaults, so
+// a bare split (an older cache line) reads as the default shape.
+constexpr int kShapeSides = 5;
 struct BatchShape {
   int split = 1;
   int layout24 = kPencilOne;
   bool serial = false;
-  int seq[4] = {0, 0, 0, 0};  // sides 8, 16, 18, 20
+  int seq[kShapeSides] = {0, 0, 0, 0, 0};  // sides 8, 16, 18, 20, 12
   int encode() const {
     int v = split | (layout24 == kPencilRagged ? 8 : 0) | (serial ? 16 : 0);
-    for (int i = 0; i < 4; ++i) v |= seq[i] ? (32 << i) : 0;
+    for (int i = 0; i < kShapeSides; ++i) v |= seq[i] ? (32 << i) : 0;
     return v;
   }
   static BatchShape decode(int v) {
@@ -423,12 +426,12 @@ struct BatchShape {
     s.split = v & 7;
     s.layout24 = (v & 8) ? kPencilRagged : kPencilOne;
     s.serial = (v & 16) != 0;
-    for (int i = 0; i < 4; ++i) s.seq[i] = (v >> (5 + i)) & 1;
+    for (int i = 0; i < kShapeSides; ++i) s.seq[i] = (v >> (5 + i)) & 1;
     return s;
   }
 };
 
-int side_slot(int n) { return n == 8 ? 0 : n == 16 ? 1 : n == 18 ? 2 : n == 20 ? 3 : -1; }
+int side_slot(int n) { return n == 8 ? 0 : n == 16 ? 1 : n == 18 ? 2 : n == 20 ? 3 : n == 12 ? 4 : -1; }
 
 int cuda_fail(cudaError_t e) { return e == cudaSuccess ? HSE_OK : (e == cudaErrorMemoryAllocation ? HSE_ERR_NOMEM : HSE_ERR_CUDA); }
 
@@ -1032,7 +1035,7 @@ void build_batch(hse_plan plan, int split, void* const* vx_out) {
     double cost;
     BatchItem it;
   };
-  std::vector<Entry> list[2];
+  std::vector<Entry> list[3];
   for (size_t c = 0; c < plan->cells.size(); ++c) {
     const hse_problem& q = plan->cells[c]->p;
     BatchCell& bc = plan->h_cells[c];
@@ -1043,7 +1046,10 @@ void build_batch(hse_plan plan, int split, void* const* vx_out) {
     const int ntiles = (q.n_tgt + T - 1) / T;
     const double n = q.grid[0];
     int sp_unused = 0, br_unused = 0;
-    const int which = batched_stage_geometry(q.grid[0], &sp_unused, &br_unused) ? 0 : 1;
+    // 0: the staged kernel, 1: the pencil-load kernel, 2: the 12^3 LayoutOne kernel
+    const int which = !batched_stage_geometry(q.grid[0], &sp_unused, &br_unused) ? 1
+                      : (q.grid[0] == 12 && bc.layout == 0)                       ? 2
+                                                                                  : 0;
     for (int sp = 0; sp < ns; ++sp) {
       const int kp0 = (int)(((long long)sp * q.nk) / ns), kp1 = (int)(((long long)(sp + 1) * q.nk) / ns);
       const double cost = (double)(kp1 - kp0) * q.n_occ * n * n * n * std::log2(n);
@@ -1051,23 +1057,26 @@ void build_batch(hse_plan plan, int split, void* const* vx_out) {
     }
   }
   std::vector<BatchItem> items;
-  for (int w = 0; w < 2; ++w) {
+  for (int w = 0; w < 3; ++w) {
     std::stable_sort(list[w].begin(), list[w].end(), [](const Entry& x, const Entry& y) { return x.cost > y.cost; });
     for (const Entry& e : list[w]) items.push_back(e.it);
   }
   plan->nitems_staged = (int)list[0].size();
+  plan->nitems_pencil = (int)list[1].size();
   plan->nitems = (int)items.size();
   cudaMemcpy(plan->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
 }
 
 // counter reset + the two persistent kernels + reduction of split cells (graph-capturable)
 cudaError_t run_batch(hse_plan plan, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(plan->d_counter, 0, 2 * sizeof(int), st);
-  const BatchArgs staged{plan->d_cells, plan->d_items, plan->nitems_staged, plan->d_counter, plan->status};
-  const BatchArgs pencil{plan->d_cells, plan->d_items + plan->nitems_staged, plan->nitems - plan->nitems_staged,
-                         plan->d_counter + 1, plan->status};
+  cudaError_t e = cudaMemsetAsync(plan->d_counter, 0, 3 * sizeof(int), st);
+  const int n0 = plan->nitems_staged, n1 = plan->nitems_pencil;
+  const BatchArgs staged{plan->d_cells, plan->d_items, n0, plan->d_counter, plan->status};
+  const BatchArgs pencil{plan->d_cells, plan->d_items + n0, n1, plan->d_counter + 1, plan->status};
+  const BatchArgs staged12{plan->d_cells, plan->d_items + n0 + n1, plan->nitems - n0 - n1, plan->d_counter + 2,
+                           plan->status};
   if (e == cudaSuccess)
-    e = launch_pairconv_batched(staged, pencil, plan->sms, plan->batch_layout24, st,
+    e = launch_pairconv_batched(staged, staged12, pencil, plan->sms, plan->batch_layout24, st,
                                 plan->batch_serial ? nullptr : plan->side_stream, plan->ev_fork, plan->ev_join);
   if (e == cudaSuccess && plan->batch_split != 1) {
     reduce_splits_batched<<<plan->sms * 4, 256, 0, st>>>(plan->d_cells, (int)plan->cells.size());
@@ -1479,7 +1488,7 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
   }
   if (rc == HSE_OK && e == cudaSuccess) e = plan_malloc(plan, &plan->d_cells, (size_t)ncells * sizeof(BatchCell));
   if (rc == HSE_OK && e == cudaSuccess) e = plan_malloc(plan, &plan->d_items, max_items * sizeof(BatchItem));
-  if (rc == HSE_OK && e == cudaSuccess) e = plan_malloc(plan, &plan->d_counter, 2 * sizeof(int));
+  if (rc == HSE_OK && e == cudaSuccess) e = plan_malloc(plan, &plan->d_counter, 3 * sizeof(int));
   if (rc == HSE_OK && e == cudaSuccess) e = plan_malloc(plan, &plan->status, sizeof(int));
   if (rc == HSE_OK && e == cudaSuccess) e = cudaMemset(plan->status, 0, sizeof(int));
   if (rc == HSE_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking);
@@ -1581,7 +1590,7 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
     // descent from the defaults, each candidate timed on the real inputs.
     const std::string key = autotune_key(plan);
     const int cached = autotune_lookup(key);
-    bool has24 = false, present[4] = {false, false, false, false};
+    bool has24 = false, present[kShapeSides] = {false, false, false, false, false};
     int nstaged_cells = 0;
     for (hse_plan c : plan->cells) {
       const int n = c->p.grid[0];
@@ -1590,13 +1599,13 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
       if (n != 24) ++nstaged_cells;
     }
     auto apply = [&](const BatchShape& s) {
-      build_batch(plan, s.split, vx_out);
       plan->batch_layout24 = s.layout24;
       plan->batch_serial = s.serial;
       for (int c = 0; c < ncells; ++c) {
         const int slot = side_slot(plan->h_cells[c].n);
         plan->h_cells[c].layout = slot >= 0 ? s.seq[slot] : 0;
       }
+      build_batch(plan, s.split, vx_out);  // the lists depend on the layouts
     };
     BatchShape best = cached > 0 ? BatchShape::decode(cached) : BatchShape();
     if (cached <= 0) {
@@ -1613,9 +1622,11 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
         if (r == cudaSuccess) r = cudaEventSynchronize(t1);
         if (r == cudaSuccess) r = cudaEventElapsedTime(ms, t0, t1);
         if (r == cudaSuccess && log_on())
-          std::fprintf(stderr, "hse: batched autotune: shape %d (k' split %d, 24^3 %s, %s, LayoutSeq sides %d%d%d%d): %.3f ms\n",
+          std::fprintf(stderr,
+                       "hse: batched autotune: shape %d (k' split %d, 24^3 %s, %s, LayoutSeq at 8 16 18 20 12: "
+                       "%d %d %d %d %d): %.3f ms\n",
                        s.encode(), s.split, s.layout24 == kPencilRagged ? "ragged" : "one pencil",
-                       s.serial ? "serial" : "concurrent", s.seq[0], s.seq[1], s.seq[2], s.seq[3], *ms);
+                       s.serial ? "serial" : "concurrent", s.seq[0], s.seq[1], s.seq[2], s.seq[3], s.seq[4], *ms);
         return r;
       };
       float best_ms = 0.f;
@@ -1639,7 +1650,7 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
         s.layout24 = kPencilRagged;
         trial(s);
       }
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < kShapeSides; ++i) {
         if (!present[i]) continue;
         BatchShape s = best;
         s.seq[i] = 1;

@@ -60,7 +60,7 @@ struct BatchCell {
   PairArgs pa;          // the cell's launch arguments (pa.out: final output or split buffer)
   float2* final_out;    // the cell's V_x u output
   int n;                // grid side
-  int layout;           // staged sides: 0 LayoutOne, 1 LayoutSeq (12^3: LayoutSeq either way)
+  int layout;           // staged sides: 0 LayoutOne, 1 LayoutSeq
 };
 struct BatchItem {
   int cell;             // index into the cell table
@@ -81,12 +81,13 @@ bool batched_stage_geometry(int n, int* sp, int* box_rows);
 // 12-warp form.
 constexpr int kPencilOne = 0;
 constexpr int kPencilRagged = 1;
-// The two persistent kernels of a batch: the pencil-load items, then the staged-partner items
-// (either list may be empty).  With side, fork and join given, the staged kernel runs on the
-// side stream, forked from and joined back into `stream` (both kernels at once; capturable),
-// else after the pencil kernel on `stream`.
-cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& pencil, int sms, int pencil_layout,
-                                    cudaStream_t stream, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+// The persistent kernels of a batch: the pencil-load items, then the staged-partner items and
+// the 12^3 LayoutOne items (any list may be empty).  With side, fork and join given, the staged
+// kernels run on the side stream, forked from and joined back into `stream` (beside the pencil
+// kernel; capturable), else after the pencil kernel on `stream`.
+cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& staged12, const BatchArgs& pencil, int sms,
+                                    int pencil_layout, cudaStream_t stream, cudaStream_t side, cudaEvent_t fork,
+                                    cudaEvent_t join);
 
 // One staged FP64 1-D transform pass along an axis of length L with element stride inner.
 cudaError_t launch_staged_fft(int L, int dir, double2* work, size_t nbatch, int N, int inner, cudaStream_t stream);

@@ -91,9 +91,10 @@ def test_autotune_cache_round_trip(tmp_path, monkeypatch):
 
 def test_every_tuned_shape_vs_oracle(tmp_path, monkeypatch):
     """The launch shapes the autotuner can choose, forced through the autotune cache: the ragged
-    24^3 layout with the two persistent kernels one after the other, two pencils a thread on
-    every staged side with a k' split of 2, and a split of 4 with the defaults; each against the
-    oracle on a batch with every supported side."""
+    24^3 layout with the kernels one after the other, two pencils a thread on every staged side
+    (12^3 then in the 512-thread staged kernel) with a k' split of 2, and a split of 4 with the
+    defaults (12^3 in its own LayoutOne kernel); each against the oracle on a batch with every
+    supported side."""
     cache = tmp_path / "autotune.tsv"
     monkeypatch.setenv("HSE_AUTOTUNE_CACHE", str(cache))
     specs = [((8, 8, 8), (2, 1, 1), 3), ((12, 12, 12), (2, 2, 1), 3), ((16, 16, 16), (1, 1, 2), 3),
@@ -108,7 +109,7 @@ def test_every_tuned_shape_vs_oracle(tmp_path, monkeypatch):
     hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)  # autotunes and stores its line
     torch.cuda.synchronize()
     key = cache.read_text().splitlines()[0].split("\t")[0]
-    for shape in (1 | 8 | 16, 2 | 32 | 64 | 128 | 256, 4):
+    for shape in (1 | 8 | 16, 2 | 32 | 64 | 128 | 256 | 512, 4):
         cache.write_text(f"{key}\t{shape}\n")
         out = hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)
         torch.cuda.synchronize()
