@@ -1,0 +1,473 @@
+// Measured prototype: the 24-point pencil DFTs of the Y and X stages (Sec. II C, Eq. "Fock":
+// the axis transforms of the 3-D FFT) as GEMMs on the fifth-generation tensor cores, against
+// the register FFT of csrc/fft_reg.cuh on the same tiles.  Test-only program (built and run by
+// tests/test_gpu_tcgen05_probe.py); not part of the library.
+//
+// A tile is 128 pencils of 24 complex values.  As real numbers a pencil is a row of 48 values
+// (re, im interleaved) and its DFT is that row times a 48 x 48 real matrix W (cos / sin blocks),
+// so a tile is the product D[128 x 48] = A[128 x 48] W[48 x 48]: one tcgen05.mma of shape
+// M = 128, N = 48 per 8-wide K step (kind::tf32), six K steps.  TF32 keeps 10 mantissa bits,
+// so both operands are split, x = hi + lo with hi = x with its 13 low mantissa bits cleared,
+// and D = A_hi W_hi + A_hi W_lo + A_lo W_hi (the lo lo term, about 2^-22 of D, is left out):
+// 18 MMAs per tile, accumulating in FP32 in Tensor Memory (lane = pencil, 48 columns).
+//
+// Shared memory holds the operands in the canonical K-major layout without swizzle: 8 x 16-byte
+// core matrices (8 rows of 4 TF32 values), the core matrices of one 8-row group along K 128
+// bytes apart (leading byte offset), the 8-row groups 12 x 128 = 1536 bytes apart (stride byte
+// offset).  One thread issues the MMAs and commits them to an mbarrier; every wait is bounded and
+// a timeout sets a status word instead of hanging.
+//
+// Output (stdout, one line each): the accuracy of both kernels against an FP64 DFT of sampled
+// pencils and their times per tile (CUDA events, after warm-up), and the executed tensor FLOP/s.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "../../paper_1507_05156_gb300/csrc/fft_reg.cuh"
+
+namespace {
+
+constexpr int kN = 24;          // DFT length
+constexpr int kK = 2 * kN;      // real row length (K = N of the GEMM)
+constexpr int kM = 128;         // pencils per tile (MMA M)
+constexpr int kLBO = 128;       // bytes between K-adjacent core matrices
+constexpr int kSBO = (kK / 4) * kLBO;  // bytes between 8-row groups: 1536
+constexpr int kTileBytes = kM * kK * 4;  // one operand tile, 24 KB
+constexpr int kWBytes = kK * kK * 4;     // the DFT matrix, 9 KB
+constexpr int kSmem = 2 * kTileBytes + 2 * kWBytes + 64;
+
+#define CHECK(x)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (x);                                                           \
+    if (e_ != cudaSuccess) {                                                        \
+      std::printf("cuda error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+      std::exit(2);                                                                 \
+    }                                                                               \
+  } while (0)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Byte offset of element (row r, k) in the canonical K-major no-swizzle layout (4-byte elements).
+__host__ __device__ constexpr uint32_t canon(int r, int k) {
+  return (uint32_t)((r >> 3) * kSBO + (k >> 2) * kLBO + (r & 7) * 16 + (k & 3) * 4);
+}
+
+// Shared-memory matrix descriptor: start address, leading and stride byte offsets (all >> 4),
+// the fixed constant 0b001 at bits 46-48, no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((kLBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((kSBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2),
+// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kK >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+  const long long deadline = clock64() + 2000000000LL;
+  uint32_t done = 0;
+  while (!done) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (!done && clock64() > deadline) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];\n\ttcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// W (hi, lo), rows n (output column of D, 48) x k (48), in the canonical layout, from the
+// host-computed FP32 matrix w[k][n] (d[n] = sum_k a[k] w[k][n]).
+__global__ void __launch_bounds__(128, 3) tc_dft_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                        const float* __restrict__ w, int ntiles, int* status) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* a_hi = sm;
+  unsigned char* a_lo = sm + kTileBytes;
+  unsigned char* w_hi = sm + 2 * kTileBytes;
+  unsigned char* w_lo = w_hi + kWBytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(w_lo + kWBytes);
+  __shared__ uint32_t tbase_sh;
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  for (int i = t; i < kK * kK; i += blockDim.x) {
+    const int k = i / kK, n = i - k * kK;
+    const float x = w[i], h = tf32_hi(x);
+    *reinterpret_cast<float*>(w_hi + canon(n, k)) = h;
+    *reinterpret_cast<float*>(w_lo + canon(n, k)) = x - h;
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tbase_sh))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = tbase_sh;
+  const uint32_t trow = tbase + ((uint32_t)(32 * warp) << 16);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    // this thread's pencil: row t of the tile, split into TF32 hi and lo parts
+    const float4* src = reinterpret_cast<const float4*>(in + ((size_t)tile * kM + t) * kN);
+#pragma unroll
+    for (int c = 0; c < kK / 4; ++c) {
+      const float4 x = __ldg(src + c);
+      const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+      *reinterpret_cast<float4*>(a_hi + canon(t, 4 * c)) = h;
+      *reinterpret_cast<float4*>(a_lo + canon(t, 4 * c)) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), wh = smem_u32(w_hi), wl = smem_u32(w_lo);
+      for (int s = 0; s < kK / 8; ++s) {
+        const uint32_t off = (uint32_t)(s * 2 * kLBO);  // eight K values = two core matrices
+        mma_tf32(tbase, smem_desc(ah + off), smem_desc(wh + off), s > 0 ? 1u : 0u);
+        mma_tf32(tbase, smem_desc(ah + off), smem_desc(wl + off), 1u);
+        mma_tf32(tbase, smem_desc(al + off), smem_desc(wh + off), 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                   : "memory");
+    }
+    // a wait that ran out anywhere stops every thread of the CTA (block-uniform exit)
+    if (__syncthreads_or(!mbar_wait(mbar, phase))) {
+      ok = false;
+      if (t == 0) atomicExch(status, 1);
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float d[kK];
+    tmem_ld16(trow, d);
+    tmem_ld16(trow + 16, d + 16);
+    tmem_ld16(trow + 32, d + 32);
+    float4* dst = reinterpret_cast<float4*>(out + ((size_t)tile * kM + t) * kN);
+#pragma unroll
+    for (int c = 0; c < kK / 4; ++c) dst[c] = make_float4(d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // the operands and the accumulator are reused by the next tile
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tbase) : "memory");
+}
+
+// The same tiles through the register FFT (one pencil per thread).
+__global__ void __launch_bounds__(128) reg_fft_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                      int ntiles) {
+  const int t = threadIdx.x;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const float4* src = reinterpret_cast<const float4*>(in + ((size_t)tile * kM + t) * kN);
+    hse::cpx<float> v[kN];
+#pragma unroll
+    for (int c = 0; c < kN / 2; ++c) {
+      const float4 x = __ldg(src + c);
+      v[2 * c] = {x.x, x.y};
+      v[2 * c + 1] = {x.z, x.w};
+    }
+    hse::fft<kN, -1, float>(v);
+    float4* dst = reinterpret_cast<float4*>(out + ((size_t)tile * kM + t) * kN);
+#pragma unroll
+    for (int c = 0; c < kN / 2; ++c) dst[c] = make_float4(v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y);
+  }
+}
+
+// Repeated transforms of one tile kept on chip, as the stages of the fused kernel transform
+// pencils that live in shared memory: each CTA loads its tile once and applies the unitary DFT
+// (the DFT / sqrt(24)) reps times; (F / sqrt(N))^4 is the identity, so after a multiple of four
+// the tile must come back.
+//   tensor cores: split the pencil rows into A (shared memory), 18 MMAs, commit, wait, read the
+//                 row back from Tensor Memory, scale;
+//   registers:    read the pencil from shared memory, register FFT, scale, write it back.
+__global__ void __launch_bounds__(128, 3) tc_rep_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                        const float* __restrict__ w, int reps, int* status) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* a_hi = sm;
+  unsigned char* a_lo = sm + kTileBytes;
+  unsigned char* w_hi = sm + 2 * kTileBytes;
+  unsigned char* w_lo = w_hi + kWBytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(w_lo + kWBytes);
+  __shared__ uint32_t tbase_sh;
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  for (int i = t; i < kK * kK; i += blockDim.x) {
+    const int k = i / kK, n = i - k * kK;
+    const float x = w[i], h = tf32_hi(x);
+    *reinterpret_cast<float*>(w_hi + canon(n, k)) = h;
+    *reinterpret_cast<float*>(w_lo + canon(n, k)) = x - h;
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tbase_sh))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = tbase_sh;
+  const uint32_t trow = tbase + ((uint32_t)(32 * warp) << 16);
+  const float sc = 0.20412414523193150818f;  // 1 / sqrt(24)
+  float x[kK];
+  const float4* src = reinterpret_cast<const float4*>(in + ((size_t)blockIdx.x * kM + t) * kN);
+#pragma unroll
+  for (int c = 0; c < kK / 4; ++c) {
+    const float4 v = __ldg(src + c);
+    x[4 * c] = v.x;
+    x[4 * c + 1] = v.y;
+    x[4 * c + 2] = v.z;
+    x[4 * c + 3] = v.w;
+  }
+  uint32_t phase = 0;
+  for (int r = 0; r < reps; ++r) {
+#pragma unroll
+    for (int c = 0; c < kK / 4; ++c) {
+      const float4 h = make_float4(tf32_hi(x[4 * c]), tf32_hi(x[4 * c + 1]), tf32_hi(x[4 * c + 2]), tf32_hi(x[4 * c + 3]));
+      *reinterpret_cast<float4*>(a_hi + canon(t, 4 * c)) = h;
+      *reinterpret_cast<float4*>(a_lo + canon(t, 4 * c)) =
+          make_float4(x[4 * c] - h.x, x[4 * c + 1] - h.y, x[4 * c + 2] - h.z, x[4 * c + 3] - h.w);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), wh = smem_u32(w_hi), wl = smem_u32(w_lo);
+      for (int s = 0; s < kK / 8; ++s) {
+        const uint32_t off = (uint32_t)(s * 2 * kLBO);
+        mma_tf32(tbase, smem_desc(ah + off), smem_desc(wh + off), s > 0 ? 1u : 0u);
+        mma_tf32(tbase, smem_desc(ah + off), smem_desc(wl + off), 1u);
+        mma_tf32(tbase, smem_desc(al + off), smem_desc(wh + off), 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                   : "memory");
+    }
+    if (__syncthreads_or(!mbar_wait(mbar, phase))) {  // block-uniform exit after a timed-out wait
+      if (t == 0) atomicExch(status, 1);
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem_ld16(trow, x);
+    tmem_ld16(trow + 16, x + 16);
+    tmem_ld16(trow + 32, x + 32);
+#pragma unroll
+    for (int e = 0; e < kK; ++e) x[e] *= sc;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  float4* dst = reinterpret_cast<float4*>(out + ((size_t)blockIdx.x * kM + t) * kN);
+#pragma unroll
+  for (int c = 0; c < kK / 4; ++c) dst[c] = make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tbase) : "memory");
+}
+
+__global__ void __launch_bounds__(128) reg_rep_kernel(const float2* __restrict__ in, float2* __restrict__ out, int reps) {
+  __shared__ float2 tile[kM * (kN + 1)];  // one pencil per row, padded against bank conflicts
+  const int t = threadIdx.x;
+  const float sc = 0.20412414523193150818f;
+  const float4* src = reinterpret_cast<const float4*>(in + ((size_t)blockIdx.x * kM + t) * kN);
+#pragma unroll
+  for (int c = 0; c < kN / 2; ++c) {
+    const float4 x = __ldg(src + c);
+    tile[t * (kN + 1) + 2 * c] = make_float2(x.x, x.y);
+    tile[t * (kN + 1) + 2 * c + 1] = make_float2(x.z, x.w);
+  }
+  __syncthreads();
+  for (int r = 0; r < reps; ++r) {
+    hse::cpx<float> v[kN];
+#pragma unroll
+    for (int e = 0; e < kN; ++e) {
+      const float2 x = tile[t * (kN + 1) + e];
+      v[e] = {x.x, x.y};
+    }
+    hse::fft<kN, -1, float>(v);
+#pragma unroll
+    for (int e = 0; e < kN; ++e) tile[t * (kN + 1) + e] = make_float2(v[e].x * sc, v[e].y * sc);
+    __syncthreads();
+  }
+  float4* dst = reinterpret_cast<float4*>(out + ((size_t)blockIdx.x * kM + t) * kN);
+#pragma unroll
+  for (int c = 0; c < kN / 2; ++c) {
+    const float2 a = tile[t * (kN + 1) + 2 * c], b = tile[t * (kN + 1) + 2 * c + 1];
+    dst[c] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
+double rel_diff(const std::vector<float2>& a, const std::vector<float2>& b, size_t n) {
+  double num = 0.0, den = 0.0;
+  for (size_t i = 0; i < n; ++i) {
+    num += (double)(a[i].x - b[i].x) * (a[i].x - b[i].x) + (double)(a[i].y - b[i].y) * (a[i].y - b[i].y);
+    den += (double)b[i].x * b[i].x + (double)b[i].y * b[i].y;
+  }
+  return std::sqrt(num / den);
+}
+
+double rel_err_sampled(const std::vector<float2>& got, const std::vector<float2>& x, int npencils) {
+  double num = 0.0, den = 0.0;
+  const double pi = 3.14159265358979323846;
+  for (int p = 0; p < npencils; p += 97) {
+    for (int k = 0; k < kN; ++k) {
+      double sr = 0.0, si = 0.0;
+      for (int n = 0; n < kN; ++n) {
+        const double a = -2.0 * pi * (double)((n * k) % kN) / kN;
+        const float2 v = x[(size_t)p * kN + n];
+        sr += v.x * std::cos(a) - v.y * std::sin(a);
+        si += v.x * std::sin(a) + v.y * std::cos(a);
+      }
+      const float2 g = got[(size_t)p * kN + k];
+      num += (g.x - sr) * (g.x - sr) + (g.y - si) * (g.y - si);
+      den += sr * sr + si * si;
+    }
+  }
+  return std::sqrt(num / den);
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  const int ntiles = argc > 1 ? std::atoi(argv[1]) : 152 * 3 * 64;
+  if (ntiles < 1) return 1;
+  const size_t npencils = (size_t)ntiles * kM;
+  std::vector<float2> x(npencils * kN);
+  srand(12345);
+  for (auto& v : x) v = make_float2((float)rand() / RAND_MAX - 0.5f, (float)rand() / RAND_MAX - 0.5f);
+  // w[k][n]: d = a W with a = (re0, im0, re1, ...), d = (Re X0, Im X0, ...), X_q = sum_m x_m e^{-2 pi i mq/N}
+  std::vector<float> w(kK * kK);
+  const double pi = 3.14159265358979323846;
+  for (int m = 0; m < kN; ++m)
+    for (int q = 0; q < kN; ++q) {
+      const double a = -2.0 * pi * (double)((m * q) % kN) / kN;
+      const double c = std::cos(a), s = std::sin(a);
+      w[(2 * m) * kK + 2 * q] = (float)c;        // re_m -> Re X_q
+      w[(2 * m + 1) * kK + 2 * q] = (float)-s;   // im_m -> Re X_q
+      w[(2 * m) * kK + 2 * q + 1] = (float)s;    // re_m -> Im X_q
+      w[(2 * m + 1) * kK + 2 * q + 1] = (float)c;  // im_m -> Im X_q
+    }
+  float2 *din, *dtc, *dreg;
+  float* dw;
+  int* dstatus;
+  CHECK(cudaMalloc(&din, x.size() * sizeof(float2)));
+  CHECK(cudaMalloc(&dtc, x.size() * sizeof(float2)));
+  CHECK(cudaMalloc(&dreg, x.size() * sizeof(float2)));
+  CHECK(cudaMalloc(&dw, w.size() * sizeof(float)));
+  CHECK(cudaMalloc(&dstatus, sizeof(int)));
+  CHECK(cudaMemset(dstatus, 0, sizeof(int)));
+  CHECK(cudaMemcpy(din, x.data(), x.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  CHECK(cudaMemcpy(dw, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CHECK(cudaFuncSetAttribute(tc_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  int sms = 0;
+  CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
+  const int grid_tc = sms * 3, grid_reg = sms * 8;
+  cudaEvent_t e0, e1;
+  CHECK(cudaEventCreate(&e0));
+  CHECK(cudaEventCreate(&e1));
+  float ms_tc = 0.f, ms_reg = 0.f;
+  for (int rep = 0; rep < 4; ++rep) {  // three warm-up rounds, the last one timed
+    CHECK(cudaEventRecord(e0));
+    tc_dft_kernel<<<grid_tc, 128, kSmem>>>(din, dtc, dw, ntiles, dstatus);
+    CHECK(cudaEventRecord(e1));
+    CHECK(cudaEventSynchronize(e1));
+    CHECK(cudaGetLastError());
+    CHECK(cudaEventElapsedTime(&ms_tc, e0, e1));
+    CHECK(cudaEventRecord(e0));
+    reg_fft_kernel<<<grid_reg, 128>>>(din, dreg, ntiles);
+    CHECK(cudaEventRecord(e1));
+    CHECK(cudaEventSynchronize(e1));
+    CHECK(cudaGetLastError());
+    CHECK(cudaEventElapsedTime(&ms_reg, e0, e1));
+  }
+  int status = 0;
+  CHECK(cudaMemcpy(&status, dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<float2> tc(x.size()), reg(x.size());
+  CHECK(cudaMemcpy(tc.data(), dtc, tc.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+  CHECK(cudaMemcpy(reg.data(), dreg, reg.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+  const double err_tc = rel_err_sampled(tc, x, (int)npencils);
+  const double err_reg = rel_err_sampled(reg, x, (int)npencils);
+  const double tflop = 3.0 * 2.0 * kM * kK * kK * (double)ntiles / (ms_tc * 1e-3) / 1e12;
+  const double bytes = 2.0 * x.size() * sizeof(float2);
+  std::printf("{\"mode\": \"global\", \"tiles\": %d, \"pencils\": %zu, \"status\": %d, \"err_tc\": %.3e, "
+              "\"err_reg\": %.3e, \"ms_tc\": %.4f, \"ms_reg\": %.4f, \"tc_tensor_tflops\": %.2f, "
+              "\"tc_hbm_gbs\": %.1f, \"reg_hbm_gbs\": %.1f, \"grid_tc\": %d, \"grid_reg\": %d}\n",
+              ntiles, npencils, status, err_tc, err_reg, ms_tc, ms_reg, tflop, bytes / (ms_tc * 1e-3) / 1e9,
+              bytes / (ms_reg * 1e-3) / 1e9, grid_tc, grid_reg);
+  bool ok = status == 0 && err_tc < 1e-5 && err_reg < 1e-5;
+
+  // repeated transforms on chip: every CTA one tile, reps transforms
+  const int reps = argc > 2 ? std::atoi(argv[2]) : 256;
+  CHECK(cudaFuncSetAttribute(tc_rep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  // resident CTAs: 3 a SM (shared memory) and 8 (warps); each CTA reads and writes one tile of
+  // the ntiles that the arrays hold, so neither count may exceed ntiles
+  const int ctas_tc = sms * 3 < ntiles ? sms * 3 : ntiles;
+  const int ctas_reg = sms * 8 < ntiles ? sms * 8 : ntiles;
+  float ms_tcr = 0.f, ms_regr = 0.f;
+  for (int rep = 0; rep < 4; ++rep) {
+    CHECK(cudaEventRecord(e0));
+    tc_rep_kernel<<<ctas_tc, 128, kSmem>>>(din, dtc, dw, reps, dstatus);
+    CHECK(cudaEventRecord(e1));
+    CHECK(cudaEventSynchronize(e1));
+    CHECK(cudaGetLastError());
+    CHECK(cudaEventElapsedTime(&ms_tcr, e0, e1));
+    CHECK(cudaEventRecord(e0));
+    reg_rep_kernel<<<ctas_reg, 128>>>(din, dreg, reps);
+    CHECK(cudaEventRecord(e1));
+    CHECK(cudaEventSynchronize(e1));
+    CHECK(cudaGetLastError());
+    CHECK(cudaEventElapsedTime(&ms_regr, e0, e1));
+  }
+  CHECK(cudaMemcpy(&status, dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  CHECK(cudaMemcpy(tc.data(), dtc, (size_t)ctas_tc * kM * kN * sizeof(float2), cudaMemcpyDeviceToHost));
+  CHECK(cudaMemcpy(reg.data(), dreg, (size_t)ctas_reg * kM * kN * sizeof(float2), cudaMemcpyDeviceToHost));
+  // reps a multiple of 4: the tile comes back (round-off grows with reps)
+  const double back_tc = rel_diff(tc, x, (size_t)ctas_tc * kM * kN);
+  const double back_reg = rel_diff(reg, x, (size_t)ctas_reg * kM * kN);
+  // per SM and microsecond: tile transforms (128 pencils each)
+  const double tps_tc = (double)ctas_tc * reps / sms / (ms_tcr * 1e3);
+  const double tps_reg = (double)ctas_reg * reps / sms / (ms_regr * 1e3);
+  const double tflop_r = 3.0 * 2.0 * kM * kK * kK * (double)ctas_tc * reps / (ms_tcr * 1e-3) / 1e12;
+  std::printf("{\"mode\": \"on_chip\", \"reps\": %d, \"status\": %d, \"back_tc\": %.3e, \"back_reg\": %.3e, "
+              "\"ms_tc\": %.4f, \"ms_reg\": %.4f, \"ctas_tc\": %d, \"ctas_reg\": %d, "
+              "\"tile_transforms_per_sm_us_tc\": %.4f, \"tile_transforms_per_sm_us_reg\": %.4f, "
+              "\"tc_tensor_tflops\": %.2f}\n",
+              reps, status, back_tc, back_reg, ms_tcr, ms_regr, ctas_tc, ctas_reg, tps_tc, tps_reg, tflop_r);
+  ok = ok && status == 0 && (reps % 4 != 0 || (back_tc < 1e-6 * reps && back_reg < 1e-6 * reps));
+  return ok ? 0 : 1;
+}

@@ -1,0 +1,33 @@
+"""Measured prototype of the tensor-core DFT on the fifth-generation tensor cores (tcgen05).
+
+tests/native/tc5_dft_probe.cu transforms tiles of 128 pencils of 24 complex values (the unit
+of work of the Y and X stages of the 24^3 kernel, Sec. II C) two ways: as one split-TF32 GEMM
+per tile with tcgen05.mma (operands in shared memory, accumulator in Tensor Memory, three
+products hi*hi + hi*lo + lo*hi) and with the register FFT of csrc/fft_reg.cuh.  Both are
+checked against an FP64 DFT of sampled pencils (relative error below 1e-5); the printed times
+per tile feed the comparison recorded in the design notes.
+"""
+import json
+import os
+import shutil
+import subprocess
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_tcgen05_dft_prototype_matches_fp64_and_is_timed(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    exe = str(tmp_path / "tc5probe")
+    src = os.path.join(HERE, "native", "tc5_dft_probe.cu")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "--expt-relaxed-constexpr",
+                    src, "-o", exe], check=True, capture_output=True, text=True)
+    res = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    print(res.stdout)
+    line = json.loads(res.stdout.strip().splitlines()[-1])
+    assert res.returncode == 0, res.stdout
+    assert line["status"] == 0
+    assert line["err_tc"] < 1e-5 and line["err_reg"] < 1e-5
