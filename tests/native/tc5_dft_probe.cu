@@ -438,21 +438,30 @@ int main(int argc, char** argv) {
   // the ntiles that the arrays hold, so neither count may exceed ntiles
   const int ctas_tc = sms * 3 < ntiles ? sms * 3 : ntiles;
   const int ctas_reg = sms * 8 < ntiles ? sms * 8 : ntiles;
+  // three warm-up launches of each, then `iters` launches of each timed back to back (a run
+  // long enough for clock sampling during it), the mean per launch reported
+  const int iters = argc > 3 ? std::atoi(argv[3]) : 1;
   float ms_tcr = 0.f, ms_regr = 0.f;
-  for (int rep = 0; rep < 4; ++rep) {
-    CHECK(cudaEventRecord(e0));
+  for (int rep = 0; rep < 3; ++rep) {
     tc_rep_kernel<<<ctas_tc, 128, kSmem>>>(din, dtc, dw, reps, dstatus);
-    CHECK(cudaEventRecord(e1));
-    CHECK(cudaEventSynchronize(e1));
-    CHECK(cudaGetLastError());
-    CHECK(cudaEventElapsedTime(&ms_tcr, e0, e1));
-    CHECK(cudaEventRecord(e0));
     reg_rep_kernel<<<ctas_reg, 128>>>(din, dreg, reps);
-    CHECK(cudaEventRecord(e1));
-    CHECK(cudaEventSynchronize(e1));
-    CHECK(cudaGetLastError());
-    CHECK(cudaEventElapsedTime(&ms_regr, e0, e1));
   }
+  CHECK(cudaDeviceSynchronize());
+  CHECK(cudaGetLastError());
+  CHECK(cudaEventRecord(e0));
+  for (int i = 0; i < iters; ++i) tc_rep_kernel<<<ctas_tc, 128, kSmem>>>(din, dtc, dw, reps, dstatus);
+  CHECK(cudaEventRecord(e1));
+  CHECK(cudaEventSynchronize(e1));
+  CHECK(cudaGetLastError());
+  CHECK(cudaEventElapsedTime(&ms_tcr, e0, e1));
+  ms_tcr /= iters;
+  CHECK(cudaEventRecord(e0));
+  for (int i = 0; i < iters; ++i) reg_rep_kernel<<<ctas_reg, 128>>>(din, dreg, reps);
+  CHECK(cudaEventRecord(e1));
+  CHECK(cudaEventSynchronize(e1));
+  CHECK(cudaGetLastError());
+  CHECK(cudaEventElapsedTime(&ms_regr, e0, e1));
+  ms_regr /= iters;
   CHECK(cudaMemcpy(&status, dstatus, sizeof(int), cudaMemcpyDeviceToHost));
   CHECK(cudaMemcpy(tc.data(), dtc, (size_t)ctas_tc * kM * kN * sizeof(float2), cudaMemcpyDeviceToHost));
   CHECK(cudaMemcpy(reg.data(), dreg, (size_t)ctas_reg * kM * kN * sizeof(float2), cudaMemcpyDeviceToHost));
@@ -463,11 +472,11 @@ int main(int argc, char** argv) {
   const double tps_tc = (double)ctas_tc * reps / sms / (ms_tcr * 1e3);
   const double tps_reg = (double)ctas_reg * reps / sms / (ms_regr * 1e3);
   const double tflop_r = 3.0 * 2.0 * kM * kK * kK * (double)ctas_tc * reps / (ms_tcr * 1e-3) / 1e12;
-  std::printf("{\"mode\": \"on_chip\", \"reps\": %d, \"status\": %d, \"back_tc\": %.3e, \"back_reg\": %.3e, "
+  std::printf("{\"mode\": \"on_chip\", \"reps\": %d, \"iters\": %d, \"status\": %d, \"back_tc\": %.3e, \"back_reg\": %.3e, "
               "\"ms_tc\": %.4f, \"ms_reg\": %.4f, \"ctas_tc\": %d, \"ctas_reg\": %d, "
               "\"tile_transforms_per_sm_us_tc\": %.4f, \"tile_transforms_per_sm_us_reg\": %.4f, "
               "\"tc_tensor_tflops\": %.2f}\n",
-              reps, status, back_tc, back_reg, ms_tcr, ms_regr, ctas_tc, ctas_reg, tps_tc, tps_reg, tflop_r);
+              reps, iters, status, back_tc, back_reg, ms_tcr, ms_regr, ctas_tc, ctas_reg, tps_tc, tps_reg, tflop_r);
   ok = ok && status == 0 && (reps % 4 != 0 || (back_tc < 1e-6 * reps && back_reg < 1e-6 * reps));
   return ok ? 0 : 1;
 }
