@@ -307,26 +307,25 @@ __device__ __forceinline__ float pencil_dot(const cpx<float> (&w)[n], const floa
 
 // L1 policy of the 16-byte chunks of a pencil-blocked orbital (a warp reads 512 contiguous
 // bytes per access) in the one-pencil-per-thread layout, whose 96-register budget spills a few
-// loop-invariant values to local memory: those reloads must hit L1.  The owner orbital is read
-// once per pair and nothing re-reads it from L1 before the next pair, so it streams past L1 (no
-// allocation); the partner is read twice per pair, in the Z forward and the Z inverse stage, so
-// its first read stays in L1 longest and its last read streams.  On the 24^3, 4x4x4 k, 16-band
-// cell: 63.8 ms with every orbital read streamed, 59.4 ms with plain loads, 58.8 ms with this.
-// The layouts with two pencils a thread (no spills) are fastest with plain loads (66.5 ms
-// against 67.1 ms with this policy) and keep them.
-enum LdPolicy : int { LD_NORMAL = 0, LD_STREAM = 1, LD_KEEP = 2 };
-constexpr int kLdOwner = LD_STREAM;
+// loop-invariant values to local memory: those reloads must hit L1.  The partner is read twice
+// per pair, in the Z forward and the Z inverse stage, so its first read stays in L1 longest
+// (evict_last); the owner and the partner's last read are plain loads.  Streaming those two past
+// L1 (L1::no_allocate or L1::evict_first) also marks their lines evict-first in L2, where the
+// owner, re-read by every pair of its target, must stay: on the 24^3, 3x3x3 k, 8-band cell it
+// raised DRAM reads from 60 MB to 2.76 GB a launch (L2 hit rate 95% -> 64%) and the 24^3,
+// 8x8x8 k, 16 + 16-band apply from 7.32 s to 7.97 s.  An explicit L2::evict_normal or
+// evict_last cache hint on the streamed loads keeps L2 but costs 25% of the time (its policy
+// register and extra instructions).  The layouts with two pencils a thread (no spills) use
+// plain loads throughout.
+enum LdPolicy : int { LD_NORMAL = 0, LD_KEEP = 1 };
+constexpr int kLdOwner = LD_NORMAL;
 constexpr int kLdPartnerFirst = LD_KEEP;
-constexpr int kLdPartnerLast = LD_STREAM;
+constexpr int kLdPartnerLast = LD_NORMAL;
 
 template <int POL>
 __device__ __forceinline__ float4 ldg_pol(const float4* p) {
   float4 v;
-  if constexpr (POL == LD_STREAM) {
-    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p));
-  } else if constexpr (POL == LD_KEEP) {
+  if constexpr (POL == LD_KEEP) {
     asm volatile("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                  : "l"(p));
