@@ -683,16 +683,47 @@ __device__ __forceinline__ void stage_z_inverse(const float2* g, int t, const fl
   }
 }
 
+// Threads per x-slab barrier of the one-pencil layout, else 0.  With one pencil per thread
+// and T = 1, thread p holds the Z pencil (x, y) = (p / n, p % n) and the Y pencil
+// (x, z) = (p / n, p % n): the Z and Y stages of a pair touch only the x-planes of their own
+// threads, and only the X stage reads across x.  The barriers Z forward -> Y forward and
+// Y inverse -> Z inverse then need only the threads of the same x-planes: lcm(n, 32) threads
+// (whole warps, n^2 / lcm(n, 32) groups, named barriers 1 ...).  The groups run ahead of one
+// another between the two CTA-wide barriers around the X stage, so their shared-memory and
+// global-load phases spread out.
+constexpr int gcd_int(int a, int b) { return b == 0 ? a : gcd_int(b, a % b); }
+template <int n, int PPT, int TS>
+constexpr int slab_bar_threads() {
+  constexpr int L = n / gcd_int(n, 32) * 32;
+  if constexpr (PPT == 1 && TS == Geo<n>::NN && Geo<n>::T == 1 && Geo<n>::ZFAST_Y == 1 && Geo<n>::NN % L == 0 &&
+                Geo<n>::NN / L <= 15 && Geo<n>::NN / L > 1) {
+    return L;
+  } else {
+    return 0;
+  }
+}
+
+// Barrier of the x-slab of thread tid (SB threads; named barrier 1 + tid / SB), or of the CTA.
+template <int SB>
+__device__ __forceinline__ void slab_sync() {
+  if constexpr (SB > 0) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / SB), "n"(SB) : "memory");
+  } else {
+    __syncthreads();
+  }
+}
+
 // One pair chain between the Z stages; all threads of the CTA call it together.
 template <int n, int PPT = 2, int TS = Geo<n>::NN / PPT>
 __device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32_t ttab, float f, bool warp_on = true) {
-  __syncthreads();
+  constexpr int SB = slab_bar_threads<n, PPT, TS>();
+  slab_sync<SB>();
   if (warp_on) stage_y<n, -1, PPT, TS>(g, t, valid);
   __syncthreads();
   if (warp_on) stage_x<n, PPT, false, n * n, TS>(g, t, valid, ttab, f);
   __syncthreads();
   if (warp_on) stage_y<n, +1, PPT, TS>(g, t, valid);
-  __syncthreads();
+  slab_sync<SB>();
 }
 
 }  // namespace hse
