@@ -95,14 +95,14 @@ bool staged_fft_supported(int L);
 
 // Template body used by the per-size translation units.  `blocks_per_sm` selects the
 // occupancy variant (1: registers uncapped; 2: two CTAs per SM where they fit).
-template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false>
+template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false, int BLK = -1>
 cudaError_t pairconv_set_attr() {
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_done[dev]) {
-    cudaError_t err = cudaFuncSetAttribute(pairconv_c64_kernel<n, MODE, MINB, PPT, TSX, TC>,
+    cudaError_t err = cudaFuncSetAttribute(pairconv_c64_kernel<n, MODE, MINB, PPT, TSX, TC, BLK>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)pairconv_smem_request<n, TC>());
     if (err != cudaSuccess) return err;
@@ -111,24 +111,39 @@ cudaError_t pairconv_set_attr() {
   return cudaSuccess;
 }
 
-template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false>
-cudaError_t launch_pairconv_variant(const PairArgs& args, cudaStream_t stream) {
-  cudaError_t err = pairconv_set_attr<n, MODE, MINB, PPT, TSX, TC>();
+// BLK >= 0: the kernel compiled for that orbital layout (args.blk must match).
+template <int n, int MODE, int MINB, int PPT, int TSX, bool TC, int BLK>
+cudaError_t launch_pairconv_blk(const PairArgs& args, cudaStream_t stream) {
+  cudaError_t err = pairconv_set_attr<n, MODE, MINB, PPT, TSX, TC, BLK>();
   if (err != cudaSuccess) return err;
   const dim3 grid(args.item_count > 0 ? (unsigned)args.item_count
                                       : (unsigned)((size_t)args.nsplit * args.nk_own * args.ntiles));
-  pairconv_c64_kernel<n, MODE, MINB, PPT, TSX, TC>
+  pairconv_c64_kernel<n, MODE, MINB, PPT, TSX, TC, BLK>
       <<<grid, GeoP<n, PPT, TSX>::THREADS, pairconv_smem_request<n, TC>(), stream>>>(args);
   count_launch();
   return cudaGetLastError();
 }
 
+// One pencil per thread (the tightest register budget) has one kernel per orbital layout, so
+// that the layout's address arithmetic is fixed at compile time; the other forms read it at
+// run time.
+template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false>
+cudaError_t launch_pairconv_variant(const PairArgs& args, cudaStream_t stream) {
+  if constexpr (PPT == 1) {
+    return args.blk ? launch_pairconv_blk<n, MODE, MINB, PPT, TSX, TC, 1>(args, stream)
+                    : launch_pairconv_blk<n, MODE, MINB, PPT, TSX, TC, 0>(args, stream);
+  } else {
+    return launch_pairconv_blk<n, MODE, MINB, PPT, TSX, TC, -1>(args, stream);
+  }
+}
+
 // Resident CTAs per SM of a variant (0 on error).
 template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false>
 int pairconv_occupancy_variant() {
-  if (pairconv_set_attr<n, MODE, MINB, PPT, TSX, TC>() != cudaSuccess) return 0;
+  constexpr int BLK = PPT == 1 ? 1 : -1;
+  if (pairconv_set_attr<n, MODE, MINB, PPT, TSX, TC, BLK>() != cudaSuccess) return 0;
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pairconv_c64_kernel<n, MODE, MINB, PPT, TSX, TC>,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pairconv_c64_kernel<n, MODE, MINB, PPT, TSX, TC, BLK>,
                                                     GeoP<n, PPT, TSX>::THREADS,
                                                     pairconv_smem_request<n, TC>()) != cudaSuccess)
     return 0;

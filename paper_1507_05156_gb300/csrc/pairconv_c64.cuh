@@ -492,27 +492,50 @@ __device__ __forceinline__ int x_pencil(int p) {
 
 // Stage X: FFT, multiply by the kernel row (cached in TMEM, already times -alpha/(N_k N))
 // times the occupation f, inverse FFT, for the PPT pencils.  Warp-wide (TMEM loads).
-// XP (one pencil per thread): the bank-spread X-pencil order of x_pencil over the first XR.
+// XP: the bank-spread X-pencil order of x_pencil over the first XR.  xs_tab (one pencil per
+// thread): each thread's X pencil as its smem offset, in that order, from a table in shared
+// memory; its kernel row then comes in eight TMEM columns at a time after the forward
+// transform instead of being held through it (fewer live registers).
 template <int n, int PPT = 2, bool XP = false, int XR = n * n, int TS = Geo<n>::NN / PPT>
-__device__ __forceinline__ void stage_x(float2* g, int t, bool valid, uint32_t ttab, float f) {
+__device__ __forceinline__ void stage_x(float2* g, int t, bool valid, uint32_t ttab, float f,
+                                        const unsigned short* xs_tab = nullptr) {
   using G = Geo<n>;
 #pragma unroll 1
   for (int ps = 0; ps < PPT; ++ps) {
     if (TS * PPT != G::NN && t + ps * TS >= G::NN) break;
-    const Pencil<n> pc(x_pencil<n, XP, XR>(t + ps * TS));
-    float tv[n];
-    TmemRow<n>::load(ttab + (uint32_t)(ps * n), tv);
     cpx<float> v[n];
-    load_s<n, 1>(v, g, pc.xs, G::Q);
-    fft<n, -1, float>(v);
+    if (PPT == 1 && n % 8 == 0 && xs_tab != nullptr) {
+      const int xs = xs_tab[t];
+      load_s<n, 1>(v, g, xs, G::Q);
+      fft<n, -1, float>(v);
 #pragma unroll
-    for (int e = 0; e < n; ++e) {
-      const float w = tv[e] * f;
-      v[e].x *= w;
-      v[e].y *= w;
+      for (int c = 0; c < n / 8; ++c) {
+        float tv[8];
+        tmem_ld8(ttab + (uint32_t)(8 * c), tv);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float w = tv[e] * f;
+          v[8 * c + e].x *= w;
+          v[8 * c + e].y *= w;
+        }
+      }
+      fft<n, +1, float>(v);
+      if (valid) store_s<n, 1>(v, g, xs, G::Q);
+    } else {
+      const Pencil<n> pc(x_pencil<n, XP, XR>(t + ps * TS));
+      float tv[n];
+      TmemRow<n>::load(ttab + (uint32_t)(ps * n), tv);
+      load_s<n, 1>(v, g, pc.xs, G::Q);
+      fft<n, -1, float>(v);
+#pragma unroll
+      for (int e = 0; e < n; ++e) {
+        const float w = tv[e] * f;
+        v[e].x *= w;
+        v[e].y *= w;
+      }
+      fft<n, +1, float>(v);
+      if (valid) store_s<n, 1>(v, g, pc.xs, G::Q);
     }
-    fft<n, +1, float>(v);
-    if (valid) store_s<n, 1>(v, g, pc.xs, G::Q);
   }
 }
 
@@ -597,7 +620,7 @@ __device__ __forceinline__ void stage_z_forward(float2* g, int t, bool valid, co
     if constexpr (PPT == 1) {
       // one pencil per thread (many warps, few registers each): the two orbitals' 16-byte
       // chunks are read and multiplied one pair at a time, so that only one pencil is live
-      const size_t off = blk ? (size_t)(p >> 5) * (n / 2) * 32 + (p & 31) : (size_t)p * (n / 2);
+      const int off = blk ? (p >> 5) * (n / 2) * 32 + (p & 31) : p * (n / 2);
       const float4* a4 = reinterpret_cast<const float4*>(a) + off;
       const float4* b4 = reinterpret_cast<const float4*>(b) + off;
 #pragma unroll
@@ -658,7 +681,7 @@ __device__ __forceinline__ void stage_z_inverse(const float2* g, int t, const fl
     if constexpr (PPT == 1 && n % 4 == 0) {
       // one pencil per thread: the accumulator row and the partner move four complex values
       // (eight TMEM columns, two 16-byte chunks) at a time, so that only phi stays live
-      const size_t off = blk ? (size_t)(p >> 5) * (n / 2) * 32 + (p & 31) : (size_t)p * (n / 2);
+      const int off = blk ? (p >> 5) * (n / 2) * 32 + (p & 31) : p * (n / 2);
       const float4* w4 = reinterpret_cast<const float4*>(wbase) + off;
 #pragma unroll
       for (int c = 0; c < n / 4; ++c) {
@@ -713,14 +736,16 @@ __device__ __forceinline__ void slab_sync() {
   }
 }
 
-// One pair chain between the Z stages; all threads of the CTA call it together.
+// One pair chain between the Z stages; all threads of the CTA call it together.  xs_tab (one
+// pencil per thread): the smem offset of each thread's X pencil in the bank-spread order.
 template <int n, int PPT = 2, int TS = Geo<n>::NN / PPT>
-__device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32_t ttab, float f, bool warp_on = true) {
+__device__ __forceinline__ void pair_middle(float2* g, int t, bool valid, uint32_t ttab, float f, bool warp_on = true,
+                                            const unsigned short* xs_tab = nullptr) {
   constexpr int SB = slab_bar_threads<n, PPT, TS>();
   slab_sync<SB>();
   if (warp_on) stage_y<n, -1, PPT, TS>(g, t, valid);
   __syncthreads();
-  if (warp_on) stage_x<n, PPT, false, n * n, TS>(g, t, valid, ttab, f);
+  if (warp_on) stage_x<n, PPT, false, n * n, TS>(g, t, valid, ttab, f, xs_tab);
   __syncthreads();
   if (warp_on) stage_y<n, +1, PPT, TS>(g, t, valid);
   slab_sync<SB>();
@@ -753,7 +778,8 @@ __device__ __forceinline__ void pair_middle_occ(float2* g, int t, bool valid, ui
 // spec: this CTA's spectrum scratch (T blocked grids) when args.vtab2 is set (MODE_OCC).
 // TC: the Y and X stages on the tensor cores (stage_y_tc / stage_x_tc; the DFT tables follow
 // the grids in shared memory), for the modes with owner = target.
-template <int n, int MODE, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false>
+// BLK: the orbital layout args.blk as a compile-time constant (0 or 1; -1: read at run time).
+template <int n, int MODE, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false, int BLK = -1>
 __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, float4* smem4, uint32_t tbase,
                                               bool warp_on, float2* spec = nullptr) {
   using G = Geo<n>;
@@ -763,7 +789,10 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
-  const bool valid = tid < G::T * TS;
+  // every kernel that runs an item launches GP::THREADS threads: where those are exactly the
+  // T * TS pencil threads every thread is valid, which the compiler then knows (uniform owner,
+  // band and occupation values, fewer vector registers)
+  const bool valid = (GP::THREADS == G::T * TS) || tid < G::T * TS;
   const int slot = valid ? tid / TS : 0;
   const int t = valid ? tid - slot * TS : 0;
   float2* g = reinterpret_cast<float2*>(smem4) + slot * G::GRID_CPX;
@@ -783,7 +812,7 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
   const int kp_end = (int)(((long long)(split + 1) * args.nk_part) / args.nsplit);
   const bool active = valid && band < args.n_own;
   const int bandc = active ? band : 0;
-  const int blk = args.blk;
+  const int blk = BLK >= 0 ? BLK : args.blk;
   const size_t ostr = orb_stride<n>(blk);
   const float2* own = args.own + ((size_t)k * args.n_own + bandc) * ostr;
 
@@ -793,6 +822,14 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     for (int e = 0; e < G::ROW; ++e) z[e] = 0.f;
 #pragma unroll
     for (int ps = 0; ps < PPT; ++ps) TmemRow<G::ROW>::store(trow0 + (uint32_t)(ps * G::ROW), z);
+  }
+  // the bank-spread X-pencil order (x_pencil) of the one-pencil layout, as smem offsets of
+  // each thread's X pencil in a table in shared memory (read once per pair, no global lookup)
+  constexpr bool kXTab = PPT == 1 && n % 8 == 0 && !TC && MODE != MODE_OCC && G::T == 1 && G::P != n;
+  __shared__ unsigned short xs_tab[kXTab ? G::NN : 1];
+  if constexpr (kXTab) {
+    for (int i = tid; i < G::NN; i += blockDim.x) xs_tab[i] = (unsigned short)Pencil<n>(x_pencil<n, true>(i)).xs;
+    // ordered before its first use by the CTA barrier in front of the first X stage
   }
 
   // compensated accumulation over the k' groups (one group per k'): APPLY / OCC keep the
@@ -811,7 +848,7 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
       const int p = t + ps * TS;
       if constexpr (PPT == 1 && n % 4 == 0) {
         // one pencil per thread: eight accumulator columns (two 16-byte chunks) at a time
-        const size_t loff = blk ? (size_t)(p >> 5) * (n / 2) * 32 + (p & 31) : (size_t)p * (n / 2);
+        const int loff = blk ? (p >> 5) * (n / 2) * 32 + (p & 31) : p * (n / 2);
         float dpart = 0.f;
 #pragma unroll
         for (int c = 0; c < n / 4; ++c) {
@@ -868,7 +905,12 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
     // q = k_i - k_j: APPLY-like modes own i (at k) and pair with j at kp; OCC owns j (at k)
     const int qrow = (MODE == MODE_OCC) ? args.qidx[kp * args.nk_own + k] : args.qidx[k * args.nk_part + kp];
     const float* dvrow = fuse_w ? args.vtab2 + (size_t)qrow * G::N : nullptr;
-    if (warp_on && !TC) cache_kernel_row<n, PPT, false, n * n, TS>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
+    if (warp_on && !TC) {
+      if constexpr (kXTab)
+        cache_kernel_row<n, PPT, true, n * n, TS>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
+      else
+        cache_kernel_row<n, PPT, false, n * n, TS>(t, ttab, args.vtab + (size_t)qrow * G::N, args.scale);
+    }
     for (int j = 0; j < args.n_part; ++j) {
       const float2* part = args.part + ((size_t)kp * args.n_part + j) * ostr;
       if constexpr (MODE != MODE_OCC) {
@@ -880,7 +922,7 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
               reinterpret_cast<const TcTables<n>*>(reinterpret_cast<const char*>(smem4) + G::SMEM_BYTES);
           pair_middle_tc<n, PPT, TS>(g, t, tct, args.vtab + (size_t)qrow * G::N, args.scale * f, warp_on);
         } else {
-          pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on);
+          pair_middle<n, PPT, TS>(g, t, valid, ttab, f, warp_on, kXTab ? xs_tab : nullptr);
         }
         if (warp_on) stage_z_inverse<n, EPI_MUL, PPT, TS>(g, t, part, trow0, blk);      // acc += u_j phi
       } else {
@@ -938,7 +980,8 @@ __device__ __forceinline__ void pairconv_item(const PairArgs& args, int item, fl
   }
 }
 
-template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false>
+// BLK: args.blk as a compile-time constant (0 or 1), or -1 (read at run time).
+template <int n, int MODE, int MINB, int PPT = 2, int TSX = Geo<n>::NN / PPT, bool TC = false, int BLK = -1>
 __global__ void __launch_bounds__(GeoP<n, PPT, TSX>::THREADS, MINB) pairconv_c64_kernel(const PairArgs args) {
   using G = GeoP<n, PPT, TSX>;
   extern __shared__ __align__(16) float4 smem4[];
@@ -956,7 +999,7 @@ __global__ void __launch_bounds__(GeoP<n, PPT, TSX>::THREADS, MINB) pairconv_c64
   const uint32_t tbase = tmem_base_sh;
   // one spectrum scratch (T blocked grids) per CTA of the launch, for MODE_OCC with omega
   float2* spec = args.spec ? args.spec + (size_t)blockIdx.x * Geo<n>::T * OrbBlk<n>::NBK : nullptr;
-  pairconv_item<n, MODE, PPT, TSX, TC>(args, args.item0 + (int)blockIdx.x, smem4, tbase, true, spec);
+  pairconv_item<n, MODE, PPT, TSX, TC, BLK>(args, args.item0 + (int)blockIdx.x, smem4, tbase, true, spec);
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
