@@ -42,7 +42,7 @@ DEFAULT_SM_MHZ = 2070.0  # maximum SM clock of a GB300, used when no measured fi
 # DRAM traffic of one launch of the fused 24^3 kernel from an ncu capture of the full
 # workload, valid only while the kernel sources hash to the value recorded with it (else
 # reported as null).
-TRAFFIC = {"sha": None, "bytes_per_launch": None}
+TRAFFIC = {"sha": "7aed2f5aa6eaed2c", "bytes_per_launch": 115.83e9}  # 106.37 GB read + 9.46 GB written
 
 
 def _code_only(src: str) -> str:
@@ -551,11 +551,21 @@ def run_config(name: str, args):
         oc = [torch.from_numpy(c.occ).to(dev) for c in cells]
         out = [torch.empty_like(u) for u in uo]
         ms = _timed(lambda: hse.hse_fock_apply_batched(plan, uo, oc, uo, out=out), steps, warmup, stream)
+        # the same cells as 32 separate single-cell calls on the same stream (one plan each)
+        plans = [hse.Plan(c.grid, c.lattice, c.kpts, c.n_occ, c.n_tgt, c.omega, c.alpha) for c in cells]
+
+        def separate():
+            for pl, u, o, r in zip(plans, uo, oc, out):
+                hse.hse_fock_apply(pl, u, o, u, out=r)
+
+        ms_sep = _timed(separate, steps, warmup, stream)
         pairs = sum(c.pairs for c in cells)
         flops = sum(algorithmic_flops_per_pair(int(np.prod(c.grid))) * c.pairs for c in cells)
         line.update(value=pairs / ms * 1e3, ms_per_step=ms, steps=steps, warmup=warmup, dtype="f32",
                     config={"workload": "batched_32_uneven_cells", "cells": len(cells), "pairs_per_step": pairs,
                             "l2": "not flushed (one graph replay per step, back to back)"},
+                    separate_calls={"ms_per_step": ms_sep, "value": pairs / ms_sep * 1e3,
+                                    "batched_speedup": ms_sep / ms},
                     roofline={"bound": "alu", "achieved": flops / ms / 1e9, "peak": FP32_PEAK_TFLOPS,
                               "unit": "TFLOP/s", "frac": flops / ms / 1e9 / FP32_PEAK_TFLOPS,
                               "peak_source": "FP32 FMA lanes x max SM clock"})
