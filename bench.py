@@ -6,8 +6,9 @@ and 32 target bands (the 16 occupied + 16 empty ones) goes through pair density 
 screened kernel -> inverse FFT -> multiply-accumulate (134,217,728 pair convolutions).  This
 is the largest single-GPU configuration of the method's workloads.  Inputs are seeded
 synthetic orbitals already resident in HBM; they (2.7 GB) are far larger than L2 (129 MB),
-so no flush is needed between steps.  The 20^3, 4x4x4 k, 16-band cell is reported beside it
-(key "c64_20cube").
+so no flush is needed between steps.  The 20^3, 4x4x4 k, 16-band cell (key "c64_20cube") and
+the 32-cell uneven batch, batched call against 32 separate calls (key "batched_32_cells"), are
+reported beside it.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl cuda|reference]
 
@@ -42,7 +43,7 @@ DEFAULT_SM_MHZ = 2070.0  # maximum SM clock of a GB300, used when no measured fi
 # DRAM traffic of one launch of the fused 24^3 kernel from an ncu capture of the full
 # workload, valid only while the kernel sources hash to the value recorded with it (else
 # reported as null).
-TRAFFIC = {"sha": "7aed2f5aa6eaed2c", "bytes_per_launch": 115.83e9}  # 106.37 GB read + 9.46 GB written
+TRAFFIC = {"sha": "146b71d8873bb8d9", "bytes_per_launch": 115.83e9}  # 106.37 GB read + 9.46 GB written
 
 
 def _code_only(src: str) -> str:
@@ -266,6 +267,37 @@ def run_second(dev, steps, warmup, sms, sm_mhz):
             "roofline_frac": flops / ms / 1e9 / peak, "l2": config_dict(cell)["l2"]}
 
 
+def run_batched(dev, steps, warmup, sms, sm_mhz):
+    """The 32-cell uneven batch (grids from {12, 16, 18, 20, 24}^3, 2^3-4^3 k, 4-16 bands;
+    5,094,023 pair convolutions): one hse_fock_apply_batched call per step (autotuned on its first
+    call, then one graph replay), and the same cells as 32 separate hse_fock_apply calls."""
+    import torch
+    from paper_1507_05156_gb300 import hse, inputs
+    stream = torch.cuda.current_stream()
+    cells = inputs.batched_cells()
+    plan = hse.BatchedPlan(cells)
+    uo = [torch.from_numpy(c.u_occ.astype(np.complex64)).to(dev) for c in cells]
+    oc = [torch.from_numpy(c.occ).to(dev) for c in cells]
+    out = [torch.empty_like(u) for u in uo]
+    ms = _timed(lambda: hse.hse_fock_apply_batched(plan, uo, oc, uo, out=out), steps, warmup, stream)
+    hse.hse_status(plan)
+    plans = [hse.Plan(c.grid, c.lattice, c.kpts, c.n_occ, c.n_tgt, c.omega, c.alpha) for c in cells]
+
+    def separate():
+        for pl, u, o, r in zip(plans, uo, oc, out):
+            hse.hse_fock_apply(pl, u, o, u, out=r)
+
+    ms_sep = _timed(separate, steps, warmup, stream)
+    pairs = sum(c.pairs for c in cells)
+    flops = sum(algorithmic_flops_per_pair(int(np.prod(c.grid))) * c.pairs for c in cells)
+    peak = fp32_peak_tflops(sms, sm_mhz)
+    return {"workload": "batched_32_uneven_cells", "cells": len(cells), "pairs_per_step": pairs,
+            "value": pairs / ms * 1e3, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "roofline_frac": flops / ms / 1e9 / peak,
+            "separate_calls": {"ms_per_step": ms_sep, "value": pairs / ms_sep * 1e3, "batched_speedup": ms_sep / ms},
+            "l2": "not flushed (one graph replay per step, back to back)"}
+
+
 def run_cuda(args, rank, world, dist):
     import torch
     from paper_1507_05156_gb300 import hse, inputs
@@ -385,6 +417,9 @@ def run_cuda(args, rank, world, dist):
     second = None
     if not args.no_second:
         second = run_second(dev, min(args.steps, 20), max(3, args.warmup), sms, sm_mhz)
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(dev, min(args.steps, 5), 2, sms, sm_mhz)
 
     # ---- the plain FP64 GPU form: every target against a sample of k' (extrapolated) ----
     fp64 = None
@@ -443,6 +478,7 @@ def run_cuda(args, rank, world, dist):
         "cpu_baseline": cpu,
         "fp64_gpu": fp64,
         "c64_20cube": second,
+        "batched_32_cells": batched,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "gpu_launches": launches,
@@ -545,29 +581,13 @@ def run_config(name: str, args):
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "data": "synthetic"}
     if name == "batched":
-        cells = inputs.batched_cells()
-        plan = hse.BatchedPlan(cells)
-        uo = [torch.from_numpy(c.u_occ.astype(np.complex64)).to(dev) for c in cells]
-        oc = [torch.from_numpy(c.occ).to(dev) for c in cells]
-        out = [torch.empty_like(u) for u in uo]
-        ms = _timed(lambda: hse.hse_fock_apply_batched(plan, uo, oc, uo, out=out), steps, warmup, stream)
-        # the same cells as 32 separate single-cell calls on the same stream (one plan each)
-        plans = [hse.Plan(c.grid, c.lattice, c.kpts, c.n_occ, c.n_tgt, c.omega, c.alpha) for c in cells]
-
-        def separate():
-            for pl, u, o, r in zip(plans, uo, oc, out):
-                hse.hse_fock_apply(pl, u, o, u, out=r)
-
-        ms_sep = _timed(separate, steps, warmup, stream)
-        pairs = sum(c.pairs for c in cells)
-        flops = sum(algorithmic_flops_per_pair(int(np.prod(c.grid))) * c.pairs for c in cells)
-        line.update(value=pairs / ms * 1e3, ms_per_step=ms, steps=steps, warmup=warmup, dtype="f32",
-                    config={"workload": "batched_32_uneven_cells", "cells": len(cells), "pairs_per_step": pairs,
-                            "l2": "not flushed (one graph replay per step, back to back)"},
-                    separate_calls={"ms_per_step": ms_sep, "value": pairs / ms_sep * 1e3,
-                                    "batched_speedup": ms_sep / ms},
-                    roofline={"bound": "alu", "achieved": flops / ms / 1e9, "peak": FP32_PEAK_TFLOPS,
-                              "unit": "TFLOP/s", "frac": flops / ms / 1e9 / FP32_PEAK_TFLOPS,
+        b = run_batched(dev, steps, warmup, sms, max_sm_mhz(None)[0])
+        line.update(value=b["value"], ms_per_step=b["ms_per_step"], steps=steps, warmup=warmup, dtype="f32",
+                    config={"workload": b["workload"], "cells": b["cells"], "pairs_per_step": b["pairs_per_step"],
+                            "l2": b["l2"]},
+                    separate_calls=b["separate_calls"],
+                    roofline={"bound": "alu", "achieved": b["roofline_frac"] * FP32_PEAK_TFLOPS,
+                              "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": b["roofline_frac"],
                               "peak_source": "FP32 FMA lanes x max SM clock"})
     elif name in ("fp64_12cube", "c64_24cube", "c64_24cube_tc"):
         w = 0 if name == "fp64_12cube" else 2
@@ -659,6 +679,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-second", action="store_true", help="skip the 20^3 cell reported beside the headline")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 32-cell batch reported beside the headline")
     ap.add_argument("--profile-case", default=None, metavar="N,KM,NB[,tc] | batched,C | workload,W",
                     help="only run two applies of one cell (for ncu captures of secondary kernels)")
     ap.add_argument("--config", choices=CONFIGS, default=None,

@@ -177,7 +177,9 @@ __global__ void __launch_bounds__(LayoutOne<12>::THREADS, 1) pairconv_batched_st
 
 // PPT, TS: the pencil layout of the 24^3 items (one pencil per thread on 576 threads, or the
 // ragged form on 384).
-template <int MODE, int PPT, int TS>
+// BLK: the orbital layout of every cell in the list as a compile-time constant (1: all read
+// pencil-blocked copies), or -1 (each cell's PairArgs::blk).
+template <int MODE, int PPT, int TS, int BLK>
 __global__ void __launch_bounds__(GeoP<24, PPT, TS>::THREADS, 1) pairconv_batched_pencil_kernel(const BatchArgs b) {
   extern __shared__ __align__(16) float4 smem4[];
   __shared__ uint32_t tmem_base_sh;
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(GeoP<24, PPT, TS>::THREADS, 1) pairconv_batche
     load_cell_args(&pa_sh, c.pa);
     switch (c.n) {
       case 24:
-        pairconv_item<24, MODE, PPT, TS>(pa_sh, wi.item, smem4, tbase, warp < GeoP<24, PPT, TS>::WARPS);
+        pairconv_item<24, MODE, PPT, TS, false, BLK>(pa_sh, wi.item, smem4, tbase, warp < GeoP<24, PPT, TS>::WARPS);
         break;
       default: break;  // the host puts only the sides above in this list
     }
@@ -250,20 +252,20 @@ bool batched_stage_geometry(int n, int* sp, int* box_rows) {
   }
 }
 
-template <int PPT, int TS>
+template <int PPT, int TS, int BLK>
 cudaError_t launch_pencil_list(const BatchArgs& pencil, int sms, cudaStream_t stream) {
   static bool done[64] = {};
-  cudaError_t err = set_smem(pairconv_batched_pencil_kernel<MODE_APPLY, PPT, TS>, kPencilSmem, done);
+  cudaError_t err = set_smem(pairconv_batched_pencil_kernel<MODE_APPLY, PPT, TS, BLK>, kPencilSmem, done);
   if (err != cudaSuccess) return err;
-  pairconv_batched_pencil_kernel<MODE_APPLY, PPT, TS>
+  pairconv_batched_pencil_kernel<MODE_APPLY, PPT, TS, BLK>
       <<<sms < pencil.nitems ? sms : pencil.nitems, GeoP<24, PPT, TS>::THREADS, kPencilSmem, stream>>>(pencil);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& staged12, const BatchArgs& pencil, int sms,
-                                    int pencil_layout, cudaStream_t stream, cudaStream_t side, cudaEvent_t fork,
-                                    cudaEvent_t join) {
+                                    int pencil_layout, bool pencil_blocked, cudaStream_t stream, cudaStream_t side,
+                                    cudaEvent_t fork, cudaEvent_t join) {
   static bool done_s[64] = {}, done_12[64] = {};
   cudaError_t err = set_smem(pairconv_batched_staged_kernel<MODE_APPLY>, kStagedSmem, done_s);
   if (err == cudaSuccess) err = set_smem(pairconv_batched_staged12_kernel<MODE_APPLY>, kStaged12Smem, done_12);
@@ -280,8 +282,11 @@ cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& st
     s2 = side;
   }
   if (pencil.nitems > 0) {
-    err = pencil_layout == kPencilRagged ? launch_pencil_list<2, kRaggedThreads>(pencil, sms, stream)
-                                         : launch_pencil_list<1, Geo<24>::NN>(pencil, sms, stream);
+    if (pencil_layout == kPencilRagged)
+      err = launch_pencil_list<2, kRaggedThreads, -1>(pencil, sms, stream);
+    else  // one pencil per thread: the layout fixed at compile time where every cell is blocked
+      err = pencil_blocked ? launch_pencil_list<1, Geo<24>::NN, 1>(pencil, sms, stream)
+                           : launch_pencil_list<1, Geo<24>::NN, -1>(pencil, sms, stream);
     if (err != cudaSuccess) return err;
   }
   if (staged.nitems > 0) {

@@ -257,6 +257,11 @@ using namespace hse;
 // occupied orbitals at the sampled k' (VJP w.r.t. u_occ).
 enum OwnerRole : int { ROLE_TGT = 0, ROLE_ENERGY = 1, ROLE_OCC = 2 };
 
+// Streams (branches of the captured graph) of the per-cell batched form: each cell's
+// single-cell launches go to the branch with the least work so far, so that a cell's last
+// wave of CTAs shares the GPU with the next cells instead of leaving SMs idle.
+constexpr int kCellBranches = 3;
+
 struct hse_plan_s {
   hse_problem p;
   std::vector<double> kpts;
@@ -333,6 +338,12 @@ struct hse_plan_s {
   bool batch_serial = false;            // autotuned: the two persistent kernels one after the other
   cudaStream_t side_stream = nullptr;   // the staged kernel's stream when both run at once
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool batch_percell = false;           // autotuned: every cell's single-cell launches, on parallel streams
+  cudaStream_t cell_side[kCellBranches - 1] = {};  // per-cell form: the branches beside the main stream
+  cudaEvent_t cell_join[kCellBranches - 1] = {};
+  std::vector<const void*> call_ptrs;   // this call's u_occ, occ, u_tgt, vx_out of each cell
+  std::vector<const void*> graph_ptrs;  // per-cell form: the call_ptrs the graph was captured with
+  bool percell_warm = false;            // per-cell form: the sub-plans' scratch exists (one uncaptured run)
   int sms = 0;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -389,7 +400,7 @@ int autotune_lookup(const std::string& key) {
     if ((size_t)(tab - line.data()) == key.size() && std::strncmp(line.data(), key.data(), key.size()) == 0) {
       const int v = std::atoi(tab + 1);
       const int split = v & 7;
-      if (v > 0 && v < (1 << 10) && (split == 1 || split == 2 || split == 4)) found = v;  // the last entry wins
+      if (v > 0 && v < (1 << 11) && (split == 1 || split == 2 || split == 4)) found = v;  // the last entry wins
     }
   }
   std::fclose(f);
@@ -408,21 +419,24 @@ void autotune_store(const std::string& key, int shape) {
 // One point of the batched autotuner's search space, stored in the autotune cache as an int:
 // bits 0-2 the k' split (1, 2 or 4), bit 3 the ragged 24^3 layout, bit 4 the kernels one after
 // the other, bits 5-9 LayoutSeq for the staged sides 8, 16, 18, 20, 12 (12^3 then runs in the
-// 512-thread staged kernel instead of its own LayoutOne kernel).  Zero bits are the defaults, so
-// a bare split (an older cache line) reads as the default shape.
+// 512-thread staged kernel instead of its own LayoutOne kernel), bit 10 the per-cell form (every
+// cell's single-cell launches on the branches of the graph; the other bits then unused).  Zero
+// bits are the defaults, so a bare split (an older cache line) reads as the default shape.
 constexpr int kShapeSides = 5;
 struct BatchShape {
   int split = 1;
   int layout24 = kPencilOne;
   bool serial = false;
   int seq[kShapeSides] = {0, 0, 0, 0, 0};  // sides 8, 16, 18, 20, 12
+  bool percell = false;
   int encode() const {
-    int v = split | (layout24 == kPencilRagged ? 8 : 0) | (serial ? 16 : 0);
+    int v = split | (layout24 == kPencilRagged ? 8 : 0) | (serial ? 16 : 0) | (percell ? 1024 : 0);
     for (int i = 0; i < kShapeSides; ++i) v |= seq[i] ? (32 << i) : 0;
     return v;
   }
   static BatchShape decode(int v) {
     BatchShape s;
+    s.percell = (v & 1024) != 0;
     s.split = v & 7;
     s.layout24 = (v & 8) ? kPencilRagged : kPencilOne;
     s.serial = (v & 16) != 0;
@@ -555,6 +569,10 @@ int hse_plan_destroy(hse_plan plan) {
   if (plan->side_stream) cudaStreamDestroy(plan->side_stream);
   if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
   if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+  for (int b = 0; b < kCellBranches - 1; ++b) {
+    if (plan->cell_side[b]) cudaStreamDestroy(plan->cell_side[b]);
+    if (plan->cell_join[b]) cudaEventDestroy(plan->cell_join[b]);
+  }
   cudaFree(plan->qidx);
   cudaFree(plan->qvec);
   cudaFree(plan->dkpts);
@@ -1067,16 +1085,74 @@ void build_batch(hse_plan plan, int split, void* const* vx_out) {
   cudaMemcpy(plan->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
 }
 
-// counter reset + the two persistent kernels + reduction of split cells (graph-capturable)
+// The per-cell form of a batched call: each cell's single-cell apply (the kernels and launch
+// shape a plan of that cell alone uses) on one of kCellBranches streams forked from st, cells
+// in decreasing work, each to the branch with the least work so far.  Graph-capturable once
+// every sub-plan's scratch exists (after one uncaptured call).  A failed device-side wait
+// records its status in the batched plan's status word.
+int run_batch_percell(hse_plan plan, cudaStream_t st) {
+  const int ncells = (int)plan->cells.size();
+  std::vector<int> order(ncells);
+  std::vector<double> cost(ncells);
+  for (int c = 0; c < ncells; ++c) {
+    const hse_problem& q = plan->cells[c]->p;
+    const double n = q.grid[0];
+    order[c] = c;
+    cost[c] = (double)q.nk * q.n_tgt * q.nk * q.n_occ * n * n * n * std::log2(n);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  cudaStream_t br[kCellBranches];
+  br[0] = st;
+  for (int b = 1; b < kCellBranches; ++b) br[b] = plan->cell_side[b - 1];
+  cudaError_t e = cudaEventRecord(plan->ev_fork, st);
+  for (int b = 1; b < kCellBranches && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(br[b], plan->ev_fork, 0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  double load[kCellBranches] = {};
+  int rc = HSE_OK;
+  for (int c : order) {
+    int b = 0;
+    for (int i = 1; i < kCellBranches; ++i)
+      if (load[i] < load[b]) b = i;
+    load[b] += cost[c];
+    const hse_plan sub = plan->cells[c];
+    PairArgs a = base_args(sub);
+    a.own = (const float2*)plan->call_ptrs[4 * c + 2];
+    a.part = (const float2*)plan->call_ptrs[4 * c + 0];
+    a.occ = (const double*)plan->call_ptrs[4 * c + 1];
+    a.out = (float2*)plan->call_ptrs[4 * c + 3];
+    a.n_part = sub->p.n_occ;
+    a.status = plan->status;
+    rc = run_pairconv(sub, MODE_APPLY, a, sub->p.n_tgt, br[b]);
+    if (rc) break;
+  }
+  // every branch joins st again, also after an error (no capture is left forked)
+  for (int b = 1; b < kCellBranches; ++b) {
+    cudaError_t je = cudaEventRecord(plan->cell_join[b - 1], br[b]);
+    if (je == cudaSuccess) je = cudaStreamWaitEvent(st, plan->cell_join[b - 1], 0);
+    if (je != cudaSuccess && rc == HSE_OK) rc = cuda_fail(je);
+  }
+  return rc;
+}
+
+// counter reset + the two persistent kernels + reduction of split cells (graph-capturable);
+// the per-cell form instead when the autotuner chose it
 cudaError_t run_batch(hse_plan plan, cudaStream_t st) {
+  if (plan->batch_percell) {
+    const int rc = run_batch_percell(plan, st);
+    if (rc == HSE_OK) plan->percell_warm = true;
+    return rc == HSE_OK ? cudaSuccess : (rc == HSE_ERR_NOMEM ? cudaErrorMemoryAllocation : cudaErrorUnknown);
+  }
   cudaError_t e = cudaMemsetAsync(plan->d_counter, 0, 3 * sizeof(int), st);
   const int n0 = plan->nitems_staged, n1 = plan->nitems_pencil;
   const BatchArgs staged{plan->d_cells, plan->d_items, n0, plan->d_counter, plan->status};
   const BatchArgs pencil{plan->d_cells, plan->d_items + n0, n1, plan->d_counter + 1, plan->status};
   const BatchArgs staged12{plan->d_cells, plan->d_items + n0 + n1, plan->nitems - n0 - n1, plan->d_counter + 2,
                            plan->status};
+  bool pencil_blocked = true;  // every 24^3 cell reads its pencil-blocked copies (set per call)
+  for (const BatchCell& bc : plan->h_cells)
+    if (bc.n == 24 && bc.pa.blk != 1) pencil_blocked = false;
   if (e == cudaSuccess)
-    e = launch_pairconv_batched(staged, staged12, pencil, plan->sms, plan->batch_layout24, st,
+    e = launch_pairconv_batched(staged, staged12, pencil, plan->sms, plan->batch_layout24, pencil_blocked, st,
                                 plan->batch_serial ? nullptr : plan->side_stream, plan->ev_fork, plan->ev_join);
   if (e == cudaSuccess && plan->batch_split != 1) {
     reduce_splits_batched<<<plan->sms * 4, 256, 0, st>>>(plan->d_cells, (int)plan->cells.size());
@@ -1466,7 +1542,6 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
     hse_plan sub = nullptr;
     rc = hse_plan_create(&sub, &cells[c]);
     if (rc) break;
-    sub->blocks_per_sm = 1;
     plan->cells.push_back(sub);
     const hse_problem& q = sub->p;
     const int T = slots_for(q.grid[0]);
@@ -1495,6 +1570,10 @@ int hse_plan_create_batched(hse_plan* out, const hse_problem* cells, int ncells)
   if (rc == HSE_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->side_stream, cudaStreamNonBlocking);
   if (rc == HSE_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming);
   if (rc == HSE_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming);
+  for (int b = 0; b < kCellBranches - 1; ++b) {
+    if (rc == HSE_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->cell_side[b], cudaStreamNonBlocking);
+    if (rc == HSE_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->cell_join[b], cudaEventDisableTiming);
+  }
   if (rc == HSE_OK && e != cudaSuccess) rc = cuda_fail(e);
   if (rc) {
     hse_plan_destroy(plan);
@@ -1525,6 +1604,13 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
     }
   }
   cudaStream_t st = S(stream);
+  plan->call_ptrs.resize(4 * (size_t)ncells);
+  for (int c = 0; c < ncells; ++c) {
+    plan->call_ptrs[4 * c + 0] = u_occ[c];
+    plan->call_ptrs[4 * c + 1] = occ[c];
+    plan->call_ptrs[4 * c + 2] = u_tgt[c];
+    plan->call_ptrs[4 * c + 3] = vx_out[c];
+  }
   // per-call pointers into the cell table; the split structure is set by build_batch
   for (int c = 0; c < ncells; ++c) {
     BatchCell& bc = plan->h_cells[c];
@@ -1599,6 +1685,7 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
       if (n != 24) ++nstaged_cells;
     }
     auto apply = [&](const BatchShape& s) {
+      plan->batch_percell = s.percell;
       plan->batch_layout24 = s.layout24;
       plan->batch_serial = s.serial;
       for (int c = 0; c < ncells; ++c) {
@@ -1621,12 +1708,17 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
         if (r == cudaSuccess) r = cudaEventRecord(t1, st);
         if (r == cudaSuccess) r = cudaEventSynchronize(t1);
         if (r == cudaSuccess) r = cudaEventElapsedTime(ms, t0, t1);
-        if (r == cudaSuccess && log_on())
-          std::fprintf(stderr,
-                       "hse: batched autotune: shape %d (k' split %d, 24^3 %s, %s, LayoutSeq at 8 16 18 20 12: "
-                       "%d %d %d %d %d): %.3f ms\n",
-                       s.encode(), s.split, s.layout24 == kPencilRagged ? "ragged" : "one pencil",
-                       s.serial ? "serial" : "concurrent", s.seq[0], s.seq[1], s.seq[2], s.seq[3], s.seq[4], *ms);
+        if (r == cudaSuccess && log_on()) {
+          if (s.percell)
+            std::fprintf(stderr, "hse: batched autotune: shape %d (per-cell launches on %d branches): %.3f ms\n",
+                         s.encode(), kCellBranches, *ms);
+          else
+            std::fprintf(stderr,
+                         "hse: batched autotune: shape %d (k' split %d, 24^3 %s, %s, LayoutSeq at 8 16 18 20 12: "
+                         "%d %d %d %d %d): %.3f ms\n",
+                         s.encode(), s.split, s.layout24 == kPencilRagged ? "ragged" : "one pencil",
+                         s.serial ? "serial" : "concurrent", s.seq[0], s.seq[1], s.seq[2], s.seq[3], s.seq[4], *ms);
+        }
         return r;
       };
       float best_ms = 0.f;
@@ -1661,6 +1753,11 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
         s.serial = true;
         trial(s);
       }
+      {
+        BatchShape s;  // the per-cell form (its other fields are unused)
+        s.percell = true;
+        trial(s);
+      }
       if (t0) cudaEventDestroy(t0);
       if (t1) cudaEventDestroy(t1);
       if (e != cudaSuccess) return cuda_fail(e);
@@ -1671,7 +1768,21 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
     plan->batch_split = best.split;
     if (log_on()) std::fprintf(stderr, "hse: batched autotune: chose shape %d\n", best.encode());
     apply(best);
-    // capture counter reset + persistent kernels + split reduction as one graph
+  }
+  // Capture counter reset + persistent kernels + split reduction (or the per-cell launches) as
+  // one graph.  The persistent form reads this call's pointers from the cell table, so its graph
+  // serves every later call; the per-cell form's kernels take them as launch arguments, so it is
+  // captured again when a call passes other arrays.
+  if (!plan->graph || (plan->batch_percell && plan->call_ptrs != plan->graph_ptrs)) {
+    if (plan->batch_percell && !plan->percell_warm) {  // the sub-plans allocate scratch on first use
+      e = run_batch(plan, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (plan->graph) {
+      cudaGraphExecDestroy(plan->graph);
+      plan->graph = nullptr;
+    }
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -1682,6 +1793,7 @@ int hse_fock_apply_batched(hse_plan plan, const void* const* u_occ, const double
     if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->graph, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e);
+    plan->graph_ptrs = plan->call_ptrs;
   }
   e = cudaMemcpyAsync(plan->d_cells, plan->h_cells.data(), ncells * sizeof(BatchCell), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaGraphLaunch(plan->graph, st);

@@ -85,9 +85,10 @@ constexpr int kPencilRagged = 1;
 // the 12^3 LayoutOne items (any list may be empty).  With side, fork and join given, the staged
 // kernels run on the side stream, forked from and joined back into `stream` (beside the pencil
 // kernel; capturable), else after the pencil kernel on `stream`.
+// pencil_blocked: every cell of the pencil-load list reads pencil-blocked copies (blk = 1).
 cudaError_t launch_pairconv_batched(const BatchArgs& staged, const BatchArgs& staged12, const BatchArgs& pencil, int sms,
-                                    int pencil_layout, cudaStream_t stream, cudaStream_t side, cudaEvent_t fork,
-                                    cudaEvent_t join);
+                                    int pencil_layout, bool pencil_blocked, cudaStream_t stream, cudaStream_t side,
+                                    cudaEvent_t fork, cudaEvent_t join);
 
 // One staged FP64 1-D transform pass along an axis of length L with element stride inner.
 cudaError_t launch_staged_fft(int L, int dir, double2* work, size_t nbatch, int N, int inner, cudaStream_t stream);

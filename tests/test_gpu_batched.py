@@ -80,7 +80,8 @@ def test_autotune_cache_round_trip(tmp_path, monkeypatch):
     first = hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)
     torch.cuda.synchronize()
     lines = cache.read_text().splitlines()
-    # the stored shape: bits 0-2 the k' split, higher bits the layouts and the serial flag
+    # the stored shape: bits 0-2 the k' split, higher bits the layouts, the serial flag and the
+    # per-cell form
     assert len(lines) == 1 and int(lines[0].split("\t")[1]) & 7 in (1, 2, 4)
     second = hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)
     torch.cuda.synchronize()
@@ -92,8 +93,9 @@ def test_autotune_cache_round_trip(tmp_path, monkeypatch):
 def test_every_tuned_shape_vs_oracle(tmp_path, monkeypatch):
     """The launch shapes the autotuner can choose, forced through the autotune cache: the ragged
     24^3 layout with the kernels one after the other, two pencils a thread on every staged side
-    (12^3 then in the 512-thread staged kernel) with a k' split of 2, and a split of 4 with the
-    defaults (12^3 in its own LayoutOne kernel); each against the oracle on a batch with every
+    (12^3 then in the 512-thread staged kernel) with a k' split of 2, a split of 4 with the
+    defaults (12^3 in its own LayoutOne kernel), and the per-cell form (every cell's single-cell
+    launches on parallel branches of the graph); each against the oracle on a batch with every
     supported side."""
     cache = tmp_path / "autotune.tsv"
     monkeypatch.setenv("HSE_AUTOTUNE_CACHE", str(cache))
@@ -109,9 +111,40 @@ def test_every_tuned_shape_vs_oracle(tmp_path, monkeypatch):
     hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)  # autotunes and stores its line
     torch.cuda.synchronize()
     key = cache.read_text().splitlines()[0].split("\t")[0]
-    for shape in (1 | 8 | 16, 2 | 32 | 64 | 128 | 256 | 512, 4):
+    for shape in (1 | 8 | 16, 2 | 32 | 64 | 128 | 256 | 512, 4, 1 | 1024):
         cache.write_text(f"{key}\t{shape}\n")
         out = hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)
         torch.cuda.synchronize()
         for c, o, ref in zip(cells, out, refs):
             assert rel(o.cpu().numpy(), ref) <= 1e-5, (shape, c.grid)
+
+
+def test_per_cell_form_recaptures_for_new_arrays(tmp_path, monkeypatch):
+    """The per-cell form passes the arrays to its kernels as launch arguments, so its graph is
+    captured again when a call passes other arrays: calls on two different input copies and
+    output buffers, on the first ones again, and once more on the same ones (a replay), each
+    against the oracle."""
+    cache = tmp_path / "autotune.tsv"
+    monkeypatch.setenv("HSE_AUTOTUNE_CACHE", str(cache))
+    specs = [((12, 12, 12), (2, 1, 1), 3), ((20, 20, 20), (1, 1, 2), 2), ((24, 24, 24), (2, 1, 1), 2)]
+    cells = [inputs.make_cell(970 + i, g, km, nb) for i, (g, km, nb) in enumerate(specs)]
+    for c in cells:
+        c.u_occ = c.u_occ.astype(np.complex64).astype(np.complex128)
+        c.u_tgt = c.u_occ
+    refs = [oracle.fock_apply(c.u_occ, c.occ, c.u_occ, c.kpts, c.lattice, c.grid, c.omega, c.alpha) for c in cells]
+    uo = [dev(c.u_occ) for c in cells]
+    oc = [dev(c.occ, torch.float64) for c in cells]
+    hse.hse_fock_apply_batched(hse.BatchedPlan(cells), uo, oc, uo)  # stores the autotune key
+    torch.cuda.synchronize()
+    key = cache.read_text().splitlines()[0].split("\t")[0]
+    cache.write_text(f"{key}\t{1 | 1024}\n")
+    plan = hse.BatchedPlan(cells)
+    outs = [[torch.full_like(u, float("nan")) for u in uo] for _ in range(2)]
+    uo2 = [u.clone() for u in uo]
+    for inputs_, out in ((uo, outs[0]), (uo2, outs[1]), (uo, outs[0]), (uo, outs[0])):
+        for o in out:
+            o.fill_(float("nan"))
+        hse.hse_fock_apply_batched(plan, inputs_, oc, inputs_, out=out)
+        torch.cuda.synchronize()
+        for c, o, ref in zip(cells, out, refs):
+            assert rel(o.cpu().numpy(), ref) <= 1e-5, c.grid
