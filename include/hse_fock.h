@@ -98,7 +98,8 @@ int hse_plan_create(hse_plan *out, const hse_problem *p);
 
 /* Batched plan over ncells independent cells of unequal grids, k-meshes and band
  * counts (all HSE_C64, cubic grids).  hse_fock_apply_batched runs every cell's
- * pairs in one persistent launch. */
+ * pairs in one captured graph: persistent kernels over all cells' work items, or each
+ * cell's single-cell launches on parallel branches, as the autotuner chooses. */
 int hse_plan_create_batched(hse_plan *out, const hse_problem *cells, int ncells);
 
 int hse_plan_destroy(hse_plan plan);
@@ -140,15 +141,21 @@ int hse_fock_apply_vjp(hse_plan plan, const void *u_occ, const double *occ, cons
 
 /* Batched V_x for a plan from hse_plan_create_batched: arrays of ncells HOST-side
  * pointers, each to that cell's device buffers (same layouts as hse_fock_apply).  The first
- * call autotunes the shape of the launch on the real inputs (synchronising the stream): the
- * k'-split granularity of the work items (1, 2, 4), the pencil layout of the 24^3 cells (one
- * pencil per thread or the ragged two-pencil form), the pencil layout of each staged grid side
- * (one or two pencils per thread), and whether the two persistent kernels (24^3 cells; the
- * other sides) run at once on two streams or one after the other; coordinate descent from the
- * defaults, at most nine timed runs.  It then captures the chosen launch as a CUDA graph,
- * which later calls replay.  With the environment variable HSE_AUTOTUNE_CACHE naming a file,
+ * call autotunes the shape of the launch on the real inputs (synchronising the stream).  For
+ * the persistent form: the k'-split granularity of the work items (1, 2, 4), the pencil layout
+ * of the 24^3 cells (one pencil per thread or the ragged two-pencil form), the pencil layout of
+ * each staged grid side (one or two pencils per thread), and whether the two persistent
+ * kernels (24^3 cells; the other sides) run at once on two streams or one after the other
+ * (coordinate descent from the defaults); then the per-cell form, in which every cell runs the
+ * launches of a single-cell plan, on three streams forked from `stream` and joined back.  At
+ * most ten timed runs.  The chosen form is captured as a CUDA graph that later calls replay.
+ * The persistent form reads each call's pointers from a device table, so its graph serves
+ * every call; the per-cell form passes them as launch arguments, so a call whose pointers
+ * differ from those of the captured graph captures it again (host work, no synchronisation
+ * beyond the first call's).  With the environment variable HSE_AUTOTUNE_CACHE naming a file,
  * the choice is stored there per GPU and cell list and read back by later plans instead of
- * timing. */
+ * timing (the first call of such a plan in the per-cell form runs once uncaptured, so that
+ * its cells' scratch exists before the capture). */
 int hse_fock_apply_batched(hse_plan plan, const void *const *u_occ, const double *const *occ,
                            const void *const *u_tgt, void *const *vx_out, hse_stream_t stream);
 
