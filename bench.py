@@ -253,18 +253,19 @@ def run_second(dev, steps, warmup, sms, sm_mhz):
         hse.hse_fock_apply(plan, u, occ, u, out=out)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for s in range(steps):
-        flush.fill_(s & 0xFF)
-        ev[s][0].record(stream)
-        hse.hse_fock_apply(plan, u, occ, u, out=out)
-        ev[s][1].record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for s in range(steps):
+            flush.fill_(s & 0xFF)
+            ev[s][0].record(stream)
+            hse.hse_fock_apply(plan, u, occ, u, out=out)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
     hse.hse_status(plan)
     ms = sum(a.elapsed_time(b) for a, b in ev) / steps
     flops = algorithmic_flops_per_pair(cell.npts) * cell.pairs
     peak = fp32_peak_tflops(sms, sm_mhz)
     return {"workload": cell.name, "value": cell.pairs / ms * 1e3, "unit": UNIT, "ms_per_step": ms, "steps": steps,
-            "roofline_frac": flops / ms / 1e9 / peak, "l2": config_dict(cell)["l2"]}
+            "roofline_frac": flops / ms / 1e9 / peak, "l2": config_dict(cell)["l2"], "clocks": clk.summary()}
 
 
 def run_batched(dev, steps, warmup, sms, sm_mhz):
@@ -279,7 +280,8 @@ def run_batched(dev, steps, warmup, sms, sm_mhz):
     uo = [torch.from_numpy(c.u_occ.astype(np.complex64)).to(dev) for c in cells]
     oc = [torch.from_numpy(c.occ).to(dev) for c in cells]
     out = [torch.empty_like(u) for u in uo]
-    ms = _timed(lambda: hse.hse_fock_apply_batched(plan, uo, oc, uo, out=out), steps, warmup, stream)
+    clk_b, clk_s = {}, {}
+    ms = _timed(lambda: hse.hse_fock_apply_batched(plan, uo, oc, uo, out=out), steps, warmup, stream, clk_b)
     hse.hse_status(plan)
     plans = [hse.Plan(c.grid, c.lattice, c.kpts, c.n_occ, c.n_tgt, c.omega, c.alpha) for c in cells]
 
@@ -287,15 +289,16 @@ def run_batched(dev, steps, warmup, sms, sm_mhz):
         for pl, u, o, r in zip(plans, uo, oc, out):
             hse.hse_fock_apply(pl, u, o, u, out=r)
 
-    ms_sep = _timed(separate, steps, warmup, stream)
+    ms_sep = _timed(separate, steps, warmup, stream, clk_s)
     pairs = sum(c.pairs for c in cells)
     flops = sum(algorithmic_flops_per_pair(int(np.prod(c.grid))) * c.pairs for c in cells)
     peak = fp32_peak_tflops(sms, sm_mhz)
     return {"workload": "batched_32_uneven_cells", "cells": len(cells), "pairs_per_step": pairs,
-            "value": pairs / ms * 1e3, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "value": pairs / ms * 1e3, "unit": UNIT, "ms_per_step": ms, "steps": clk_b.get("timed_calls", steps),
             "roofline_frac": flops / ms / 1e9 / peak,
-            "separate_calls": {"ms_per_step": ms_sep, "value": pairs / ms_sep * 1e3, "batched_speedup": ms_sep / ms},
-            "l2": "not flushed (one graph replay per step, back to back)"}
+            "separate_calls": {"ms_per_step": ms_sep, "value": pairs / ms_sep * 1e3, "batched_speedup": ms_sep / ms,
+                               "clocks": clk_s},
+            "clocks": clk_b, "l2": "not flushed (one graph replay per step, back to back)"}
 
 
 def run_cuda(args, rank, world, dist):
@@ -549,18 +552,36 @@ def _measured_peak(key: str):
 CONFIGS = ("fp64_12cube", "c64_24cube", "c64_24cube_tc", "diff_16cube", "batched")
 
 
-def _timed(fn, steps, warmup, stream):
-    """Mean milliseconds of fn() over `steps` calls after `warmup`, CUDA events on `stream`."""
+def _timed(fn, steps, warmup, stream, clocks=None, min_seconds=1.0):
+    """Mean milliseconds of fn() over the timed calls after `warmup`, CUDA events on `stream`.
+    With a dict `clocks`, nvidia-smi samples the timed region and the dict receives their
+    summary and the number of timed calls, which is raised above `steps` where needed so that
+    the region lasts at least `min_seconds` (the sampler's 50 ms period sees it)."""
     import torch
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(steps):
+    if clocks is not None and min_seconds > 0:
+        a.record(stream)
         fn()
-    b.record(stream)
-    b.synchronize()
+        b.record(stream)
+        b.synchronize()
+        steps = max(steps, int(np.ceil(min_seconds * 1e3 / max(a.elapsed_time(b), 1e-3))))
+    sampler = ClockSampler(torch.cuda.current_device()) if clocks is not None else None
+    if sampler:
+        sampler.__enter__()
+    try:
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+    finally:
+        if sampler:
+            sampler.__exit__(None, None, None)
+    if clocks is not None:
+        clocks.update(sampler.summary(), timed_calls=steps)
     return a.elapsed_time(b) / steps
 
 
@@ -582,10 +603,10 @@ def run_config(name: str, args):
             "vs_baseline": None, "data": "synthetic"}
     if name == "batched":
         b = run_batched(dev, steps, warmup, sms, max_sm_mhz(None)[0])
-        line.update(value=b["value"], ms_per_step=b["ms_per_step"], steps=steps, warmup=warmup, dtype="f32",
+        line.update(value=b["value"], ms_per_step=b["ms_per_step"], steps=b["steps"], warmup=warmup, dtype="f32",
                     config={"workload": b["workload"], "cells": b["cells"], "pairs_per_step": b["pairs_per_step"],
                             "l2": b["l2"]},
-                    separate_calls=b["separate_calls"],
+                    separate_calls=b["separate_calls"], clocks=b["clocks"],
                     roofline={"bound": "alu", "achieved": b["roofline_frac"] * FP32_PEAK_TFLOPS,
                               "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": b["roofline_frac"],
                               "peak_source": "FP32 FMA lanes x max SM clock"})
@@ -602,11 +623,13 @@ def run_config(name: str, args):
         u_tgt = torch.from_numpy(cell.u_tgt).to(dev, d)
         occ = torch.from_numpy(cell.occ).to(dev)
         out = torch.empty_like(u_tgt)
-        ms = _timed(lambda: hse.hse_fock_apply(plan, u_occ, occ, u_tgt, out=out), steps, warmup, stream)
+        clk = {}
+        ms = _timed(lambda: hse.hse_fock_apply(plan, u_occ, occ, u_tgt, out=out), steps, warmup, stream, clk)
         hse.hse_status(plan)
+        line["clocks"] = clk
         flops = algorithmic_flops_per_pair(int(np.prod(cell.grid))) * cell.pairs
         peak = FP64_NOMINAL_TFLOPS if w == 0 else FP32_PEAK_TFLOPS
-        line.update(value=cell.pairs / ms * 1e3, ms_per_step=ms, steps=steps, warmup=warmup,
+        line.update(value=cell.pairs / ms * 1e3, ms_per_step=ms, steps=clk.get("timed_calls", steps), warmup=warmup,
                     dtype="f64" if w == 0 else "f32",
                     config=dict(config_dict(cell), l2="not flushed" + (" (inputs 2.7 GB > L2)" if w == 2 else "")),
                     roofline={"bound": "alu", "achieved": flops / ms / 1e9, "peak": peak, "unit": "TFLOP/s",
@@ -626,7 +649,7 @@ def run_config(name: str, args):
                                 "note": "executed FP16 tensor flops of the Y/X GEMMs only"}
     elif name == "diff_16cube":
         cell = inputs.workload(4)
-        res = {}
+        res, clk = {}, {}
         for d, tag in ((torch.complex64, "c64"), (torch.complex128, "c128")):
             plan = hse.Plan(cell.grid, cell.lattice, cell.kpts, cell.n_occ, cell.n_tgt, cell.omega, cell.alpha,
                             dtype=d)
@@ -634,11 +657,11 @@ def run_config(name: str, args):
             occ = torch.from_numpy(cell.occ).to(dev)
             ybar = (0.5 * u).contiguous()
             out = torch.empty_like(u)
-            res[f"apply_ms_{tag}"] = _timed(lambda: hse.hse_fock_apply(plan, u, occ, u, out=out), steps, warmup,
-                                            stream)
-            res[f"vjp_ms_{tag}"] = _timed(lambda: hse.hse_fock_apply_vjp(plan, u, occ, u, ybar), steps, warmup,
-                                          stream)
-            res[f"energy_ms_{tag}"] = _timed(lambda: hse.hse_exchange_energy(plan, u, occ), steps, warmup, stream)
+            for key, fn in ((f"apply_ms_{tag}", lambda: hse.hse_fock_apply(plan, u, occ, u, out=out)),
+                            (f"vjp_ms_{tag}", lambda: hse.hse_fock_apply_vjp(plan, u, occ, u, ybar)),
+                            (f"energy_ms_{tag}", lambda: hse.hse_exchange_energy(plan, u, occ))):
+                clk[key] = {}
+                res[key] = _timed(fn, steps, warmup, stream, clk[key])
             hse.hse_status(plan)
         # backprop through 20 Taylor steps (dt = 0.02, E = 0.005 along x), checkpointed, complex64
         geom = tdks.Geometry(cell.grid, cell.lattice, cell.kpts, alpha=cell.alpha)
@@ -652,17 +675,20 @@ def run_config(name: str, args):
             loss = (out.conj() * psi0).real.sum()
             loss.backward()
 
-        res["backprop_20_steps_ms_c64"] = _timed(backprop, 1, 1, stream)
+        clk["backprop_20_steps_ms_c64"] = {}
+        res["backprop_20_steps_ms_c64"] = _timed(backprop, 1, 1, stream, clk["backprop_20_steps_ms_c64"])
         # the VJP executes three pair convolutions per pair (one for u_tgt, two for u_occ)
         vflops = 3 * algorithmic_flops_per_pair(int(np.prod(cell.grid))) * cell.pairs
         line["roofline"] = {"bound": "alu", "achieved": vflops / res["vjp_ms_c64"] / 1e9, "peak": FP32_PEAK_TFLOPS,
                             "unit": "TFLOP/s", "frac": vflops / res["vjp_ms_c64"] / 1e9 / FP32_PEAK_TFLOPS,
                             "peak_source": "FP32 FMA lanes x max SM clock",
                             "note": "three executed pair convolutions per pair of the forward"}
-        line.update(value=cell.pairs / res["vjp_ms_c64"] * 1e3, ms_per_step=res["vjp_ms_c64"], steps=steps,
+        line.update(value=cell.pairs / res["vjp_ms_c64"] * 1e3, ms_per_step=res["vjp_ms_c64"],
+                    steps=clk["vjp_ms_c64"].get("timed_calls", steps),
                     warmup=warmup, dtype="f32",
                     config=dict(config_dict(cell), timed="hse_fock_apply_vjp (all three gradients), complex64",
                                 l2="not flushed (inputs 7 MB, calls back to back)"),
+                    clocks=clk["vjp_ms_c64"], clocks_per_measurement=clk,
                     **{k: round(v, 4) for k, v in res.items()})
     print(json.dumps(line), flush=True)
 
