@@ -74,3 +74,20 @@ def test_workload_shapes_match_the_stated_configs():
     assert w[1]["grid"] == (20, 20, 20) and w[1]["kmesh"] == (4, 4, 4) and w[1]["n_occ"] == 16
     assert w[2]["grid"] == (24, 24, 24) and w[2]["kmesh"] == (8, 8, 8) and w[2]["n_occ"] + w[2]["n_empty"] == 32
     assert np.prod(w[0]["kmesh"]) == 8 and np.prod(w[4]["kmesh"]) == 27
+
+
+def test_clock_summary_reads_median_clock_and_throttle_reasons():
+    # nvidia-smi --format=csv,noheader,nounits lines: index, clocks.sm, clocks.max.sm, power,
+    # active mask, hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+    s = bench.ClockSampler(0)
+    s.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 2055, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 910.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line", ""]
+    out = s.summary()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+    s.lines = ["0, 1400, 2070, 500.0, 0x8, Active, Not Active, Active, Not Active"]
+    assert s.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    s.lines = []
+    assert s.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
