@@ -43,7 +43,7 @@ DEFAULT_SM_MHZ = 2070.0  # maximum SM clock of a GB300, used when no measured fi
 # DRAM traffic of one launch of the fused 24^3 kernel from an ncu capture of the full
 # workload, valid only while the kernel sources hash to the value recorded with it (else
 # reported as null).
-TRAFFIC = {"sha": "146b71d8873bb8d9", "bytes_per_launch": 115.83e9}  # 106.37 GB read + 9.46 GB written
+TRAFFIC = {"sha": "a6f17334f06074fd", "bytes_per_launch": 115.83e9}  # 106.37 GB read + 9.46 GB written
 
 
 def _code_only(src: str) -> str:

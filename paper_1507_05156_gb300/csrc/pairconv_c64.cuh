@@ -421,7 +421,7 @@ struct Pencil {
   int ys;      // Y stage: pencil (x = p / n, z = p % n), stride P
   int xs;      // X stage: pencil (y = p / n, z = p % n), stride Q
   int vr;      // X stage: kernel row element (x, y, z) at x n^2 + p
-  __device__ __forceinline__ explicit Pencil(int p) {
+  __host__ __device__ __forceinline__ explicit Pencil(int p) {
     const int hi = p / n, lo = p - hi * n;
     const int zx = G::ZFAST_Y ? hi : lo;
     const int zy = G::ZFAST_Y ? lo : hi;
